@@ -1,0 +1,210 @@
+"""ctypes wrapper of the plain CPU oracle (``fabf_oracle.c``).
+
+TEST INFRASTRUCTURE.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package.  The CUDA product
+path (``paper_1811_02308_gb300``) never imports it.
+
+All arrays are numpy; images are uint8 (H, W) with an optional row pitch,
+``theta`` and ``sigma`` are float32 (H, W) C-contiguous.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "fabf_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+NMAX = 6
+WMAX = 40
+
+
+def build(force: bool = False) -> str:
+    """Compile ``liboracle.so`` next to its source with gcc (no CUDA)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".tmp.%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-ffp-contract=off",
+                               "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    lib = C.CDLL(build())
+    u8p = C.POINTER(C.c_uint8)
+    f32p = C.POINTER(C.c_float)
+    f64p = C.POINTER(C.c_double)
+    i64p = C.POINTER(C.c_int64)
+    i32p = C.POINTER(C.c_int32)
+    L = C.c_long
+    I = C.c_int
+    lib.oracle_hilbert_inverse.argtypes = [I, i64p]
+    lib.oracle_integrals.argtypes = [C.c_double, C.c_double, I, f64p]
+    lib.oracle_bounds.argtypes = [u8p, I, I, L, I, u8p, u8p]
+    lib.oracle_moments.argtypes = [u8p, I, I, L, I, I, i64p]
+    lib.oracle_shifted_moments.argtypes = [u8p, I, I, L, I, I, i64p]
+    lib.oracle_fabf.argtypes = [u8p, f32p, f32p, I, I, L, I, I, f64p, C.POINTER(L)]
+    lib.oracle_fabf_pixels.argtypes = [u8p, f32p, f32p, I, I, L, I, I, i32p, i32p, L,
+                                       f64p, C.POINTER(L)]
+    lib.oracle_fabf_trace.argtypes = [u8p, f32p, f32p, I, I, L, I, I, I, I, i32p, i64p,
+                                      i64p, f64p, f64p, f64p, f64p, f64p, f64p, i32p]
+    lib.oracle_bruteforce.argtypes = [u8p, f32p, f32p, I, I, L, I, f64p]
+    lib.oracle_bruteforce_pixels.argtypes = [u8p, f32p, f32p, I, I, L, I, i32p, i32p, L,
+                                             f64p]
+    for fn in (lib.oracle_hilbert_inverse, lib.oracle_integrals, lib.oracle_bounds,
+               lib.oracle_moments, lib.oracle_shifted_moments, lib.oracle_fabf,
+               lib.oracle_fabf_pixels, lib.oracle_fabf_trace, lib.oracle_bruteforce,
+               lib.oracle_bruteforce_pixels):
+        fn.restype = C.c_int
+    _lib = lib
+    return lib
+
+
+def _ptr(a, t):
+    return a.ctypes.data_as(C.POINTER(t))
+
+
+def _maps(theta, sigma):
+    return (np.ascontiguousarray(theta, dtype=np.float32),
+            np.ascontiguousarray(sigma, dtype=np.float32))
+
+
+def _check(rc, what):
+    if rc != 0:
+        raise ValueError("oracle %s rejected its arguments (rc=%d)" % (what, rc))
+
+
+def hilbert_inverse(N: int) -> np.ndarray:
+    """Closed-form inverse of the (N+1)x(N+1) Hilbert matrix, Eq. (19), int64."""
+    out = np.zeros((N + 1, N + 1), dtype=np.int64)
+    _check(_load().oracle_hilbert_inverse(N, _ptr(out, C.c_int64)), "hilbert_inverse")
+    return out
+
+
+def integrals(lam: float, t0: float, K: int) -> np.ndarray:
+    """I_0..I_K of Eq. (28), each times exp(lambda d^2), d = dist(t0, [0,1])."""
+    out = np.zeros(K + 1, dtype=np.float64)
+    _check(_load().oracle_integrals(float(lam), float(t0), int(K), _ptr(out, C.c_double)),
+           "integrals")
+    return out
+
+
+def bounds(f, w):
+    """alpha_i, beta_i of Eq. (8): window min and max, uint8 (H, W) each."""
+    f = np.ascontiguousarray(f, dtype=np.uint8)
+    H, W = f.shape
+    a = np.zeros((H, W), np.uint8)
+    b = np.zeros((H, W), np.uint8)
+    _check(_load().oracle_bounds(_ptr(f, C.c_uint8), H, W, W, w, _ptr(a, C.c_uint8),
+                                 _ptr(b, C.c_uint8)), "bounds")
+    return a, b
+
+
+def moments(f, w, N):
+    """m_k of Eq. (17) (k = 0..N), int64 (N+1, H, W); m_0 is the window size."""
+    f = np.ascontiguousarray(f, dtype=np.uint8)
+    H, W = f.shape
+    m = np.zeros((N + 1, H, W), np.int64)
+    _check(_load().oracle_moments(_ptr(f, C.c_uint8), H, W, W, w, N, _ptr(m, C.c_int64)),
+           "moments")
+    return m
+
+
+def shifted_moments(f, w, N):
+    """M_k = sum over the window of (f - alpha)^k, int64 (N+1, H, W)."""
+    f = np.ascontiguousarray(f, dtype=np.uint8)
+    H, W = f.shape
+    M = np.zeros((N + 1, H, W), np.int64)
+    _check(_load().oracle_shifted_moments(_ptr(f, C.c_uint8), H, W, W, w, N,
+                                          _ptr(M, C.c_int64)), "shifted_moments")
+    return M
+
+
+def fabf(f, theta, sigma, w, N):
+    """Algorithm 1 on the whole image -> (g_hat float64 (H, W), n_fallback)."""
+    f = np.ascontiguousarray(f, dtype=np.uint8)
+    H, W = f.shape
+    theta, sigma = _maps(theta, sigma)
+    out = np.zeros((H, W), np.float64)
+    nf = C.c_long(0)
+    _check(_load().oracle_fabf(_ptr(f, C.c_uint8), _ptr(theta, C.c_float),
+                               _ptr(sigma, C.c_float), H, W, W, w, N,
+                               _ptr(out, C.c_double), C.byref(nf)), "fabf")
+    return out, nf.value
+
+
+def fabf_pixels(f, theta, sigma, w, N, ys, xs):
+    """Algorithm 1 at pixels (ys[j], xs[j]) -> (values float64, n_fallback)."""
+    f = np.ascontiguousarray(f, dtype=np.uint8)
+    H, W = f.shape
+    theta, sigma = _maps(theta, sigma)
+    ys = np.ascontiguousarray(ys, dtype=np.int32)
+    xs = np.ascontiguousarray(xs, dtype=np.int32)
+    out = np.zeros(len(ys), np.float64)
+    nf = C.c_long(0)
+    _check(_load().oracle_fabf_pixels(_ptr(f, C.c_uint8), _ptr(theta, C.c_float),
+                                      _ptr(sigma, C.c_float), H, W, W, w, N,
+                                      _ptr(ys, C.c_int32), _ptr(xs, C.c_int32), len(ys),
+                                      _ptr(out, C.c_double), C.byref(nf)), "fabf_pixels")
+    return out, nf.value
+
+
+def fabf_trace(f, theta, sigma, w, N, y, x):
+    """Every intermediate of Algorithm 1 at one pixel, as a dict."""
+    f = np.ascontiguousarray(f, dtype=np.uint8)
+    H, W = f.shape
+    theta, sigma = _maps(theta, sigma)
+    ab = np.zeros(2, np.int32)
+    m = np.zeros(N + 1, np.int64)
+    M = np.zeros(N + 1, np.int64)
+    mu = np.full(N + 1, np.nan)
+    c = np.full(N + 1, np.nan)
+    t0lam = np.full(2, np.nan)
+    I = np.full(N + 2, np.nan)
+    T = np.full(2, np.nan)
+    g = np.zeros(1)
+    fl = np.zeros(1, np.int32)
+    _check(_load().oracle_fabf_trace(
+        _ptr(f, C.c_uint8), _ptr(theta, C.c_float), _ptr(sigma, C.c_float), H, W, W, w, N,
+        int(y), int(x), _ptr(ab, C.c_int32), _ptr(m, C.c_int64), _ptr(M, C.c_int64),
+        _ptr(mu, C.c_double), _ptr(c, C.c_double), _ptr(t0lam, C.c_double),
+        _ptr(I, C.c_double), _ptr(T, C.c_double), _ptr(g, C.c_double),
+        _ptr(fl, C.c_int32)), "fabf_trace")
+    return dict(alpha=int(ab[0]), beta=int(ab[1]), m=m, M=M, mu=mu, c=c, t0=t0lam[0],
+                lam=t0lam[1], I=I, T1=T[0], T2=T[1], g=g[0], flat=bool(fl[0] & 1),
+                fallback=bool(fl[0] & 2))
+
+
+def bruteforce(f, theta, sigma, w):
+    """Brute-force adaptive bilateral filter, Eqs. (1)-(3), float64 (H, W)."""
+    f = np.ascontiguousarray(f, dtype=np.uint8)
+    H, W = f.shape
+    theta, sigma = _maps(theta, sigma)
+    out = np.zeros((H, W), np.float64)
+    _check(_load().oracle_bruteforce(_ptr(f, C.c_uint8), _ptr(theta, C.c_float),
+                                     _ptr(sigma, C.c_float), H, W, W, w,
+                                     _ptr(out, C.c_double)), "bruteforce")
+    return out
+
+
+def bruteforce_pixels(f, theta, sigma, w, ys, xs):
+    f = np.ascontiguousarray(f, dtype=np.uint8)
+    H, W = f.shape
+    theta, sigma = _maps(theta, sigma)
+    ys = np.ascontiguousarray(ys, dtype=np.int32)
+    xs = np.ascontiguousarray(xs, dtype=np.int32)
+    out = np.zeros(len(ys), np.float64)
+    _check(_load().oracle_bruteforce_pixels(_ptr(f, C.c_uint8), _ptr(theta, C.c_float),
+                                            _ptr(sigma, C.c_float), H, W, W, w,
+                                            _ptr(ys, C.c_int32), _ptr(xs, C.c_int32),
+                                            len(ys), _ptr(out, C.c_double)),
+           "bruteforce_pixels")
+    return out
