@@ -1,0 +1,193 @@
+/*
+ * fabf.h -- C ABI of the GB300 implementation of fast adaptive bilateral
+ * filtering (R. G. Gavaskar and K. N. Chaudhury, "Fast Adaptive Bilateral
+ * Filtering").  Equation and section numbers below are the paper's.
+ *
+ * The operation (Sec. I-A, Eqs. (1)-(3)): for an 8-bit image f on the grid
+ * I, a per-pixel range-kernel centre theta(i) and width sigma(i), and a box
+ * spatial kernel omega == 1 on the window [-w, w]^2 clipped to the image,
+ *
+ *     g(i) = sum_j phi_i(f(i-j) - theta(i)) f(i-j) / sum_j phi_i(f(i-j) - theta(i)),
+ *     phi_i(t) = exp(-t^2 / (2 sigma(i)^2)).
+ *
+ * The library computes the paper's O(1) approximation g_hat of g
+ * (Algorithm 1, Eq. (29)): the local histogram on [alpha_i, beta_i] is
+ * replaced by the degree-N polynomial with the same first N+1 moments
+ * (Eqs. (14), (19), (24)) and the sums by integrals evaluated in closed form
+ * and by the integration-by-parts recursion (Eqs. (28), (30)-(32)).
+ *
+ * Conventions shared by every call:
+ *   - Every call returns a fabf_status; no exception or signal crosses the ABI.
+ *   - Layout: the image is H rows of W bytes, row r starting at img + r*pitch
+ *     (pitch >= W).  theta, sigma and out are dense H x W row-major arrays
+ *     (row stride W elements).  out is float64 when out_is_f64 != 0, else
+ *     float32.
+ *   - Pointers may be device pointers (cudaMalloc, or memory the CUDA driver
+ *     reports as device or managed) or ordinary host pointers; the kind is
+ *     detected per pointer.  The caller owns every buffer it passes.
+ *   - Limits: 1 <= H, W <= 65535, 1 <= w <= 40, 0 <= N <= 6.  N or w beyond
+ *     that returns FABF_EUNSUPPORTED (the int64 power sums are exact only up
+ *     to N = 6, w = 40); nothing falls back to the CPU.
+ *   - Per-pixel data errors (sigma <= 0 or not finite, theta not finite) give
+ *     NaN at that pixel and are reported as FABF_EINVAL: directly when the
+ *     call blocks, else by fabf_get_status().
+ *   - The library uses one GPU, selected by fabf_config.device; calls on a
+ *     context must not run concurrently from several host threads.
+ */
+#ifndef FABF_H
+#define FABF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fabf_ctx fabf_ctx;
+
+typedef enum {
+    FABF_OK = 0,
+    FABF_EINVAL = 1,        /* bad argument or bad per-pixel data */
+    FABF_ENOMEM = 2,        /* device or host allocation failed, or over budget */
+    FABF_EAGAIN = 3,        /* not finished yet (serving) */
+    FABF_EUNSUPPORTED = 4,  /* N or w outside the supported range */
+    FABF_ECUDA = 5,         /* a CUDA runtime or driver call failed */
+    FABF_ETIMEOUT = 6,      /* a bounded wait (host or device) gave up */
+    FABF_ENOTFOUND = 7      /* unknown serving ticket */
+} fabf_status;
+
+/* Arithmetic of the per-pixel stages (Sec. II-B, II-C).
+ *   FABF_FP64: everything after the exact integer stages in binary64.
+ *   FABF_FP64FIT_FP32REC: shift-scale and Hilbert fit in binary64, the
+ *     integrals, recursion and ratio in binary32.
+ *   FABF_CFP32: fit with compensated binary32 dot products, the rest in
+ *     binary32. */
+typedef enum { FABF_FP64 = 0, FABF_FP64FIT_FP32REC = 1, FABF_CFP32 = 2 } fabf_precision;
+
+typedef struct {
+    int device;                  /* CUDA device ordinal */
+    size_t mem_budget_bytes;     /* device bytes the serving loop may hold (0 = 16 GiB) */
+    int precision;               /* fabf_precision used by fabf_filter / batch / serve */
+    int autotune;                /* nonzero: pick tile shapes by measurement */
+    const char* tune_cache_path; /* optional file for autotuner results (may be NULL) */
+} fabf_config;
+
+/* One filtering request (batch and serving).  passes >= 1 applies the filter
+ * repeatedly (texture filtering, Sec. IV-C): pass p+1 takes as image the
+ * previous output rounded half-to-even and clamped to [0, 255], as centre
+ * theta_{p+1} = f_{p+1} + (theta - f), and as width sigma_p * sigma_decay. */
+typedef struct {
+    const uint8_t* img;
+    const float* theta;
+    const float* sigma;
+    int H, W;
+    size_t pitch;
+    int w;
+    int N;
+    int passes;
+    float sigma_decay;
+    void* out;
+    int out_is_f64;
+} fabf_request;
+
+/* Create a context on cfg->device (cfg may be NULL: device 0, FP64).
+ * On success *out owns a CUDA stream-independent context; release it with
+ * fabf_destroy.  Errors: FABF_EINVAL (out NULL, bad precision), FABF_ECUDA. */
+int fabf_create(const fabf_config* cfg, fabf_ctx** out);
+
+/* Release everything the context holds (waits for its own work first). */
+int fabf_destroy(fabf_ctx* ctx);
+
+/* Change the precision used by later calls on ctx (fabf_precision). */
+int fabf_set_precision(fabf_ctx* ctx, int precision);
+
+/* Algorithm 1 (Sec. II-D) on one image: out[i] = g_hat(i) of Eq. (29), with
+ * g_hat(i) = f(i) where alpha_i == beta_i.  cuda_stream is a cudaStream_t
+ * (NULL = legacy default stream).  If img, theta, sigma and out are all
+ * device pointers the work is only enqueued on the stream (stream-ordered,
+ * the call returns at once; per-pixel data errors are read later with
+ * fabf_get_status).  If any of them is a host pointer, the call stages the
+ * host buffers through device memory and returns after out is written.
+ * Errors: FABF_EINVAL, FABF_EUNSUPPORTED, FABF_ENOMEM, FABF_ECUDA,
+ * FABF_ETIMEOUT (a tile copy into shared memory did not complete). */
+int fabf_filter(fabf_ctx* ctx, const uint8_t* img, const float* theta, const float* sigma,
+                int H, int W, size_t pitch, int w, int N, void* out, int out_is_f64,
+                void* cuda_stream);
+
+/* Wait for cuda_stream, then report and clear the data errors of the
+ * stream-ordered calls made on ctx since the last query: *status receives
+ * FABF_OK, FABF_EINVAL or FABF_ETIMEOUT; *n_fallback (may be NULL) the number
+ * of pixels where the fitted approximation had a non-positive denominator
+ * and the sigma -> infinity limit (the box mean) was returned instead. */
+int fabf_get_status(fabf_ctx* ctx, void* cuda_stream, int* status, uint64_t* n_fallback);
+
+/* Filter n images of any sizes, w and N in one persistent launch replayed
+ * from a captured CUDA graph (tile shapes from the autotuner).  Pointers as
+ * in fabf_filter (device pointers stay stream-ordered).  passes must be 1.
+ * Errors as fabf_filter. */
+int fabf_filter_batch(fabf_ctx* ctx, const fabf_request* reqs, int n, void* cuda_stream);
+
+/* Serving: admit one request into the continuous-batching loop.  The inputs
+ * are copied at admission (caller buffers are free when the call returns);
+ * out must stay valid until fabf_serve_poll reports completion.  Errors:
+ * FABF_EINVAL, FABF_EUNSUPPORTED, FABF_ENOMEM (larger than the whole budget),
+ * FABF_EAGAIN (budget full right now: retry later). */
+int fabf_serve_submit(fabf_ctx* ctx, const fabf_request* req, uint64_t* ticket);
+
+/* Serving: wait up to timeout_us microseconds (0 = do not wait) for ticket.
+ * Returns FABF_OK and *result = the request's status once it is done,
+ * FABF_EAGAIN while it is pending, FABF_ENOTFOUND for an unknown or already
+ * collected ticket. */
+int fabf_serve_poll(fabf_ctx* ctx, uint64_t ticket, int timeout_us, int* result);
+
+/* Text of a fabf_status value (static storage). */
+const char* fabf_status_str(int status);
+
+/* ---- host-side helpers (no GPU needed) ---------------------------------- */
+
+/* The exact inverse of the (N+1) x (N+1) Hilbert matrix of Eq. (18), by the
+ * closed form of Eq. (19), row-major into out[(N+1)*(N+1)] -- the table the
+ * kernels use.  Errors: FABF_EINVAL (out NULL), FABF_EUNSUPPORTED (N > 6). */
+int fabf_hilbert_inverse(int N, int64_t* out);
+
+/* Dynamic shared memory (bytes) the fused kernel needs for (w, N). */
+int fabf_fused_smem_bytes(int w, int N, size_t* bytes);
+
+/* ---- test entry points (device pointers only, synchronous) -------------- */
+
+/* Every intermediate of Algorithm 1 from the fused kernel, one plane of
+ * H x W per quantity and index (planes stacked, row stride W):
+ *   alpha, beta: uint8 (Eq. (8));  m: (N+1) int64 planes, m_k of Eq. (17);
+ *   M: (N+1) int64 planes, M_k = sum (f - alpha)^k (numerator of Eq. (24));
+ *   mu, c: (N+1) float64 planes (Eq. (24), Eq. (19) times mu);
+ *   t0lam: 2 planes (t0, lambda of Eq. (25));  I: N+2 planes (Eq. (28),
+ *   scaled by exp(lambda d^2), d = distance from t0 to [0, 1]);
+ *   T: 2 planes (T1, T2 of Algorithm 1);  flags: int32 (bit0 flat, bit1 box
+ *   mean fallback);  out: float64 g_hat.  M, mu, c, t0lam, I, T are left
+ *   untouched at flat pixels.  Errors as fabf_filter. */
+int fabf_debug_stages(fabf_ctx* ctx, const uint8_t* img, const float* theta,
+                      const float* sigma, int H, int W, size_t pitch, int w, int N,
+                      uint8_t* alpha, uint8_t* beta, int64_t* m, int64_t* M, double* mu,
+                      double* c, double* t0lam, double* I, double* T, int32_t* flags,
+                      double* out);
+
+/* The integral engine alone: out[j*(K+1) + k] = I_k(lambda[j], t0[j]) for
+ * k = 0..K (Eq. (28), scaled by exp(lambda d^2)), 1 <= K <= 7, lambda > 0,
+ * in the given precision (FABF_FP64 or FABF_FP64FIT_FP32REC for binary32). */
+int fabf_debug_integrals(fabf_ctx* ctx, const double* lambda, const double* t0, int64_t n,
+                         int K, int precision, double* out);
+
+/* Brute-force adaptive bilateral filter, Eqs. (1)-(3), with the box kernel on
+ * the clipped window: the GPU comparator (O(w^2) per pixel).  use_f64
+ * selects binary64 or binary32 arithmetic.  Pointers and stream as in
+ * fabf_filter. */
+int fabf_bruteforce(fabf_ctx* ctx, const uint8_t* img, const float* theta, const float* sigma,
+                    int H, int W, size_t pitch, int w, void* out, int out_is_f64, int use_f64,
+                    void* cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FABF_H */

@@ -1,0 +1,426 @@
+// Host runtime behind the C ABI declared in include/fabf.h: argument checks,
+// pointer-kind detection and staging of host buffers, TMA descriptor
+// encoding, kernel dispatch over the polynomial degree N, and the status
+// words the kernels report into.  No CPU fallback exists: every pixel is
+// computed by the CUDA kernels.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+
+#include "../../include/fabf.h"
+#include "fabf_internal.h"
+#include "fabf_kernels.cuh"
+
+using namespace fabf;
+
+// ---------------------------------------------------------------------------
+// Small helpers
+// ---------------------------------------------------------------------------
+namespace fabf {
+
+int cuda_status(cudaError_t e)
+{
+    if (e == cudaSuccess) return FABF_OK;
+    if (e == cudaErrorMemoryAllocation) return FABF_ENOMEM;
+    return FABF_ECUDA;
+}
+
+bool is_device_ptr(const void* p)
+{
+    if (!p) return false;
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int check_filter_args(const void* img, const void* theta, const void* sigma, const void* out,
+                      int H, int W, size_t pitch, int w, int N)
+{
+    if (!img || !theta || !sigma || !out) return FABF_EINVAL;
+    if (H < 1 || W < 1 || H > 65535 || W > 65535) return FABF_EINVAL;
+    if (pitch < (size_t)W) return FABF_EINVAL;
+    if (w < 1 || N < 0) return FABF_EINVAL;
+    if (w > kWMax || N > kNMax) return FABF_EUNSUPPORTED;
+    return FABF_OK;
+}
+
+static PFN_cuTensorMapEncodeTiled_v12000 get_encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        else
+            (void)cudaGetLastError();
+    });
+    return fn;
+}
+
+// 2-D uint8 tensor map over the image, box Cb x R (inner x outer).
+bool encode_image_tmap(CUtensorMap* tm, const uint8_t* img, int H, int W, size_t pitch, int Cb, int R)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = get_encode_fn();
+    if (!enc) return false;
+    if ((reinterpret_cast<uintptr_t>(img) & 15) || (pitch & 15)) return false;
+    if (Cb > 256 || R > 256) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)W, (cuuint64_t)H};
+    cuuint64_t strides[1] = {(cuuint64_t)pitch};
+    cuuint32_t box[2] = {(cuuint32_t)Cb, (cuuint32_t)R};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<uint8_t*>(img), dims, strides,
+                     box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+void fused_geometry(int w, int* off, int* Cb)
+{
+    *off = (16 - (w & 15)) & 15;
+    *Cb = (*off + kTileW + 2 * w + 15) & ~15;
+}
+
+// ---- FP64 fused kernel dispatch ------------------------------------------
+template <int N>
+static cudaError_t launch_fused_n(const CUtensorMap& tm, const FusedParams& p, dim3 grid, size_t smem,
+                                  cudaStream_t s)
+{
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(fabf_fused_kernel<N>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 110 * 1024);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    fabf_fused_kernel<N><<<grid, kThreads, smem, s>>>(tm, p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fused_fp64(int N, const CUtensorMap& tm, const FusedParams& p, dim3 grid, size_t smem,
+                              cudaStream_t s)
+{
+    switch (N) {
+    case 0: return launch_fused_n<0>(tm, p, grid, smem, s);
+    case 1: return launch_fused_n<1>(tm, p, grid, smem, s);
+    case 2: return launch_fused_n<2>(tm, p, grid, smem, s);
+    case 3: return launch_fused_n<3>(tm, p, grid, smem, s);
+    case 4: return launch_fused_n<4>(tm, p, grid, smem, s);
+    case 5: return launch_fused_n<5>(tm, p, grid, smem, s);
+    case 6: return launch_fused_n<6>(tm, p, grid, smem, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace fabf
+
+// ---------------------------------------------------------------------------
+// Context
+// ---------------------------------------------------------------------------
+struct fabf_ctx {
+    int device = 0;
+    int precision = FABF_FP64;
+    size_t budget = 0;
+    int autotune = 0;
+    unsigned* d_status = nullptr;            // [0] status bits
+    unsigned long long* d_nfb = nullptr;     // fallback pixel count
+    void* stage = nullptr;                   // grow-only staging buffer for host pointers
+    size_t stage_bytes = 0;
+    fabf::ServeState* serve = nullptr;
+    fabf::BatchState* batch = nullptr;
+};
+
+namespace fabf {
+
+static int ensure_stage(fabf_ctx* ctx, size_t bytes)
+{
+    if (bytes <= ctx->stage_bytes) return FABF_OK;
+    if (ctx->stage) cudaFree(ctx->stage);
+    ctx->stage = nullptr;
+    ctx->stage_bytes = 0;
+    if (cudaMalloc(&ctx->stage, bytes) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return FABF_ENOMEM;
+    }
+    ctx->stage_bytes = bytes;
+    return FABF_OK;
+}
+
+static int read_and_clear_status(fabf_ctx* ctx, cudaStream_t s, int* status, uint64_t* nfb)
+{
+    unsigned st = 0;
+    unsigned long long n = 0;
+    cudaError_t e = cudaMemcpyAsync(&st, ctx->d_status, sizeof(st), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&n, ctx->d_nfb, sizeof(n), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_status, 0, sizeof(unsigned), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_nfb, 0, sizeof(unsigned long long), s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (status) *status = (st & kStatusTimeout) ? FABF_ETIMEOUT : (st & kStatusBadInput) ? FABF_EINVAL : FABF_OK;
+    if (nfb) *nfb = n;
+    return FABF_OK;
+}
+
+// Launch the fused kernel on device buffers.
+int run_fused(fabf_ctx* ctx, const uint8_t* img, size_t pitch, const float* theta, const float* sigma,
+              int H, int W, int w, int N, void* out, int out_f64, const DebugPlanes* dbg,
+              cudaStream_t s)
+{
+    if (ctx->precision != FABF_FP64) return FABF_EUNSUPPORTED;
+    FusedParams p;
+    std::memset(&p, 0, sizeof(p));
+    p.img = img;
+    p.pitch = (long long)pitch;
+    p.theta = theta;
+    p.sigma = sigma;
+    p.out = out;
+    p.H = H;
+    p.W = W;
+    p.w = w;
+    p.out_f64 = out_f64;
+    fused_geometry(w, &p.off, &p.Cb);
+    p.status = ctx->d_status;
+    p.n_fallback = ctx->d_nfb;
+    if (dbg) p.dbg = *dbg;
+    const int R = kTileH + 2 * w;
+    CUtensorMap tm;
+    std::memset(&tm, 0, sizeof(tm));
+    p.use_tma = encode_image_tmap(&tm, img, H, W, pitch, p.Cb, R) ? 1 : 0;
+    dim3 grid((W + kTileW - 1) / kTileW, (H + kTileH - 1) / kTileH);
+    const size_t smem = fused_smem_bytes(N, w, p.Cb);
+    return cuda_status(launch_fused_fp64(N, tm, p, grid, smem, s));
+}
+
+}  // namespace fabf
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+int fabf_create(const fabf_config* cfg, fabf_ctx** out)
+{
+    if (!out) return FABF_EINVAL;
+    *out = nullptr;
+    fabf_config c{};
+    if (cfg) c = *cfg;
+    if (c.precision < FABF_FP64 || c.precision > FABF_CFP32) return FABF_EINVAL;
+    fabf_ctx* ctx = new (std::nothrow) fabf_ctx();
+    if (!ctx) return FABF_ENOMEM;
+    ctx->device = c.device;
+    ctx->precision = c.precision;
+    ctx->budget = c.mem_budget_bytes ? c.mem_budget_bytes : (size_t)16 << 30;
+    ctx->autotune = c.autotune;
+    cudaError_t e = cudaSetDevice(c.device);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_status, 256);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_nfb, 256);
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_status, 0, 256);
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_nfb, 0, 256);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        if (ctx->d_status) cudaFree(ctx->d_status);
+        if (ctx->d_nfb) cudaFree(ctx->d_nfb);
+        delete ctx;
+        return cuda_status(e);
+    }
+    *out = ctx;
+    return FABF_OK;
+}
+
+int fabf_destroy(fabf_ctx* ctx)
+{
+    if (!ctx) return FABF_EINVAL;
+    cudaSetDevice(ctx->device);
+    fabf::serve_destroy(ctx->serve);
+    fabf::batch_destroy(ctx->batch);
+    cudaDeviceSynchronize();
+    if (ctx->stage) cudaFree(ctx->stage);
+    cudaFree(ctx->d_status);
+    cudaFree(ctx->d_nfb);
+    delete ctx;
+    return FABF_OK;
+}
+
+int fabf_set_precision(fabf_ctx* ctx, int precision)
+{
+    if (!ctx || precision < FABF_FP64 || precision > FABF_CFP32) return FABF_EINVAL;
+    ctx->precision = precision;
+    return FABF_OK;
+}
+
+int fabf_filter(fabf_ctx* ctx, const uint8_t* img, const float* theta, const float* sigma, int H, int W,
+                size_t pitch, int w, int N, void* out, int out_is_f64, void* cuda_stream)
+{
+    if (!ctx) return FABF_EINVAL;
+    int rc = check_filter_args(img, theta, sigma, out, H, W, pitch, w, N);
+    if (rc) return rc;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return FABF_ECUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    const bool di = is_device_ptr(img), dt = is_device_ptr(theta), ds = is_device_ptr(sigma),
+               dout = is_device_ptr(out);
+    const size_t npix = (size_t)H * W;
+    const size_t osz = out_is_f64 ? 8 : 4;
+    if (di && dt && ds && dout)
+        return run_fused(ctx, img, pitch, theta, sigma, H, W, w, N, out, out_is_f64, nullptr, s);
+
+    // Host buffers: stage through one device allocation (16-byte aligned parts).
+    const size_t ipitch = ((size_t)W + 15) & ~(size_t)15;
+    size_t o_img = 0, o_th = o_img + ((ipitch * H + 255) & ~(size_t)255);
+    size_t o_sg = o_th + ((npix * 4 + 255) & ~(size_t)255);
+    size_t o_out = o_sg + ((npix * 4 + 255) & ~(size_t)255);
+    size_t total = o_out + npix * osz;
+    rc = ensure_stage(ctx, total);
+    if (rc) return rc;
+    uint8_t* base = static_cast<uint8_t*>(ctx->stage);
+    const uint8_t* d_img = img;
+    size_t d_pitch = pitch;
+    const float* d_th = theta;
+    const float* d_sg = sigma;
+    void* d_out = out;
+    cudaError_t e = cudaSuccess;
+    if (!di) {
+        e = cudaMemcpy2DAsync(base + o_img, ipitch, img, pitch, W, H, cudaMemcpyHostToDevice, s);
+        d_img = base + o_img;
+        d_pitch = ipitch;
+    }
+    if (e == cudaSuccess && !dt) {
+        e = cudaMemcpyAsync(base + o_th, theta, npix * 4, cudaMemcpyHostToDevice, s);
+        d_th = reinterpret_cast<const float*>(base + o_th);
+    }
+    if (e == cudaSuccess && !ds) {
+        e = cudaMemcpyAsync(base + o_sg, sigma, npix * 4, cudaMemcpyHostToDevice, s);
+        d_sg = reinterpret_cast<const float*>(base + o_sg);
+    }
+    if (!dout) d_out = base + o_out;
+    if (e != cudaSuccess) return cuda_status(e);
+    rc = run_fused(ctx, d_img, d_pitch, d_th, d_sg, H, W, w, N, d_out, out_is_f64, nullptr, s);
+    if (rc) return rc;
+    if (!dout) {
+        e = cudaMemcpyAsync(out, d_out, npix * osz, cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    int st = FABF_OK;
+    rc = read_and_clear_status(ctx, s, &st, nullptr);
+    return rc ? rc : st;
+}
+
+int fabf_get_status(fabf_ctx* ctx, void* cuda_stream, int* status, uint64_t* n_fallback)
+{
+    if (!ctx || !status) return FABF_EINVAL;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return FABF_ECUDA;
+    return read_and_clear_status(ctx, static_cast<cudaStream_t>(cuda_stream), status, n_fallback);
+}
+
+const char* fabf_status_str(int status)
+{
+    switch (status) {
+    case FABF_OK: return "ok";
+    case FABF_EINVAL: return "invalid argument or per-pixel data";
+    case FABF_ENOMEM: return "out of memory or over the memory budget";
+    case FABF_EAGAIN: return "not ready, try again";
+    case FABF_EUNSUPPORTED: return "unsupported parameters (N > 6 or w > 40)";
+    case FABF_ECUDA: return "CUDA error";
+    case FABF_ETIMEOUT: return "bounded wait timed out";
+    case FABF_ENOTFOUND: return "unknown ticket";
+    default: return "unknown status";
+    }
+}
+
+int fabf_hilbert_inverse(int N, int64_t* out)
+{
+    if (!out) return FABF_EINVAL;
+    if (N < 0) return FABF_EINVAL;
+    if (N > kNMax) return FABF_EUNSUPPORTED;
+    for (int m = 1; m <= N + 1; ++m)
+        for (int n = 1; n <= N + 1; ++n) out[(m - 1) * (N + 1) + (n - 1)] = hilbert_inverse_entry(N, m, n);
+    return FABF_OK;
+}
+
+int fabf_fused_smem_bytes(int w, int N, size_t* bytes)
+{
+    if (!bytes || w < 1 || N < 0) return FABF_EINVAL;
+    if (w > kWMax || N > kNMax) return FABF_EUNSUPPORTED;
+    int off, Cb;
+    fused_geometry(w, &off, &Cb);
+    *bytes = fused_smem_bytes(N, w, Cb);
+    return FABF_OK;
+}
+
+int fabf_debug_stages(fabf_ctx* ctx, const uint8_t* img, const float* theta, const float* sigma, int H,
+                      int W, size_t pitch, int w, int N, uint8_t* alpha, uint8_t* beta, int64_t* m,
+                      int64_t* M, double* mu, double* c, double* t0lam, double* I, double* T,
+                      int32_t* flags, double* out)
+{
+    if (!ctx) return FABF_EINVAL;
+    int rc = check_filter_args(img, theta, sigma, out, H, W, pitch, w, N);
+    if (rc) return rc;
+    if (!alpha || !beta || !m || !M || !mu || !c || !t0lam || !I || !T || !flags) return FABF_EINVAL;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return FABF_ECUDA;
+    DebugPlanes d{alpha, beta, m, M, mu, c, t0lam, I, T, flags};
+    const int saved = ctx->precision;
+    ctx->precision = FABF_FP64;
+    rc = run_fused(ctx, img, pitch, theta, sigma, H, W, w, N, out, 1, &d, 0);
+    ctx->precision = saved;
+    if (rc) return rc;
+    int st = FABF_OK;
+    rc = read_and_clear_status(ctx, 0, &st, nullptr);
+    return rc ? rc : st;
+}
+
+int fabf_debug_integrals(fabf_ctx* ctx, const double* lambda, const double* t0, int64_t n, int K,
+                         int precision, double* out)
+{
+    if (!ctx || !lambda || !t0 || !out || n < 0 || K < 1 || K > 7) return FABF_EINVAL;
+    if (precision != FABF_FP64) return FABF_EUNSUPPORTED;
+    if (n == 0) return FABF_OK;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return FABF_ECUDA;
+    const int threads = 128;
+    const unsigned blocks = (unsigned)((n + threads - 1) / threads);
+    switch (K) {
+    case 1: integrals_kernel<1><<<blocks, threads>>>(lambda, t0, n, out); break;
+    case 2: integrals_kernel<2><<<blocks, threads>>>(lambda, t0, n, out); break;
+    case 3: integrals_kernel<3><<<blocks, threads>>>(lambda, t0, n, out); break;
+    case 4: integrals_kernel<4><<<blocks, threads>>>(lambda, t0, n, out); break;
+    case 5: integrals_kernel<5><<<blocks, threads>>>(lambda, t0, n, out); break;
+    case 6: integrals_kernel<6><<<blocks, threads>>>(lambda, t0, n, out); break;
+    default: integrals_kernel<7><<<blocks, threads>>>(lambda, t0, n, out); break;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    return cuda_status(e);
+}
+
+int fabf_bruteforce(fabf_ctx* ctx, const uint8_t* img, const float* theta, const float* sigma, int H, int W,
+                    size_t pitch, int w, void* out, int out_is_f64, int use_f64, void* cuda_stream)
+{
+    if (!ctx) return FABF_EINVAL;
+    int rc = check_filter_args(img, theta, sigma, out, H, W, pitch, w, 0);
+    if (rc) return rc;
+    if (!is_device_ptr(img) || !is_device_ptr(theta) || !is_device_ptr(sigma) || !is_device_ptr(out))
+        return FABF_EINVAL;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return FABF_ECUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    dim3 grid((W + 31) / 32, (H + 7) / 8);
+    if (use_f64)
+        bruteforce_kernel<double><<<grid, 256, 0, s>>>(img, (long long)pitch, theta, sigma, H, W, w, out,
+                                                       out_is_f64);
+    else
+        bruteforce_kernel<float><<<grid, 256, 0, s>>>(img, (long long)pitch, theta, sigma, H, W, w, out,
+                                                      out_is_f64);
+    return cuda_status(cudaGetLastError());
+}
+
+}  // extern "C"

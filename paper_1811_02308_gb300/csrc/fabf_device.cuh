@@ -1,0 +1,247 @@
+// Per-pixel device mathematics of fast adaptive bilateral filtering
+// (Gavaskar & Chaudhury), Algorithm 1 of Sec. II-D, for one pixel whose
+// window statistics (alpha, beta, m_0..m_N) are already known.
+//
+// Equation numbers are the paper's.  The integer stages are exact; the
+// FP64 fit reproduces the oracle's rounding step for step (same operations in
+// the same order), and the integrals are evaluated by a hybrid of the paper's
+// forward recursion (Eq. 30) and the same recursion run downwards, which is
+// the numerically stable direction when lambda is small.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace fabf {
+
+constexpr int kNMax = 6;    // int64 power sums are exact for N <= 6, w <= 40
+constexpr int kWMax = 40;
+
+// Status bits a kernel ORs into its status word.
+constexpr unsigned kStatusBadInput = 1u;    // sigma <= 0 / non-finite, theta non-finite
+constexpr unsigned kStatusTimeout = 2u;     // a bounded device wait gave up
+
+// ---------------------------------------------------------------------------
+// Hilbert inverse, Eq. (19), as exact integers (max |entry| 133,402,500 at
+// N = 6, exactly representable in binary64).
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr long long binom_c(int n, int k)
+{
+    if (k < 0 || k > n) return 0;
+    long long r = 1;
+    for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
+    return r;
+}
+
+// (A^{-1})_{m,n} with the paper's 1-based indices.
+__host__ __device__ constexpr long long hilbert_inverse_entry(int N, int m, int n)
+{
+    const long long b = binom_c(m + n - 2, m - 1);
+    return (((m + n) & 1) ? -1LL : 1LL) * (long long)(m + n - 1) * binom_c(N + m, N + 1 - n) *
+           binom_c(N + n, N + 1 - m) * b * b;
+}
+
+struct AinvTable {
+    double v[kNMax + 1][kNMax + 1][kNMax + 1];   // [N][n][k], 0-based
+};
+
+__host__ __device__ constexpr AinvTable make_ainv_table()
+{
+    AinvTable t{};
+    for (int N = 0; N <= kNMax; ++N)
+        for (int n = 0; n <= N; ++n)
+            for (int k = 0; k <= N; ++k)
+                t.v[N][n][k] = (double)hilbert_inverse_entry(N, n + 1, k + 1);
+    return t;
+}
+
+struct RecipTable {
+    double v[64];   // v[j] = 1 / j (v[0] unused)
+};
+
+__host__ __device__ constexpr RecipTable make_recip_table()
+{
+    RecipTable t{};
+    for (int j = 1; j < 64; ++j) t.v[j] = 1.0 / (double)j;
+    return t;
+}
+
+// Both tables are built at compile time; each translation unit that includes
+// this header holds its own copy in constant memory.
+static __constant__ AinvTable c_ainv = make_ainv_table();
+static __constant__ RecipTable c_recip = make_recip_table();
+
+// ---------------------------------------------------------------------------
+// Integrals I_k = int_0^1 t^k exp(-lambda (t - t0)^2) dt, Eq. (28), k = 0..K,
+// each multiplied by exp(lambda d^2) with d the distance from t0 to [0, 1].
+// That factor is common to numerator and denominator of Eq. (29) and keeps
+// every value representable however far the range-kernel centre lies from
+// [alpha, beta].
+//
+//  lambda >= 1: Eq. (31) for I_0 (erf; scaled erfc when t0 is outside
+//               [0, 1]), Eq. (32) for I_1, Eq. (30) forward for I_2..I_K.
+//  lambda <  1: Eq. (30) solved for I_{k-2} and run downwards from a start
+//               index Kp >= K + 1 (chosen from lambda, made warp-uniform)
+//               with the start values I_k ~ E_1 / (k + 1 + 2 lambda (t0-1))
+//               (mass of t^k near t = 1).  The recursion's own error
+//               amplification is below one in that direction, so the start
+//               error dies out and no erf is needed.
+// ---------------------------------------------------------------------------
+constexpr double kLambdaForward = 1.0;
+
+__device__ __forceinline__ int backward_start_index(double lam)
+{
+    return lam <= 0.1 ? 24 : (lam <= 0.3 ? 32 : (lam <= 0.7 ? 40 : 48));
+}
+
+template <int K>
+__device__ __forceinline__ void integrals_fp64(double lam, double t0, double (&I)[K + 1])
+{
+    static_assert(K >= 1 && K <= 7, "K out of range");
+    const double inv2l = 0.5 / lam;
+    if (lam >= kLambdaForward) {
+        const double rl = rsqrt(lam);
+        const double sl = lam * rl;                               // sqrt(lambda)
+        const double h = 0.88622692545275801364908374167057 * rl; // 1/2 sqrt(pi/lambda)
+        double E0s, E1s, I0;
+        if (t0 < 0.0) {
+            E0s = 1.0;
+            E1s = exp(lam * (2.0 * t0 - 1.0));
+            I0 = h * (erfcx(-sl * t0) - E1s * erfcx(sl * (1.0 - t0)));
+        } else if (t0 > 1.0) {
+            E1s = 1.0;
+            E0s = exp(lam * (1.0 - 2.0 * t0));
+            I0 = h * (erfcx(sl * (t0 - 1.0)) - E0s * erfcx(sl * t0));
+        } else {
+            E0s = exp(-lam * t0 * t0);
+            E1s = exp(-lam * (1.0 - t0) * (1.0 - t0));
+            I0 = h * (erf(sl * (1.0 - t0)) + erf(sl * t0));
+        }
+        const double e1 = E1s * inv2l;
+        I[0] = I0;
+        I[1] = fma(t0, I0, (E0s - E1s) * inv2l);
+#pragma unroll
+        for (int k = 2; k <= K; ++k) I[k] = fma(t0, I[k - 1], fma((double)(k - 1) * inv2l, I[k - 2], -e1));
+    } else {
+        double E1s;
+        if (t0 < 0.0) E1s = exp(lam * (2.0 * t0 - 1.0));
+        else if (t0 > 1.0) E1s = 1.0;
+        else E1s = exp(-lam * (1.0 - t0) * (1.0 - t0));
+        int Kp = backward_start_index(lam);
+        Kp = __reduce_max_sync(__activemask(), (unsigned)Kp);
+        const double l2 = 2.0 * lam;
+        const double q = l2 * (t0 - 1.0);
+        double r1 = (double)(Kp + 2) + q, r0 = (double)(Kp + 1) + q;
+        double hi = E1s / (r1 > 1.0 ? r1 : (double)(Kp + 2));    // I_{Kp+1}
+        double lo = E1s / (r0 > 1.0 ? r0 : (double)(Kp + 1));    // I_{Kp}
+        // (hi, lo) = (I_k, I_{k-1}); produce I_{k-2} for k = Kp+1 .. K+2.
+        for (int k = Kp + 1; k >= K + 2; --k) {
+            const double nx = fma(l2, fma(-t0, lo, hi), E1s) * c_recip.v[k - 1];
+            hi = lo;
+            lo = nx;
+        }
+        I[K] = lo;
+        const double top = hi;   // I_{K+1}, used by the first tail step only
+#pragma unroll
+        for (int k = K + 1; k >= 2; --k) {
+            const double Ik = (k == K + 1) ? top : I[k];
+            I[k - 2] = fma(l2, fma(-t0, I[k - 1], Ik), E1s) * (1.0 / (double)(k - 1));
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// One pixel of Algorithm 1 in FP64.  m[0] is the window size, m[k] the
+// window sum of f^k (exact, k = 0..max(N,1)).  Returns g_hat(i).
+// ---------------------------------------------------------------------------
+struct PixelTrace {       // optional per-pixel export of every stage
+    int64_t M[kNMax + 1];
+    double mu[kNMax + 1];
+    double c[kNMax + 1];
+    double t0, lam;
+    double I[kNMax + 2];
+    double T1, T2;
+    int fallback;
+};
+
+template <int N>
+__device__ __forceinline__ double fabf_pixel_fp64(const AinvTable& A, int alpha, int beta, int fi,
+                                                  const int64_t (&m)[(N < 1 ? 1 : N) + 1],
+                                                  float theta_f, float sigma_f, int& fallback,
+                                                  PixelTrace* tr)
+{
+    constexpr int K = N < 1 ? 1 : N;   // mu_1 is needed by the fallback even for N = 0
+    fallback = 0;
+    if (alpha == beta) return (double)fi;   // flat window: g(i) = f(i), Sec. II-A
+    const int d = beta - alpha;
+
+    // Eq. (24) in exact integers: M_b = sum_window (f - alpha)^b from the
+    // power sums via S(a, b) = S(a+1, b-1) - alpha S(a, b-1), where
+    // S(a, b) = sum f^a (f - alpha)^b.  Every S and every product stays in
+    // [0, m_0 255^6] < 2^63 for N <= 6, w <= 40, so nothing overflows.
+    int64_t s[K + 1], M[K + 1];
+#pragma unroll
+    for (int a = 0; a <= K; ++a) s[a] = m[a];
+    M[0] = s[0];
+#pragma unroll
+    for (int b = 1; b <= K; ++b) {
+#pragma unroll
+        for (int a = 0; a <= K - b; ++a) s[a] = s[a + 1] - (int64_t)alpha * s[a];
+        M[b] = s[0];
+    }
+    // mu_k = M_k / (beta - alpha)^k: one correctly rounded division of two
+    // binary64 values ((beta - alpha)^k <= 255^6 is exact).
+    double mu[K + 1];
+    int64_t dk = 1;
+#pragma unroll
+    for (int k = 0; k <= K; ++k) {
+        mu[k] = (double)M[k] / (double)dk;
+        dk *= d;
+    }
+    // c = A^{-1} mu, Eq. (19) and Algorithm 1, fused multiply-adds over
+    // ascending k starting from zero.
+    double c[N + 1];
+#pragma unroll
+    for (int n = 0; n <= N; ++n) {
+        double acc = 0.0;
+#pragma unroll
+        for (int k = 0; k <= N; ++k) acc = fma(A.v[N][n][k], mu[k], acc);
+        c[n] = acc;
+    }
+    // Eq. (25) and Algorithm 1.
+    const double sg = (double)sigma_f;
+    const double t0 = ((double)theta_f - (double)alpha) / (double)d;
+    const double lam = (double)(d * d) / (2.0 * sg * sg);
+    double I[N + 2];
+    integrals_fp64<N + 1>(lam, t0, I);
+    // Eq. (29), accumulated in the order of Algorithm 1.
+    double T1 = c[0] * I[1], T2 = c[0] * I[0];
+#pragma unroll
+    for (int k = 2; k <= N + 1; ++k) {
+        T1 = fma(c[k - 1], I[k], T1);
+        T2 = fma(c[k - 1], I[k - 1], T2);
+    }
+    double F = T1 / T2;
+    if (!(T2 > 0.0) || !isfinite(F)) {   // fitted polynomial not positive enough
+        F = mu[1] / mu[0];                // sigma -> infinity limit (box mean)
+        fallback = 1;
+    }
+    if (tr) {
+#pragma unroll
+        for (int k = 0; k <= N; ++k) {
+            tr->M[k] = M[k];
+            tr->mu[k] = mu[k];
+            tr->c[k] = c[k];
+        }
+#pragma unroll
+        for (int k = 0; k <= N + 1; ++k) tr->I[k] = I[k];
+        tr->t0 = t0;
+        tr->lam = lam;
+        tr->T1 = T1;
+        tr->T2 = T2;
+        tr->fallback = fallback;
+    }
+    return (double)alpha + (double)d * F;
+}
+
+}  // namespace fabf

@@ -1,0 +1,295 @@
+"""Thin Python binding of ``libfabf.so`` (include/fabf.h): ctypes argument
+marshalling only.  Every step of the filter runs in the CUDA kernels; if the
+library is missing or cannot be loaded this module raises -- there is no CPU
+fallback.
+
+Arrays may be torch tensors (CUDA or CPU) or numpy arrays; CUDA tensors are
+passed to the library as device pointers, everything else as host pointers.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+FABF_OK = 0
+FABF_EINVAL = 1
+FABF_ENOMEM = 2
+FABF_EAGAIN = 3
+FABF_EUNSUPPORTED = 4
+FABF_ECUDA = 5
+FABF_ETIMEOUT = 6
+FABF_ENOTFOUND = 7
+
+FABF_FP64 = 0
+FABF_FP64FIT_FP32REC = 1
+FABF_CFP32 = 2
+
+_lib = None
+
+
+class FabfError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__("%s failed: %s (status %d)" % (what, status_str(status), status))
+
+
+class _Config(C.Structure):
+    _fields_ = [("device", C.c_int), ("mem_budget_bytes", C.c_size_t), ("precision", C.c_int),
+                ("autotune", C.c_int), ("tune_cache_path", C.c_char_p)]
+
+
+class Request(C.Structure):
+    """``fabf_request`` of include/fabf.h."""
+    _fields_ = [("img", C.c_void_p), ("theta", C.c_void_p), ("sigma", C.c_void_p),
+                ("H", C.c_int), ("W", C.c_int), ("pitch", C.c_size_t), ("w", C.c_int),
+                ("N", C.c_int), ("passes", C.c_int), ("sigma_decay", C.c_float),
+                ("out", C.c_void_p), ("out_is_f64", C.c_int)]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None):
+    """Load libfabf.so (raises if it is missing: build it with build.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError("libfabf.so not found at %s: run paper_1811_02308_gb300.build.build() "
+                           "(the CUDA library is required; there is no CPU fallback)" % path)
+    lib = C.CDLL(path)
+    vp, i, sz = C.c_void_p, C.c_int, C.c_size_t
+    sig = {
+        "fabf_create": ([C.POINTER(_Config), C.POINTER(vp)], i),
+        "fabf_destroy": ([vp], i),
+        "fabf_set_precision": ([vp, i], i),
+        "fabf_filter": ([vp, vp, vp, vp, i, i, sz, i, i, vp, i, vp], i),
+        "fabf_get_status": ([vp, vp, C.POINTER(i), C.POINTER(C.c_uint64)], i),
+        "fabf_filter_batch": ([vp, C.POINTER(Request), i, vp], i),
+        "fabf_serve_submit": ([vp, C.POINTER(Request), C.POINTER(C.c_uint64)], i),
+        "fabf_serve_poll": ([vp, C.c_uint64, i, C.POINTER(i)], i),
+        "fabf_status_str": ([i], C.c_char_p),
+        "fabf_hilbert_inverse": ([i, vp], i),
+        "fabf_fused_smem_bytes": ([i, i, C.POINTER(sz)], i),
+        "fabf_debug_stages": ([vp, vp, vp, vp, i, i, sz, i, i] + [vp] * 11, i),
+        "fabf_debug_integrals": ([vp, vp, vp, C.c_int64, i, i, vp], i),
+        "fabf_bruteforce": ([vp, vp, vp, vp, i, i, sz, i, vp, i, i, vp], i),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def status_str(status: int) -> str:
+    try:
+        return load().fabf_status_str(int(status)).decode()
+    except Exception:   # noqa: BLE001 - only used to format messages
+        return "status %d" % status
+
+
+def _check(rc: int, what: str) -> None:
+    if rc != FABF_OK:
+        raise FabfError(rc, what)
+
+
+# ---------------------------------------------------------------------------
+# marshalling helpers
+# ---------------------------------------------------------------------------
+def _is_torch(a) -> bool:
+    return type(a).__module__.startswith("torch")
+
+
+def _ptr(a) -> int:
+    if a is None:
+        return 0
+    if _is_torch(a):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    raise TypeError("expected a torch tensor or numpy array, got %r" % type(a))
+
+
+def _stream_of(*arrays) -> int:
+    for a in arrays:
+        if _is_torch(a) and a.is_cuda:
+            import torch
+            return torch.cuda.current_stream(a.device).cuda_stream
+    return 0
+
+
+def _empty_like_out(ref, H, W, f64):
+    if _is_torch(ref):
+        import torch
+        return torch.empty((H, W), dtype=torch.float64 if f64 else torch.float32, device=ref.device)
+    return np.empty((H, W), dtype=np.float64 if f64 else np.float32)
+
+
+class Context:
+    """``fabf_ctx``: one GPU, one default precision."""
+
+    def __init__(self, device: int = 0, precision: int = FABF_FP64, mem_budget_bytes: int = 0,
+                 autotune: int = 0, tune_cache_path: str | None = None):
+        lib = load()
+        cfg = _Config(device, mem_budget_bytes, precision, autotune,
+                      tune_cache_path.encode() if tune_cache_path else None)
+        h = C.c_void_p()
+        _check(lib.fabf_create(C.byref(cfg), C.byref(h)), "fabf_create")
+        self._h = h
+        self.device = device
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().fabf_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:   # noqa: BLE001 - interpreter shutdown
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def fabf_set_precision(ctx: Context, precision: int) -> None:
+    _check(load().fabf_set_precision(ctx.handle, int(precision)), "fabf_set_precision")
+
+
+def fabf_filter(ctx: Context, img, theta, sigma, w: int, N: int, out=None, out_is_f64: bool = True,
+                pitch: int | None = None, stream: int | None = None, check: bool = True):
+    """Algorithm 1 on one image (``fabf_filter``); returns ``out``.
+
+    ``img`` is (H, W) uint8, or (H, pitch) with ``pitch`` given and the image
+    in its first W columns (then pass W via theta's shape).
+    """
+    H, W = int(theta.shape[0]), int(theta.shape[1])
+    p = int(pitch) if pitch is not None else int(img.shape[1])
+    if out is None:
+        out = _empty_like_out(theta, H, W, out_is_f64)
+    s = _stream_of(img, theta, sigma, out) if stream is None else stream
+    rc = load().fabf_filter(ctx.handle, _ptr(img), _ptr(theta), _ptr(sigma), H, W, p, int(w), int(N),
+                            _ptr(out), 1 if out_is_f64 else 0, s)
+    if check:
+        _check(rc, "fabf_filter")
+        return out
+    return out, rc
+
+
+def fabf_get_status(ctx: Context, stream: int = 0):
+    """(status, n_fallback) of the stream-ordered calls since the last query."""
+    st = C.c_int(0)
+    nf = C.c_uint64(0)
+    _check(load().fabf_get_status(ctx.handle, stream, C.byref(st), C.byref(nf)), "fabf_get_status")
+    return st.value, nf.value
+
+
+def fabf_hilbert_inverse(N: int) -> np.ndarray:
+    out = np.zeros((N + 1, N + 1), dtype=np.int64)
+    _check(load().fabf_hilbert_inverse(int(N), out.ctypes.data), "fabf_hilbert_inverse")
+    return out
+
+
+def fabf_fused_smem_bytes(w: int, N: int) -> int:
+    b = C.c_size_t(0)
+    _check(load().fabf_fused_smem_bytes(int(w), int(N), C.byref(b)), "fabf_fused_smem_bytes")
+    return b.value
+
+
+def fabf_debug_stages(ctx: Context, img, theta, sigma, w: int, N: int):
+    """Every intermediate of Algorithm 1 (device tensors in, dict of tensors out)."""
+    import torch
+    H, W = int(theta.shape[0]), int(theta.shape[1])
+    dev = theta.device
+    o = dict(
+        alpha=torch.zeros((H, W), dtype=torch.uint8, device=dev),
+        beta=torch.zeros((H, W), dtype=torch.uint8, device=dev),
+        m=torch.zeros((N + 1, H, W), dtype=torch.int64, device=dev),
+        M=torch.zeros((N + 1, H, W), dtype=torch.int64, device=dev),
+        mu=torch.full((N + 1, H, W), float("nan"), dtype=torch.float64, device=dev),
+        c=torch.full((N + 1, H, W), float("nan"), dtype=torch.float64, device=dev),
+        t0lam=torch.full((2, H, W), float("nan"), dtype=torch.float64, device=dev),
+        I=torch.full((N + 2, H, W), float("nan"), dtype=torch.float64, device=dev),
+        T=torch.full((2, H, W), float("nan"), dtype=torch.float64, device=dev),
+        flags=torch.zeros((H, W), dtype=torch.int32, device=dev),
+        out=torch.zeros((H, W), dtype=torch.float64, device=dev),
+    )
+    rc = load().fabf_debug_stages(ctx.handle, _ptr(img), _ptr(theta), _ptr(sigma), H, W,
+                                  int(img.shape[1]), int(w), int(N),
+                                  *[_ptr(o[k]) for k in ("alpha", "beta", "m", "M", "mu", "c",
+                                                         "t0lam", "I", "T", "flags", "out")])
+    _check(rc, "fabf_debug_stages")
+    return o
+
+
+def fabf_debug_integrals(ctx: Context, lam, t0, K: int, precision: int = FABF_FP64):
+    """I_0..I_K for device float64 tensors lam, t0 -> (n, K+1) float64 tensor."""
+    import torch
+    n = int(lam.numel())
+    out = torch.empty((n, K + 1), dtype=torch.float64, device=lam.device)
+    _check(load().fabf_debug_integrals(ctx.handle, _ptr(lam), _ptr(t0), n, int(K), int(precision),
+                                       _ptr(out)), "fabf_debug_integrals")
+    return out
+
+
+def fabf_bruteforce(ctx: Context, img, theta, sigma, w: int, out=None, out_is_f64: bool = True,
+                    use_f64: bool = True, stream: int | None = None):
+    """Brute-force adaptive bilateral filter on the GPU (device tensors)."""
+    H, W = int(theta.shape[0]), int(theta.shape[1])
+    if out is None:
+        out = _empty_like_out(theta, H, W, out_is_f64)
+    s = _stream_of(img, theta, sigma, out) if stream is None else stream
+    _check(load().fabf_bruteforce(ctx.handle, _ptr(img), _ptr(theta), _ptr(sigma), H, W,
+                                  int(img.shape[1]), int(w), _ptr(out), 1 if out_is_f64 else 0,
+                                  1 if use_f64 else 0, s), "fabf_bruteforce")
+    return out
+
+
+def make_request(img, theta, sigma, w: int, N: int, out, out_is_f64: bool = True, passes: int = 1,
+                 sigma_decay: float = 0.8, pitch: int | None = None) -> Request:
+    H, W = int(theta.shape[0]), int(theta.shape[1])
+    return Request(_ptr(img), _ptr(theta), _ptr(sigma), H, W,
+                   int(pitch) if pitch is not None else int(img.shape[1]), int(w), int(N),
+                   int(passes), float(sigma_decay), _ptr(out), 1 if out_is_f64 else 0)
+
+
+def fabf_filter_batch(ctx: Context, reqs, stream: int = 0) -> None:
+    arr = (Request * len(reqs))(*reqs)
+    _check(load().fabf_filter_batch(ctx.handle, arr, len(reqs), stream), "fabf_filter_batch")
+
+
+def fabf_serve_submit(ctx: Context, req: Request, check: bool = True):
+    t = C.c_uint64(0)
+    rc = load().fabf_serve_submit(ctx.handle, C.byref(req), C.byref(t))
+    if check:
+        _check(rc, "fabf_serve_submit")
+        return t.value
+    return rc, t.value
+
+
+def fabf_serve_poll(ctx: Context, ticket: int, timeout_us: int = 0):
+    """(rc, result): rc FABF_OK when done (result = the request's status),
+    FABF_EAGAIN while pending, FABF_ENOTFOUND for an unknown ticket."""
+    r = C.c_int(0)
+    rc = load().fabf_serve_poll(ctx.handle, C.c_uint64(ticket), int(timeout_us), C.byref(r))
+    return rc, r.value

@@ -1,0 +1,74 @@
+"""The C-ABI library builds, loads and exports every symbol include/fabf.h
+declares; host-side logic that needs no GPU (no compute calls here)."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+import scipy.linalg
+
+from paper_1811_02308_gb300 import build, fabf
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return fabf.load()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "fabf.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(fabf_\w+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary_calls():
+    names = declared_functions()
+    for n in ("fabf_create", "fabf_destroy", "fabf_filter", "fabf_filter_batch",
+              "fabf_serve_submit", "fabf_serve_poll", "fabf_status_str"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_library_is_built_for_sm_103a():
+    # the build passes exactly one -gencode for sm_103a
+    assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+@pytest.mark.parametrize("N", range(7))
+def test_kernel_hilbert_table_is_exact(lib, N):
+    got = fabf.fabf_hilbert_inverse(N)
+    ref = scipy.linalg.invhilbert(N + 1, exact=True)
+    assert got.tolist() == [[int(v) for v in row] for row in ref]
+
+
+def test_argument_checks_without_gpu(lib):
+    null = C.c_void_p(0)
+    assert lib.fabf_filter(null, 0, 0, 0, 4, 4, 4, 1, 1, 0, 1, 0) == fabf.FABF_EINVAL
+    out = np.zeros(64, np.int64)
+    assert lib.fabf_hilbert_inverse(7, out.ctypes.data) == fabf.FABF_EUNSUPPORTED
+    assert lib.fabf_hilbert_inverse(3, None) == fabf.FABF_EINVAL
+    b = C.c_size_t(0)
+    assert lib.fabf_fused_smem_bytes(41, 5, C.byref(b)) == fabf.FABF_EUNSUPPORTED
+    assert lib.fabf_fused_smem_bytes(5, 7, C.byref(b)) == fabf.FABF_EUNSUPPORTED
+    assert lib.fabf_fused_smem_bytes(0, 5, C.byref(b)) == fabf.FABF_EINVAL
+    assert lib.fabf_create(None, None) == fabf.FABF_EINVAL
+
+
+def test_shared_memory_fits_two_ctas_per_sm(lib):
+    # 227 KB per SM: two resident CTAs need <= 113 KB each, for every (w, N)
+    worst = max(fabf.fabf_fused_smem_bytes(w, N) for w in range(1, 41) for N in range(7))
+    assert worst <= 113 * 1024
+
+
+def test_status_strings(lib):
+    for s in range(8):
+        assert fabf.status_str(s)
+    assert "unknown" in fabf.status_str(99)
