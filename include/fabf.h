@@ -144,6 +144,32 @@ int fabf_serve_poll(fabf_ctx* ctx, uint64_t ticket, int timeout_us, int* result)
 /* Text of a fabf_status value (static storage). */
 const char* fabf_status_str(int status);
 
+/* Allocation-free variant of fabf_filter (the paper has no counterpart).
+ * For callers that must not allocate device memory -- a real-time thread
+ * that cannot absorb cudaMalloc's device-wide synchronisation, a plugin
+ * whose host framework owns every allocation, a thread in the middle of a
+ * stream capture -- and therefore cannot create a context.  It runs the same
+ * FP64 fused kernel as fabf_filter on the caller's device buffers and needs
+ * no context; the kernel's scratch (its status word and fallback-pixel
+ * counter, 16 bytes) lives in a 256-byte array compiled into the library,
+ * which every GPU that loads the library holds until the process exits.
+ *   - img, theta, sigma, out must be device pointers (FABF_EINVAL otherwise:
+ *     host buffers would need device staging).  Layout, limits and the other
+ *     errors as fabf_filter; the GPU is the calling thread's current device.
+ *   - The first call on a device looks up the array's device address (once
+ *     per device); make that first call before any stream capture.
+ *   - The call clears the scratch, enqueues the kernel on cuda_stream, then
+ *     waits for the stream and returns FABF_OK, FABF_EINVAL (bad per-pixel
+ *     data) or FABF_ETIMEOUT; *n_fallback (may be NULL) receives the number
+ *     of pixels that took the box-mean fallback.
+ *   - All calls share the one array: calls whose work overlaps on the GPU
+ *     (other streams, other host threads) race on it and may report each
+ *     other's status.  It calls no cudaMalloc, cudaFree or allocating
+ *     library routine. */
+int fabf_filter_noalloc(const uint8_t* img, const float* theta, const float* sigma, int H, int W,
+                        size_t pitch, int w, int N, void* out, int out_is_f64, void* cuda_stream,
+                        uint64_t* n_fallback);
+
 /* ---- host-side helpers (no GPU needed) ---------------------------------- */
 
 /* The exact inverse of the (N+1) x (N+1) Hilbert matrix of Eq. (18), by the

@@ -16,6 +16,7 @@ LIB = os.path.join(HERE, "libfabf.so")
 SOURCES = [
     "fabf_api.cu",
     "fabf_batch_serve.cu",
+    "fabf_noalloc.cu",
 ]
 HEADERS = ["fabf_device.cuh", "fabf_kernels.cuh", "fabf_internal.h"]
 

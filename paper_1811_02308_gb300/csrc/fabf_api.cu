@@ -204,6 +204,35 @@ int run_fused(fabf_ctx* ctx, const uint8_t* img, size_t pitch, const float* thet
     return cuda_status(launch_fused_fp64(N, tm, p, grid, smem, s));
 }
 
+// Launch the fused FP64 kernel on device buffers with caller-provided status
+// words (used by the allocation-free entry point in fabf_noalloc.cu).
+int launch_fused_scratch(const uint8_t* img, size_t pitch, const float* theta, const float* sigma, int H,
+                         int W, int w, int N, void* out, int out_f64, unsigned* status,
+                         unsigned long long* n_fallback, cudaStream_t s)
+{
+    FusedParams p;
+    std::memset(&p, 0, sizeof(p));
+    p.img = img;
+    p.pitch = (long long)pitch;
+    p.theta = theta;
+    p.sigma = sigma;
+    p.out = out;
+    p.H = H;
+    p.W = W;
+    p.w = w;
+    p.out_f64 = out_f64;
+    fused_geometry(w, &p.off, &p.Cb);
+    p.status = status;
+    p.n_fallback = n_fallback;
+    const int R = kTileH + 2 * w;
+    CUtensorMap tm;
+    std::memset(&tm, 0, sizeof(tm));
+    p.use_tma = encode_image_tmap(&tm, img, H, W, pitch, p.Cb, R) ? 1 : 0;
+    dim3 grid((W + kTileW - 1) / kTileW, (H + kTileH - 1) / kTileH);
+    const size_t smem = fused_smem_bytes(N, w, p.Cb);
+    return cuda_status(launch_fused_fp64(N, tm, p, grid, smem, s));
+}
+
 }  // namespace fabf
 
 // ---------------------------------------------------------------------------

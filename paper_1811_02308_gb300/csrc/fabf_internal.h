@@ -21,6 +21,10 @@ void fused_geometry(int w, int* off, int* Cb);
 int run_fused(fabf_ctx* ctx, const uint8_t* img, size_t pitch, const float* theta, const float* sigma, int H,
               int W, int w, int N, void* out, int out_f64, const DebugPlanes* dbg, cudaStream_t s);
 
+int launch_fused_scratch(const uint8_t* img, size_t pitch, const float* theta, const float* sigma, int H,
+                         int W, int w, int N, void* out, int out_f64, unsigned* status,
+                         unsigned long long* n_fallback, cudaStream_t s);
+
 void serve_destroy(ServeState* s);
 void batch_destroy(BatchState* b);
 

@@ -75,6 +75,7 @@ def load(path: str | None = None):
         "fabf_serve_submit": ([vp, C.POINTER(Request), C.POINTER(C.c_uint64)], i),
         "fabf_serve_poll": ([vp, C.c_uint64, i, C.POINTER(i)], i),
         "fabf_status_str": ([i], C.c_char_p),
+        "fabf_filter_noalloc": ([vp, vp, vp, i, i, sz, i, i, vp, i, vp, C.POINTER(C.c_uint64)], i),
         "fabf_hilbert_inverse": ([i, vp], i),
         "fabf_fused_smem_bytes": ([i, i, C.POINTER(sz)], i),
         "fabf_debug_stages": ([vp, vp, vp, vp, i, i, sz, i, i] + [vp] * 11, i),
@@ -194,6 +195,19 @@ def fabf_filter(ctx: Context, img, theta, sigma, w: int, N: int, out=None, out_i
         _check(rc, "fabf_filter")
         return out
     return out, rc
+
+
+def fabf_filter_noalloc(img, theta, sigma, w: int, N: int, out, out_is_f64: bool = True,
+                        pitch: int | None = None, stream: int | None = None):
+    """``fabf_filter_noalloc``: no context, device tensors only, blocking.
+    Returns (status, n_fallback)."""
+    H, W = int(theta.shape[0]), int(theta.shape[1])
+    p = int(pitch) if pitch is not None else int(img.shape[1])
+    s = _stream_of(img, theta, sigma, out) if stream is None else stream
+    nf = C.c_uint64(0)
+    rc = load().fabf_filter_noalloc(_ptr(img), _ptr(theta), _ptr(sigma), H, W, p, int(w), int(N),
+                                    _ptr(out), 1 if out_is_f64 else 0, s, C.byref(nf))
+    return rc, nf.value
 
 
 def fabf_get_status(ctx: Context, stream: int = 0):
