@@ -33,6 +33,10 @@ N_BLOBS = 200
 METRIC = "FABF Mpix/s (N=5,w=20) & % of roofline vs plain FP64 form; served p50/p99 ms"
 WORKLOAD = ("1920x1080 uint8 synthetic (200 blobs, 4 step edges, noise 10), box w=20, N=5, "
             "theta=f+zeta (zeta in [-20,20]), sigma in [5,60]")
+# DRAM bytes (read + write) per launch of the fused FP64 kernel on this
+# workload, from the ncu capture in profiles/ (scaled from 4096x4096 by pixel
+# count); set to None whenever the kernel changes until it is re-captured.
+NCU_TRAFFIC_BYTES = 30.8e6
 SM_COUNT, SM_MAX_MHZ = 152, 2070.0
 FP64_FLOP_PER_SM_CLK = 4.0        # 2 DFMA per clock per SM (nominal 1.25 TFLOP/s FP64)
 
@@ -169,6 +173,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--traffic-bytes", type=float, default=None,
                     help="DRAM bytes per launch of the fused kernel from an ncu capture")
+    ap.add_argument("--profile", default=None, metavar="HxW",
+                    help="profiling case: one input of this size, no end-to-end or CPU legs")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -188,7 +194,12 @@ def main():
     ctx = fabf.Context(device=local)
     dev = torch.device("cuda", local)
 
+    global H_, W_
     n_distinct, n_slots = 4, 8
+    if args.profile:
+        H_, W_ = (int(v) for v in args.profile.lower().split("x"))
+        n_distinct, n_slots = 1, 1
+        args.no_cpu_baseline = True
     host = make_slot_inputs(n_distinct, 1000 + 17 * rank)
     slots = []
     for i in range(n_slots):
@@ -241,6 +252,11 @@ def main():
     npix = H_ * W_
     value = ws * npix * args.steps / (total_ms / 1e3) / 1e6
 
+    if args.profile:
+        print(json.dumps({"profile": args.profile, "ms_per_step": total_ms / args.steps,
+                          "status": st}), flush=True)
+        ctx.close()
+        return 0
     # end to end through the C ABI with pinned host buffers (copies inside)
     f, th, s = host[0]
     hf = torch.from_numpy(f).pin_memory()
@@ -269,7 +285,8 @@ def main():
     achieved = flops / (kern_ms / 1e3) / 1e12
     peak = SM_COUNT * SM_MAX_MHZ * 1e6 * FP64_FLOP_PER_SM_CLK / 1e12
     roofline = {"bound": "alu", "pipe": "fp64", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": args.traffic_bytes,
+                "frac": achieved / peak,
+                "traffic": args.traffic_bytes if args.traffic_bytes is not None else NCU_TRAFFIC_BYTES,
                 "peak_source": "nominal FP64 (152 SM x 4 flop/clk x 2070 MHz)",
                 "flops_per_pixel": fp64_flops_per_pixel(NDEG),
                 "kernel_ms": kern_ms, "hbm_bytes_per_pixel": 17}
