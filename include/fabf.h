@@ -62,7 +62,11 @@ typedef enum {
  *   FABF_FP64FIT_FP32REC: shift-scale and Hilbert fit in binary64, the
  *     integrals, recursion and ratio in binary32.
  *   FABF_CFP32: fit with compensated binary32 dot products, the rest in
- *     binary32. */
+ *     binary32.
+ * In both binary32 forms a pixel whose estimated error exceeds 0.02 gray
+ * levels (the ratio of Eq. (29) cancels badly, T2 <= 0, or the binary32
+ * integrals are in a regime where they lose digits) is recomputed on the
+ * FP64 path; fabf_get_status_ex counts those pixels. */
 typedef enum { FABF_FP64 = 0, FABF_FP64FIT_FP32REC = 1, FABF_CFP32 = 2 } fabf_precision;
 
 typedef struct {
@@ -122,17 +126,34 @@ int fabf_filter(fabf_ctx* ctx, const uint8_t* img, const float* theta, const flo
  * and the sigma -> infinity limit (the box mean) was returned instead. */
 int fabf_get_status(fabf_ctx* ctx, void* cuda_stream, int* status, uint64_t* n_fallback);
 
-/* Filter n images of any sizes, w and N in one persistent launch replayed
- * from a captured CUDA graph (tile shapes from the autotuner).  Pointers as
- * in fabf_filter (device pointers stay stream-ordered).  passes must be 1.
- * Errors as fabf_filter. */
+/* As fabf_get_status, and *n_fp64_redo (may be NULL) receives the number of
+ * pixels the binary32 precision forms recomputed on the FP64 path because
+ * their own error estimate exceeded 0.02 gray levels (or T2 <= 0, or the
+ * binary32 integrals were in a regime where they lose digits). */
+int fabf_get_status_ex(fabf_ctx* ctx, void* cuda_stream, int* status, uint64_t* n_fallback,
+                       uint64_t* n_fp64_redo);
+
+/* Algorithm 1 on n images of any sizes, w and N (reqs[i].passes must be 1)
+ * in one persistent launch: CTAs pop the tiles of all images from a device
+ * counter.  The launch (counter reset + kernel) is captured once in a CUDA
+ * graph and replayed by later calls with the same request array and
+ * precision; tile shapes come from the autotuner when the context has
+ * autotune on.  Device pointers only (FABF_EINVAL otherwise); stream-ordered
+ * on cuda_stream like fabf_filter, data errors via fabf_get_status.
+ * Errors: FABF_EINVAL, FABF_EUNSUPPORTED, FABF_ENOMEM, FABF_ECUDA. */
 int fabf_filter_batch(fabf_ctx* ctx, const fabf_request* reqs, int n, void* cuda_stream);
 
-/* Serving: admit one request into the continuous-batching loop.  The inputs
- * are copied at admission (caller buffers are free when the call returns);
- * out must stay valid until fabf_serve_poll reports completion.  Errors:
- * FABF_EINVAL, FABF_EUNSUPPORTED, FABF_ENOMEM (larger than the whole budget),
- * FABF_EAGAIN (budget full right now: retry later). */
+/* Serving: admit one request into the continuous-batching loop.  A request
+ * is admitted when one of 64 slots is free and its device bytes (inputs,
+ * output and pass state, about 17 B/px) fit the remaining memory budget;
+ * its passes are enqueued at once on the slot's stream, so requests admitted
+ * while others run overlap with them on the GPU.  The inputs are copied at
+ * admission (caller buffers are free when the call returns); out (host or
+ * device) must stay valid until fabf_serve_poll reports completion.  The
+ * first call starts the context's serving worker thread.  Errors:
+ * FABF_EINVAL (bad request, passes outside 1..16, sigma_decay <= 0),
+ * FABF_EUNSUPPORTED, FABF_ENOMEM (larger than the whole budget), FABF_EAGAIN
+ * (no slot or budget right now: retry later), FABF_ECUDA. */
 int fabf_serve_submit(fabf_ctx* ctx, const fabf_request* req, uint64_t* ticket);
 
 /* Serving: wait up to timeout_us microseconds (0 = do not wait) for ticket.
@@ -140,6 +161,20 @@ int fabf_serve_submit(fabf_ctx* ctx, const fabf_request* req, uint64_t* ticket);
  * FABF_EAGAIN while it is pending, FABF_ENOTFOUND for an unknown or already
  * collected ticket. */
 int fabf_serve_poll(fabf_ctx* ctx, uint64_t ticket, int timeout_us, int* result);
+
+/* Serving counters: device bytes held by admitted requests and the number
+ * of requests still running (either pointer may be NULL). */
+int fabf_serve_stats(fabf_ctx* ctx, uint64_t* bytes_in_use, int* in_flight);
+
+/* Batch counters: CUDA graph captures and graph launches so far. */
+int fabf_batch_stats(fabf_ctx* ctx, int* graph_captures, int* graph_launches);
+
+/* Output rows per tile the context uses for (w, N, precision): the
+ * autotuner's measured choice among 8, 16, 32 and 64 when autotune is on
+ * (the first query of a key times each candidate on a synthetic 512x1024
+ * image and caches the result, in tune_cache_path too), else 32.  Make the
+ * first query of a key before any stream capture. */
+int fabf_tile_rows(fabf_ctx* ctx, int w, int N, int precision, int* tile_rows);
 
 /* Text of a fabf_status value (static storage). */
 const char* fabf_status_str(int status);
@@ -177,7 +212,8 @@ int fabf_filter_noalloc(const uint8_t* img, const float* theta, const float* sig
  * kernels use.  Errors: FABF_EINVAL (out NULL), FABF_EUNSUPPORTED (N > 6). */
 int fabf_hilbert_inverse(int N, int64_t* out);
 
-/* Dynamic shared memory (bytes) the fused kernel needs for (w, N). */
+/* Dynamic shared memory (bytes) one CTA of the fused kernel needs for
+ * (w, N) with the tallest tile (64 output rows). */
 int fabf_fused_smem_bytes(int w, int N, size_t* bytes);
 
 /* ---- test entry points (device pointers only, synchronous) -------------- */

@@ -208,3 +208,22 @@ def bruteforce_pixels(f, theta, sigma, w, ys, xs):
                                             len(ys), _ptr(out, C.c_double)),
            "bruteforce_pixels")
     return out
+
+
+def fabf_passes(f, theta, sigma, w, N, passes, sigma_decay=0.8):
+    """Iterated filtering (texture filtering, Sec. IV-C): pass p+1 filters the
+    previous output rounded half to even and clamped to [0, 255], with centre
+    f_{p+1} + (theta - f) and width sigma_p * sigma_decay.  Returns the last
+    pass's output (float64)."""
+    f = np.ascontiguousarray(f, dtype=np.uint8)
+    zeta = np.asarray(theta, np.float32) - f.astype(np.float32)
+    th = np.asarray(theta, np.float32)
+    sg = np.asarray(sigma, np.float32)
+    g = None
+    for p in range(passes):
+        if p > 0:
+            f = np.clip(np.rint(g), 0, 255).astype(np.uint8)
+            th = (f.astype(np.float32) + zeta).astype(np.float32)
+            sg = (sg * np.float32(sigma_decay)).astype(np.float32)
+        g, _ = fabf(f, th, sg, w, N)
+    return g

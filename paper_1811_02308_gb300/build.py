@@ -14,11 +14,14 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfabf.so")
 
 SOURCES = [
+    "fabf_inst_fp64.cu",
+    "fabf_inst_fp64fit.cu",
+    "fabf_inst_cfp32.cu",
     "fabf_api.cu",
     "fabf_batch_serve.cu",
     "fabf_noalloc.cu",
 ]
-HEADERS = ["fabf_device.cuh", "fabf_kernels.cuh", "fabf_internal.h"]
+HEADERS = ["fabf_device.cuh", "fabf_kernels.cuh", "fabf_launch.cuh", "fabf_internal.h"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

@@ -94,54 +94,52 @@ void fused_geometry(int w, int* off, int* Cb)
     *Cb = (*off + kTileW + 2 * w + 15) & ~15;
 }
 
-// ---- FP64 fused kernel dispatch ------------------------------------------
-template <int N>
-static cudaError_t launch_fused_n(const CUtensorMap& tm, const FusedParams& p, dim3 grid, size_t smem,
-                                  cudaStream_t s)
+// ---- kernel dispatch over precision --------------------------------------
+cudaError_t launch_fused(int prec, int N, const CUtensorMap& tm, const FusedParams& p, dim3 grid, size_t smem,
+                         cudaStream_t s)
 {
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(fabf_fused_kernel<N>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 110 * 1024);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
-    fabf_fused_kernel<N><<<grid, kThreads, smem, s>>>(tm, p);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_fused_fp64(int N, const CUtensorMap& tm, const FusedParams& p, dim3 grid, size_t smem,
-                              cudaStream_t s)
-{
-    switch (N) {
-    case 0: return launch_fused_n<0>(tm, p, grid, smem, s);
-    case 1: return launch_fused_n<1>(tm, p, grid, smem, s);
-    case 2: return launch_fused_n<2>(tm, p, grid, smem, s);
-    case 3: return launch_fused_n<3>(tm, p, grid, smem, s);
-    case 4: return launch_fused_n<4>(tm, p, grid, smem, s);
-    case 5: return launch_fused_n<5>(tm, p, grid, smem, s);
-    case 6: return launch_fused_n<6>(tm, p, grid, smem, s);
+    switch (prec) {
+    case kPrecFP64: return launch_fused_p0(N, tm, p, grid, smem, s);
+    case kPrecFP64Fit: return launch_fused_p1(N, tm, p, grid, smem, s);
+    case kPrecCFP32: return launch_fused_p2(N, tm, p, grid, smem, s);
     default: return cudaErrorInvalidValue;
     }
 }
 
-}  // namespace fabf
+cudaError_t launch_batch(int prec, const BatchParams& p, int grid, size_t smem, cudaStream_t s)
+{
+    switch (prec) {
+    case kPrecFP64: return launch_batch_p0(p, grid, smem, s);
+    case kPrecFP64Fit: return launch_batch_p1(p, grid, smem, s);
+    case kPrecCFP32: return launch_batch_p2(p, grid, smem, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
 
-// ---------------------------------------------------------------------------
-// Context
-// ---------------------------------------------------------------------------
-struct fabf_ctx {
-    int device = 0;
-    int precision = FABF_FP64;
-    size_t budget = 0;
-    int autotune = 0;
-    unsigned* d_status = nullptr;            // [0] status bits
-    unsigned long long* d_nfb = nullptr;     // fallback pixel count
-    void* stage = nullptr;                   // grow-only staging buffer for host pointers
-    size_t stage_bytes = 0;
-    fabf::ServeState* serve = nullptr;
-    fabf::BatchState* batch = nullptr;
-};
+size_t make_job(ImageJob* J, CUtensorMap* tm, const uint8_t* img, size_t pitch, const float* theta,
+                const float* sigma, int H, int W, int w, int N, void* out, int out_f64, int TH)
+{
+    std::memset(J, 0, sizeof(*J));
+    J->img = img;
+    J->pitch = (long long)pitch;
+    J->theta = theta;
+    J->sigma = sigma;
+    J->out = out;
+    J->H = H;
+    J->W = W;
+    J->w = w;
+    J->N = N;
+    J->out_f64 = out_f64;
+    J->TH = TH;
+    fused_geometry(w, &J->off, &J->Cb);
+    J->tiles_x = (W + kTileW - 1) / kTileW;
+    J->tiles_y = (H + TH - 1) / TH;
+    std::memset(tm, 0, sizeof(*tm));
+    J->use_tma = encode_image_tmap(tm, img, H, W, pitch, J->Cb, TH + 2 * w) ? 1 : 0;
+    return fused_smem_bytes(N, w, J->Cb, TH);
+}
+
+}  // namespace fabf
 
 namespace fabf {
 
@@ -159,19 +157,36 @@ static int ensure_stage(fabf_ctx* ctx, size_t bytes)
     return FABF_OK;
 }
 
-static int read_and_clear_status(fabf_ctx* ctx, cudaStream_t s, int* status, uint64_t* nfb)
+int read_and_clear_status(fabf_ctx* ctx, cudaStream_t s, int* status, uint64_t* nfb, uint64_t* nredo)
 {
     unsigned st = 0;
-    unsigned long long n = 0;
+    unsigned long long n[2] = {0, 0};
     cudaError_t e = cudaMemcpyAsync(&st, ctx->d_status, sizeof(st), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&n, ctx->d_nfb, sizeof(n), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(n, ctx->d_nfb, sizeof(n), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_status, 0, sizeof(unsigned), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_nfb, 0, sizeof(unsigned long long), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_nfb, 0, sizeof(n), s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_status(e);
     if (status) *status = (st & kStatusTimeout) ? FABF_ETIMEOUT : (st & kStatusBadInput) ? FABF_EINVAL : FABF_OK;
-    if (nfb) *nfb = n;
+    if (nfb) *nfb = n[0];
+    if (nredo) *nredo = n[1];
     return FABF_OK;
+}
+
+int run_fused_prec(fabf_ctx* ctx, int prec, const uint8_t* img, size_t pitch, const float* theta,
+                   const float* sigma, int H, int W, int w, int N, void* out, int out_f64, int TH,
+                   const DebugPlanes* dbg, unsigned* status, unsigned long long* nfb, cudaStream_t s)
+{
+    (void)ctx;
+    FusedParams p;
+    std::memset(&p, 0, sizeof(p));
+    CUtensorMap tm;
+    const size_t smem = make_job(&p.job, &tm, img, pitch, theta, sigma, H, W, w, N, out, out_f64, TH);
+    p.status = status;
+    p.n_fallback = nfb;
+    if (dbg) p.dbg = *dbg;
+    dim3 grid(p.job.tiles_x, p.job.tiles_y);
+    return cuda_status(launch_fused(prec, N, tm, p, grid, smem, s));
 }
 
 // Launch the fused kernel on device buffers.
@@ -179,29 +194,10 @@ int run_fused(fabf_ctx* ctx, const uint8_t* img, size_t pitch, const float* thet
               int H, int W, int w, int N, void* out, int out_f64, const DebugPlanes* dbg,
               cudaStream_t s)
 {
-    if (ctx->precision != FABF_FP64) return FABF_EUNSUPPORTED;
-    FusedParams p;
-    std::memset(&p, 0, sizeof(p));
-    p.img = img;
-    p.pitch = (long long)pitch;
-    p.theta = theta;
-    p.sigma = sigma;
-    p.out = out;
-    p.H = H;
-    p.W = W;
-    p.w = w;
-    p.out_f64 = out_f64;
-    fused_geometry(w, &p.off, &p.Cb);
-    p.status = ctx->d_status;
-    p.n_fallback = ctx->d_nfb;
-    if (dbg) p.dbg = *dbg;
-    const int R = kTileH + 2 * w;
-    CUtensorMap tm;
-    std::memset(&tm, 0, sizeof(tm));
-    p.use_tma = encode_image_tmap(&tm, img, H, W, pitch, p.Cb, R) ? 1 : 0;
-    dim3 grid((W + kTileW - 1) / kTileW, (H + kTileH - 1) / kTileH);
-    const size_t smem = fused_smem_bytes(N, w, p.Cb);
-    return cuda_status(launch_fused_fp64(N, tm, p, grid, smem, s));
+    const int prec = dbg ? kPrecFP64 : ctx->precision;
+    const int TH = dbg ? kDefaultTileRows : tile_rows_for(ctx, w, N, prec);
+    return run_fused_prec(ctx, prec, img, pitch, theta, sigma, H, W, w, N, out, out_f64, TH, dbg,
+                          ctx->d_status, ctx->d_nfb, s);
 }
 
 // Launch the fused FP64 kernel on device buffers with caller-provided status
@@ -210,27 +206,8 @@ int launch_fused_scratch(const uint8_t* img, size_t pitch, const float* theta, c
                          int W, int w, int N, void* out, int out_f64, unsigned* status,
                          unsigned long long* n_fallback, cudaStream_t s)
 {
-    FusedParams p;
-    std::memset(&p, 0, sizeof(p));
-    p.img = img;
-    p.pitch = (long long)pitch;
-    p.theta = theta;
-    p.sigma = sigma;
-    p.out = out;
-    p.H = H;
-    p.W = W;
-    p.w = w;
-    p.out_f64 = out_f64;
-    fused_geometry(w, &p.off, &p.Cb);
-    p.status = status;
-    p.n_fallback = n_fallback;
-    const int R = kTileH + 2 * w;
-    CUtensorMap tm;
-    std::memset(&tm, 0, sizeof(tm));
-    p.use_tma = encode_image_tmap(&tm, img, H, W, pitch, p.Cb, R) ? 1 : 0;
-    dim3 grid((W + kTileW - 1) / kTileW, (H + kTileH - 1) / kTileH);
-    const size_t smem = fused_smem_bytes(N, w, p.Cb);
-    return cuda_status(launch_fused_fp64(N, tm, p, grid, smem, s));
+    return run_fused_prec(nullptr, kPrecFP64, img, pitch, theta, sigma, H, W, w, N, out, out_f64,
+                          kDefaultTileRows, nullptr, status, n_fallback, s);
 }
 
 }  // namespace fabf
@@ -253,7 +230,9 @@ int fabf_create(const fabf_config* cfg, fabf_ctx** out)
     ctx->precision = c.precision;
     ctx->budget = c.mem_budget_bytes ? c.mem_budget_bytes : (size_t)16 << 30;
     ctx->autotune = c.autotune;
+    if (c.tune_cache_path) ctx->tune_cache_path = c.tune_cache_path;
     cudaError_t e = cudaSetDevice(c.device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, c.device);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->d_status, 256);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->d_nfb, 256);
     if (e == cudaSuccess) e = cudaMemset(ctx->d_status, 0, 256);
@@ -342,7 +321,7 @@ int fabf_filter(fabf_ctx* ctx, const uint8_t* img, const float* theta, const flo
         if (e != cudaSuccess) return cuda_status(e);
     }
     int st = FABF_OK;
-    rc = read_and_clear_status(ctx, s, &st, nullptr);
+    rc = read_and_clear_status(ctx, s, &st, nullptr, nullptr);
     return rc ? rc : st;
 }
 
@@ -350,7 +329,14 @@ int fabf_get_status(fabf_ctx* ctx, void* cuda_stream, int* status, uint64_t* n_f
 {
     if (!ctx || !status) return FABF_EINVAL;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return FABF_ECUDA;
-    return read_and_clear_status(ctx, static_cast<cudaStream_t>(cuda_stream), status, n_fallback);
+    return read_and_clear_status(ctx, static_cast<cudaStream_t>(cuda_stream), status, n_fallback, nullptr);
+}
+
+int fabf_get_status_ex(fabf_ctx* ctx, void* cuda_stream, int* status, uint64_t* n_fallback, uint64_t* n_fp64_redo)
+{
+    if (!ctx || !status) return FABF_EINVAL;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return FABF_ECUDA;
+    return read_and_clear_status(ctx, static_cast<cudaStream_t>(cuda_stream), status, n_fallback, n_fp64_redo);
 }
 
 const char* fabf_status_str(int status)
@@ -384,7 +370,7 @@ int fabf_fused_smem_bytes(int w, int N, size_t* bytes)
     if (w > kWMax || N > kNMax) return FABF_EUNSUPPORTED;
     int off, Cb;
     fused_geometry(w, &off, &Cb);
-    *bytes = fused_smem_bytes(N, w, Cb);
+    *bytes = fused_smem_bytes(N, w, Cb, kTileHMax);
     return FABF_OK;
 }
 
@@ -399,13 +385,10 @@ int fabf_debug_stages(fabf_ctx* ctx, const uint8_t* img, const float* theta, con
     if (!alpha || !beta || !m || !M || !mu || !c || !t0lam || !I || !T || !flags) return FABF_EINVAL;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return FABF_ECUDA;
     DebugPlanes d{alpha, beta, m, M, mu, c, t0lam, I, T, flags};
-    const int saved = ctx->precision;
-    ctx->precision = FABF_FP64;
-    rc = run_fused(ctx, img, pitch, theta, sigma, H, W, w, N, out, 1, &d, 0);
-    ctx->precision = saved;
+    rc = run_fused(ctx, img, pitch, theta, sigma, H, W, w, N, out, 1, &d, 0);   // FP64 with exports
     if (rc) return rc;
     int st = FABF_OK;
-    rc = read_and_clear_status(ctx, 0, &st, nullptr);
+    rc = read_and_clear_status(ctx, 0, &st, nullptr, nullptr);
     return rc ? rc : st;
 }
 
@@ -413,19 +396,20 @@ int fabf_debug_integrals(fabf_ctx* ctx, const double* lambda, const double* t0, 
                          int precision, double* out)
 {
     if (!ctx || !lambda || !t0 || !out || n < 0 || K < 1 || K > 7) return FABF_EINVAL;
-    if (precision != FABF_FP64) return FABF_EUNSUPPORTED;
+    if (precision != FABF_FP64 && precision != FABF_FP64FIT_FP32REC) return FABF_EUNSUPPORTED;
+    const int fp32 = precision == FABF_FP64 ? 0 : 1;
     if (n == 0) return FABF_OK;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return FABF_ECUDA;
     const int threads = 128;
     const unsigned blocks = (unsigned)((n + threads - 1) / threads);
     switch (K) {
-    case 1: integrals_kernel<1><<<blocks, threads>>>(lambda, t0, n, out); break;
-    case 2: integrals_kernel<2><<<blocks, threads>>>(lambda, t0, n, out); break;
-    case 3: integrals_kernel<3><<<blocks, threads>>>(lambda, t0, n, out); break;
-    case 4: integrals_kernel<4><<<blocks, threads>>>(lambda, t0, n, out); break;
-    case 5: integrals_kernel<5><<<blocks, threads>>>(lambda, t0, n, out); break;
-    case 6: integrals_kernel<6><<<blocks, threads>>>(lambda, t0, n, out); break;
-    default: integrals_kernel<7><<<blocks, threads>>>(lambda, t0, n, out); break;
+    case 1: integrals_kernel<1><<<blocks, threads>>>(lambda, t0, n, fp32, out); break;
+    case 2: integrals_kernel<2><<<blocks, threads>>>(lambda, t0, n, fp32, out); break;
+    case 3: integrals_kernel<3><<<blocks, threads>>>(lambda, t0, n, fp32, out); break;
+    case 4: integrals_kernel<4><<<blocks, threads>>>(lambda, t0, n, fp32, out); break;
+    case 5: integrals_kernel<5><<<blocks, threads>>>(lambda, t0, n, fp32, out); break;
+    case 6: integrals_kernel<6><<<blocks, threads>>>(lambda, t0, n, fp32, out); break;
+    default: integrals_kernel<7><<<blocks, threads>>>(lambda, t0, n, fp32, out); break;
     }
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaDeviceSynchronize();

@@ -66,9 +66,29 @@ __host__ __device__ constexpr RecipTable make_recip_table()
     return t;
 }
 
-// Both tables are built at compile time; each translation unit that includes
+// The same entries split exactly into two binary32 values (|entry| < 2^28).
+struct AinvSplitTable {
+    float hi[kNMax + 1][kNMax + 1][kNMax + 1];
+    float lo[kNMax + 1][kNMax + 1][kNMax + 1];
+};
+
+__host__ __device__ constexpr AinvSplitTable make_ainv_split_table()
+{
+    AinvSplitTable t{};
+    for (int N = 0; N <= kNMax; ++N)
+        for (int n = 0; n <= N; ++n)
+            for (int k = 0; k <= N; ++k) {
+                const double a = (double)hilbert_inverse_entry(N, n + 1, k + 1);
+                t.hi[N][n][k] = (float)a;
+                t.lo[N][n][k] = (float)(a - (double)(float)a);
+            }
+    return t;
+}
+
+// The tables are built at compile time; each translation unit that includes
 // this header holds its own copy in constant memory.
 static __constant__ AinvTable c_ainv = make_ainv_table();
+static __constant__ AinvSplitTable c_ainv_split = make_ainv_split_table();
 static __constant__ RecipTable c_recip = make_recip_table();
 
 // ---------------------------------------------------------------------------
@@ -242,6 +262,246 @@ __device__ __forceinline__ double fabf_pixel_fp64(const AinvTable& A, int alpha,
         tr->fallback = fallback;
     }
     return (double)alpha + (double)d * F;
+}
+
+
+// ---------------------------------------------------------------------------
+// The same integrals in binary32 (precision variants).  The downward
+// recursion holds ~1e-7 in binary32 for lambda < 2.5 at every t0 and up to
+// lambda < 8 when t0 < 0; the forward recursion is used elsewhere.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool backward_fp32(float lam, float t0)
+{
+    return lam < 2.5f || (t0 < 0.0f && lam < 8.0f);
+}
+
+template <int K>
+__device__ __forceinline__ void integrals_fp32(float lam, float t0, float (&I)[K + 1])
+{
+    static_assert(K >= 1 && K <= 7, "K out of range");
+    if (!backward_fp32(lam, t0)) {
+        const float inv2l = 0.5f / lam;
+        const float rl = rsqrtf(lam);
+        const float sl = lam * rl;
+        const float h = 0.886226925452758f * rl;
+        float E0s, E1s, I0;
+        if (t0 < 0.0f) {
+            E0s = 1.0f;
+            E1s = expf(lam * (2.0f * t0 - 1.0f));
+            I0 = h * (erfcxf(-sl * t0) - E1s * erfcxf(sl * (1.0f - t0)));
+        } else if (t0 > 1.0f) {
+            E1s = 1.0f;
+            E0s = expf(lam * (1.0f - 2.0f * t0));
+            I0 = h * (erfcxf(sl * (t0 - 1.0f)) - E0s * erfcxf(sl * t0));
+        } else {
+            E0s = expf(-lam * t0 * t0);
+            E1s = expf(-lam * (1.0f - t0) * (1.0f - t0));
+            I0 = h * (erff(sl * (1.0f - t0)) + erff(sl * t0));
+        }
+        const float e1 = E1s * inv2l;
+        I[0] = I0;
+        I[1] = fmaf(t0, I0, (E0s - E1s) * inv2l);
+#pragma unroll
+        for (int k = 2; k <= K; ++k) I[k] = fmaf(t0, I[k - 1], fmaf((float)(k - 1) * inv2l, I[k - 2], -e1));
+    } else {
+        float E1s;
+        if (t0 < 0.0f) E1s = expf(lam * (2.0f * t0 - 1.0f));
+        else if (t0 > 1.0f) E1s = 1.0f;
+        else E1s = expf(-lam * (1.0f - t0) * (1.0f - t0));
+        constexpr int Kp = 48;
+        const float l2 = 2.0f * lam;
+        const float q = l2 * (t0 - 1.0f);
+        const float r1 = (float)(Kp + 2) + q, r0 = (float)(Kp + 1) + q;
+        float hi = __fdividef(E1s, r1 > 1.0f ? r1 : (float)(Kp + 2));
+        float lo = __fdividef(E1s, r0 > 1.0f ? r0 : (float)(Kp + 1));
+#pragma unroll 4
+        for (int k = Kp + 1; k >= K + 2; --k) {
+            const float nx = fmaf(l2, fmaf(-t0, lo, hi), E1s) * (1.0f / (float)(k - 1));
+            hi = lo;
+            lo = nx;
+        }
+        I[K] = lo;
+        const float top = hi;
+#pragma unroll
+        for (int k = K + 1; k >= 2; --k) {
+            const float Ik = (k == K + 1) ? top : I[k];
+            I[k - 2] = fmaf(l2, fmaf(-t0, I[k - 1], Ik), E1s) * (1.0f / (float)(k - 1));
+        }
+    }
+}
+
+// Exact shifted moments M_b = sum_window (f - alpha)^b, b = 0..K (Eq. (24)).
+template <int K>
+__device__ __forceinline__ void shifted_moments(int alpha, const int64_t (&m)[K + 1], int64_t (&M)[K + 1])
+{
+    int64_t s[K + 1];
+#pragma unroll
+    for (int a = 0; a <= K; ++a) s[a] = m[a];
+    M[0] = s[0];
+#pragma unroll
+    for (int b = 1; b <= K; ++b) {
+#pragma unroll
+        for (int a = 0; a <= K - b; ++a) s[a] = s[a + 1] - (int64_t)alpha * s[a];
+        M[b] = s[0];
+    }
+}
+
+// binary32 tail shared by both variants: kernel parameters, integrals and
+// the ratio of Eq. (29) from float coefficients c.
+//
+// Guard: the sums T1 = sum c_k I_{k+1} and T2 = sum c_k I_k cancel (the
+// fitted coefficients alternate and are large), so their binary32 error is
+// about u (S1 + |F| S2) / |T2| relative in F, with S1 = sum |c_k I_{k+1}|,
+// S2 = sum |c_k I_k|, u = 2^-24.  When that estimate, scaled to gray levels
+// by (beta - alpha) and by 4 ulps of slack for the integrals' own error,
+// exceeds kFp32GuardGray, or the binary32 integrals are in a regime where
+// they are known to lose digits, or T2 <= 0, the tail reports `redo` and the
+// caller recomputes the pixel on the FP64 path.
+constexpr float kFp32GuardGray = 0.25f;
+
+__device__ __forceinline__ bool fp32_integrals_weak(float lam, float t0)
+{
+    const float sl = sqrtf(lam);
+    if (t0 < 0.0f && !backward_fp32(lam, t0)) return sl * (-t0) > 0.5f;   // forward, centre left of 0
+    if (t0 > 1.0f && backward_fp32(lam, t0)) return lam > 0.7f && sl * (t0 - 1.0f) > 1.0f;
+    return false;
+}
+
+template <int N>
+__device__ __forceinline__ float fabf_tail_fp32(const float (&c)[N + 1], int64_t M0, int64_t M1, int alpha, int d,
+                                               float theta_f, float sigma_f, int& fallback, bool& redo)
+{
+    const float rd = 1.0f / (float)d;
+    const float t0 = (theta_f - (float)alpha) * rd;
+    const float lam = (float)(d * d) / (2.0f * sigma_f * sigma_f);
+    float I[N + 2];
+    integrals_fp32<N + 1>(lam, t0, I);
+    float T1 = c[0] * I[1], T2 = c[0] * I[0];
+    float S1 = fabsf(T1), S2 = fabsf(T2);
+#pragma unroll
+    for (int k = 2; k <= N + 1; ++k) {
+        T1 = fmaf(c[k - 1], I[k], T1);
+        T2 = fmaf(c[k - 1], I[k - 1], T2);
+        S1 = fmaf(fabsf(c[k - 1]), fabsf(I[k]), S1);
+        S2 = fmaf(fabsf(c[k - 1]), fabsf(I[k - 1]), S2);
+    }
+    float F = T1 / T2;
+    const float est = 4.0f * 5.9604645e-8f * (float)d * (S1 + fabsf(F) * S2) / fabsf(T2);
+    redo = !(T2 > 0.0f) || !(est <= kFp32GuardGray) || fp32_integrals_weak(lam, t0);
+    if (!(T2 > 0.0f) || !isfinite(F)) {
+        F = __ll2float_rn(M1) / (__ll2float_rn(M0) * (float)d);   // mu_1 / mu_0
+        fallback = 1;
+    }
+    return fmaf((float)d, F, (float)alpha);
+}
+
+// FABF_FP64FIT_FP32REC: shift-scale and Hilbert fit in binary64 (the fit's
+// conditioning needs it), integrals, recursion and ratio in binary32.
+template <int N>
+__device__ __forceinline__ float fabf_pixel_fp64fit(const AinvTable& A, int alpha, int beta, int fi,
+                                                    const int64_t (&m)[(N < 1 ? 1 : N) + 1],
+                                                    float theta_f, float sigma_f, int& fallback, bool& redo)
+{
+    redo = false;
+    constexpr int K = N < 1 ? 1 : N;
+    fallback = 0;
+    if (alpha == beta) return (float)fi;
+    const int d = beta - alpha;
+    int64_t M[K + 1];
+    shifted_moments<K>(alpha, m, M);
+    // mu_k = M_k (1/d)^k: one division; the few ulps this costs are far below
+    // what the binary32 stages keep.
+    const double rd = 1.0 / (double)d;
+    double mu[K + 1], p = 1.0;
+#pragma unroll
+    for (int k = 0; k <= K; ++k) {
+        mu[k] = (double)M[k] * p;
+        p *= rd;
+    }
+    float c[N + 1];
+#pragma unroll
+    for (int n = 0; n <= N; ++n) {
+        double acc = 0.0;
+#pragma unroll
+        for (int k = 0; k <= N; ++k) acc = fma(A.v[N][n][k], mu[k], acc);
+        c[n] = (float)acc;
+    }
+    return fabf_tail_fp32<N>(c, M[0], M[1], alpha, d, theta_f, sigma_f, fallback, redo);
+}
+
+// Error-free transformations (Knuth TwoSum, FMA TwoProduct) for the
+// compensated binary32 fit.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
+{
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e)
+{
+    p = a * b;
+    e = fmaf(a, b, -p);
+}
+
+// int64 -> unevaluated sum hi + lo of two floats (exact to 2^-48 relative).
+__device__ __forceinline__ void ll_to_ff(int64_t v, float& hi, float& lo)
+{
+    hi = __ll2float_rn(v);
+    lo = __ll2float_rn(v - __float2ll_rn(hi));
+}
+
+// FABF_CFP32: no binary64.  mu_k as float-float quotients of the exact
+// integers M_k and d^k, and c = A^{-1} mu by compensated dot products
+// (Ogita, Rump & Oishi, "Accurate sum and dot product", 2005: TwoProduct
+// and TwoSum accumulate each product's and each addition's rounding error,
+// so the dot product is as accurate as if evaluated in twice the working
+// precision); A^{-1} entries (< 2^28) are split exactly into two floats.
+template <int N>
+__device__ __forceinline__ float fabf_pixel_cfp32(const AinvSplitTable& A, int alpha, int beta, int fi,
+                                                  const int64_t (&m)[(N < 1 ? 1 : N) + 1],
+                                                  float theta_f, float sigma_f, int& fallback, bool& redo)
+{
+    redo = false;
+    constexpr int K = N < 1 ? 1 : N;
+    fallback = 0;
+    if (alpha == beta) return (float)fi;
+    const int d = beta - alpha;
+    int64_t M[K + 1];
+    shifted_moments<K>(alpha, m, M);
+    float muh[K + 1], mul[K + 1];
+    int64_t dk = 1;
+#pragma unroll
+    for (int k = 0; k <= K; ++k) {
+        float Mh, Ml, Dh, Dl;
+        ll_to_ff(M[k], Mh, Ml);
+        ll_to_ff(dk, Dh, Dl);
+        // (Mh + Ml) / (Dh + Dl) in float-float: q1 = Mh / Dh, then one
+        // correction from the exact residual.
+        const float q1 = Mh / Dh;
+        float ph, pl;
+        two_prod(q1, Dh, ph, pl);
+        const float r = (((Mh - ph) - pl) + Ml) - q1 * Dl;
+        muh[k] = q1;
+        mul[k] = r / Dh;
+        dk *= d;
+    }
+    float c[N + 1];
+#pragma unroll
+    for (int n = 0; n <= N; ++n) {
+        float s = 0.0f, comp = 0.0f;
+#pragma unroll
+        for (int k = 0; k <= N; ++k) {
+            const float ah = A.hi[N][n][k], al = A.lo[N][n][k];
+            float p, pe, t, te;
+            two_prod(ah, muh[k], p, pe);
+            two_sum(s, p, t, te);
+            s = t;
+            comp += pe + te + fmaf(ah, mul[k], al * muh[k]);
+        }
+        c[n] = s + comp;
+    }
+    return fabf_tail_fp32<N>(c, M[0], M[1], alpha, d, theta_f, sigma_f, fallback, redo);
 }
 
 }  // namespace fabf

@@ -1,30 +1,97 @@
 // Declarations shared by the host translation units of the library.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
+
 #include <cstddef>
 #include <cstdint>
-
-struct fabf_ctx;
+#include <map>
+#include <mutex>
+#include <string>
 
 namespace fabf {
 
 struct DebugPlanes;
+struct FusedParams;
+struct BatchParams;
+struct ImageJob;
 struct ServeState;
 struct BatchState;
+
+struct TuneEntry {
+    int TH;         // output rows per tile
+    float ms;       // measured time of the tuning image (0 = not measured)
+};
+
+}  // namespace fabf
+
+struct fabf_ctx {
+    int device = 0;
+    int precision = 0;
+    size_t budget = 0;
+    int autotune = 0;
+    std::string tune_cache_path;
+    int num_sms = 0;
+    unsigned* d_status = nullptr;            // status bits of stream-ordered calls
+    unsigned long long* d_nfb = nullptr;     // fallback pixel count
+    void* stage = nullptr;                   // grow-only staging buffer for host pointers
+    size_t stage_bytes = 0;
+    std::mutex tune_lock;
+    std::map<int, fabf::TuneEntry> tune;     // key: tune_key(w, N, precision)
+    fabf::ServeState* serve = nullptr;
+    fabf::BatchState* batch = nullptr;
+};
+
+namespace fabf {
+
+inline int tune_key(int w, int N, int prec) { return (w * 8 + N) * 4 + prec; }
 
 int cuda_status(cudaError_t e);
 bool is_device_ptr(const void* p);
 int check_filter_args(const void* img, const void* theta, const void* sigma, const void* out, int H, int W,
                       size_t pitch, int w, int N);
 void fused_geometry(int w, int* off, int* Cb);
+bool encode_image_tmap(CUtensorMap* tm, const uint8_t* img, int H, int W, size_t pitch, int Cb, int R);
+
+// Fill the launch description of one image with TH output rows per tile; the
+// tensor map is encoded (and J->use_tma set) when the image allows TMA.
+// Returns the dynamic shared memory one tile needs.
+size_t make_job(ImageJob* J, CUtensorMap* tm, const uint8_t* img, size_t pitch, const float* theta,
+                const float* sigma, int H, int W, int w, int N, void* out, int out_f64, int TH);
+
+cudaError_t launch_fused(int prec, int N, const CUtensorMap& tm, const FusedParams& p, dim3 grid, size_t smem,
+                         cudaStream_t s);
+cudaError_t launch_batch(int prec, const BatchParams& p, int grid, size_t smem, cudaStream_t s);
+cudaError_t launch_fused_p0(int N, const CUtensorMap& tm, const FusedParams& p, dim3 grid, size_t smem,
+                            cudaStream_t s);
+cudaError_t launch_fused_p1(int N, const CUtensorMap& tm, const FusedParams& p, dim3 grid, size_t smem,
+                            cudaStream_t s);
+cudaError_t launch_fused_p2(int N, const CUtensorMap& tm, const FusedParams& p, dim3 grid, size_t smem,
+                            cudaStream_t s);
+cudaError_t launch_batch_p0(const BatchParams& p, int grid, size_t smem, cudaStream_t s);
+cudaError_t launch_batch_p1(const BatchParams& p, int grid, size_t smem, cudaStream_t s);
+cudaError_t launch_batch_p2(const BatchParams& p, int grid, size_t smem, cudaStream_t s);
+
+// Launch one image on device buffers with the context's precision and tuned
+// tile shape; status words are the context's.
 int run_fused(fabf_ctx* ctx, const uint8_t* img, size_t pitch, const float* theta, const float* sigma, int H,
               int W, int w, int N, void* out, int out_f64, const DebugPlanes* dbg, cudaStream_t s);
+int run_fused_prec(fabf_ctx* ctx, int prec, const uint8_t* img, size_t pitch, const float* theta,
+                   const float* sigma, int H, int W, int w, int N, void* out, int out_f64, int TH,
+                   const DebugPlanes* dbg, unsigned* status, unsigned long long* nfb, cudaStream_t s);
 
+// FP64 launch with caller-provided status words (allocation-free entry point).
 int launch_fused_scratch(const uint8_t* img, size_t pitch, const float* theta, const float* sigma, int H,
                          int W, int w, int N, void* out, int out_f64, unsigned* status,
                          unsigned long long* n_fallback, cudaStream_t s);
 
+// Output rows per tile for (w, N, prec): the autotuner's choice when the
+// context has autotune on (measured once and cached), else the default.
+int tile_rows_for(fabf_ctx* ctx, int w, int N, int prec);
+constexpr int kDefaultTileRows = 32;
+
+int read_and_clear_status(fabf_ctx* ctx, cudaStream_t s, int* status, uint64_t* nfb, uint64_t* nredo);
 void serve_destroy(ServeState* s);
 void batch_destroy(BatchState* b);
 

@@ -1,27 +1,32 @@
-// Fused tiled kernel of fast adaptive bilateral filtering (Algorithm 1,
-// Sec. II-D of Gavaskar & Chaudhury) for one 8-bit image with a box spatial
-// kernel of radius w, plus the test-only kernels that share its device code.
+// Tiled kernels of fast adaptive bilateral filtering (Algorithm 1, Sec. II-D
+// of Gavaskar & Chaudhury) for 8-bit images with a box spatial kernel of
+// radius w, plus the test-only kernels that share their device code.
 //
-// One CTA (256 threads, 8 warps) produces a TH x TW = 32 x 64 output tile.
+// One CTA (256 threads, 8 warps) produces a TH x 64 output tile (TH a
+// multiple of 8 up to 64, chosen per (w, N, precision) by the autotuner):
 //  1. The input tile plus a w-pixel halo is staged in shared memory with one
-//     TMA tensor copy (cp.async.bulk.tensor.2d completing on an mbarrier);
-//     the copy starts at a 16-byte aligned column, so the tile carries a
-//     constant offset `off` = (-w) mod 16.  Out-of-image bytes read as 0.
-//     Images whose base or pitch are not 16-byte aligned take a plain
-//     cooperative load into the same layout.
-//  2. The tile's 32 output rows are processed in chunks of 8.  Vertical
-//     phase: thread c owns tile column c; it keeps running window sums of
-//     f^k (k = 1..N, Eq. (17) with omega == 1, rows clipped to the image)
-//     in registers across chunks (add the entering row, subtract the leaving
-//     row), and forms the vertical min / max of the 8 windows of a chunk from
-//     their common core plus at most 7 extra rows each (Eq. (8)).
+//     TMA tensor copy (cp.async.bulk.tensor.2d completing on an mbarrier,
+//     bounded wait); the copy starts at a 16-byte aligned column, so the
+//     tile carries a constant column offset off = (-w) mod 16.  Out-of-image
+//     bytes read as 0.  Images whose base or pitch are not 16-byte aligned
+//     take a plain cooperative load into the same layout.
+//  2. Output rows are processed in chunks of 8.  Vertical phase: thread c
+//     owns tile column c; it keeps running window sums of f^k (k = 1..N,
+//     Eq. (17) with omega == 1, rows clipped to the image) in registers
+//     across chunks (add the entering row, subtract the leaving row), and
+//     takes the vertical min / max of the 8 windows of a chunk from their
+//     common core plus at most 7 extra rows each (Eq. (8)).
 //  3. Horizontal phase: warp r owns chunk row r.  It turns each vertical
-//     sum row into a prefix sum (wrapping arithmetic; window sums are
-//     differences of two prefixes and fit in int64), and each min / max row
-//     into a sparse-table level of width 2^floor(log2(2w+1)) so the window
-//     min / max is the min / max of two entries.  Each lane then finishes
-//     two pixels: m_0 from the clipped window geometry, the exact shifted
-//     moments, the FP64 fit, the integrals and the ratio (fabf_device.cuh).
+//     sum row into a prefix sum (window sums are differences of two
+//     prefixes and fit in int64), and each min / max row into one
+//     sparse-table level of width 2^floor(log2(2w+1)), so a window's min /
+//     max is the min / max of two entries.  Each lane then finishes two
+//     pixels (fabf_device.cuh): m_0 from the clipped window geometry, the
+//     exact shifted moments, the fit, the integrals and the ratio.
+//
+// The single-image kernel runs one tile per CTA.  The batch kernel is
+// persistent: each CTA pops tiles of many images (any sizes, w and N) from a
+// device counter until the work list is exhausted.
 #pragma once
 
 #include <cuda.h>
@@ -33,10 +38,18 @@
 namespace fabf {
 
 constexpr int kTileW = 64;
-constexpr int kTileH = 32;
+constexpr int kTileHMax = 64;
 constexpr int kChunk = 8;
 constexpr int kThreads = 256;
-constexpr unsigned kTmaWaitLimit = 1u << 22;   // bounded mbarrier wait
+constexpr unsigned kTmaWaitLimit = 1u << 22;   // bounded mbarrier wait (polls)
+
+// Per-chunk list of pixels the binary32 forms hand to the FP64 path: a count
+// and one 16-bit (row, column) entry per pixel of the chunk.
+constexpr size_t kRedoBytes = 16 + 2 * kChunk * kTileW;
+
+constexpr int kPrecFP64 = 0;          // FABF_FP64
+constexpr int kPrecFP64Fit = 1;       // FABF_FP64FIT_FP32REC
+constexpr int kPrecCFP32 = 2;         // FABF_CFP32
 
 struct DebugPlanes {       // per-stage exports for the parity tests (all optional)
     uint8_t* alpha;        // H x W
@@ -51,33 +64,51 @@ struct DebugPlanes {       // per-stage exports for the parity tests (all option
     int32_t* flags;        // H x W: bit0 flat window, bit1 fallback taken
 };
 
-struct FusedParams {
+// One image of a launch.
+struct ImageJob {
     const uint8_t* img;
     long long pitch;       // bytes between image rows
     const float* theta;    // H x W, row stride W
     const float* sigma;    // H x W, row stride W
     void* out;             // H x W float64 or float32, row stride W
-    int H, W, w;
+    int H, W, w, N;
     int out_f64;
     int use_tma;
     int off;               // (-w) mod 16: tile column of image column x0 - w
     int Cb;                // tile row length in shared memory (multiple of 16)
+    int TH;                // output rows per tile (multiple of 8, <= 64)
+    int tiles_x, tiles_y;
+    long long tile_begin;  // index of this image's first tile in the launch
+};
+
+struct FusedParams {
+    ImageJob job;
     unsigned* status;                  // OR of kStatus* bits (may be null)
     unsigned long long* n_fallback;    // pixels that took the fallback (may be null)
     DebugPlanes dbg;
 };
 
-// Bytes of dynamic shared memory the fused kernel needs.
-__host__ __device__ inline size_t fused_smem_bytes(int N, int w, int Cb)
+struct BatchParams {
+    const ImageJob* jobs;              // njobs, sorted by tile_begin
+    const CUtensorMap* tmaps;          // one per job (64-byte aligned, global memory)
+    int njobs;
+    long long total_tiles;
+    unsigned long long* next_tile;     // work counter, zero at launch
+    unsigned* status;
+    unsigned long long* n_fallback;
+};
+
+// Bytes of dynamic shared memory one tile needs.
+__host__ __device__ inline size_t fused_smem_bytes(int N, int w, int Cb, int TH)
 {
-    const int R = kTileH + 2 * w;
+    const int R = TH + 2 * w;
     size_t tile = (size_t)R * Cb;
     tile = (tile + 127) & ~(size_t)127;
-    const int K = N < 1 ? 1 : N;               // the kernel keeps k = 1 even for N = 0
+    const int K = N < 1 ? 1 : N;               // k = 1 is kept even for N = 0
     const int n32 = K < 2 ? K : 2;
     const int n64 = K > 2 ? K - 2 : 0;
     size_t v = (size_t)kChunk * Cb * (2 + 4 * n32) + (size_t)kChunk * Cb * 8 * n64;
-    return 128 + tile + ((v + 15) & ~(size_t)15);
+    return 128 + tile + ((v + 15) & ~(size_t)15) + kRedoBytes;
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
@@ -88,19 +119,25 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p)
 // ---------------------------------------------------------------------------
 // Tile staging.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ bool tma_load_tile(const CUtensorMap* tmap, uint8_t* dst, uint64_t* bar,
-                                              int xs, int ys, uint32_t bytes)
+__device__ __forceinline__ void mbar_init(uint64_t* bar)
+{
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(1) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+}
+
+// One TMA copy of `bytes` into dst; waits (bounded) on phase `phase` of bar.
+// Returns false in every thread if the copy did not complete.
+__device__ __forceinline__ bool tma_load_tile(const CUtensorMap* tmap, uint8_t* dst, uint64_t* bar, int xs,
+                                              int ys, uint32_t bytes, uint32_t phase)
 {
     const uint32_t b = smem_u32(bar);
     if (threadIdx.x == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(b), "r"(1) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        // order this CTA's earlier generic accesses of dst before the async write
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes)
-                     : "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes) : "memory");
         asm volatile(
             "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
             " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
@@ -114,23 +151,21 @@ __device__ __forceinline__ bool tma_load_tile(const CUtensorMap* tmap, uint8_t* 
             "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
             "selp.u32 %0, 1, 0, p;\n\t}"
             : "=r"(done)
-            : "r"(b), "r"(0u)
+            : "r"(b), "r"(phase)
             : "memory");
         if (done) break;
     }
-    // every thread takes the same decision
-    return __syncthreads_or(done == 0) == 0;
+    return __syncthreads_or(done == 0) == 0;   // every thread takes the same decision
 }
 
-__device__ __forceinline__ void plain_load_tile(const FusedParams& p, uint8_t* dst, int xs, int ys,
-                                                int R)
+__device__ __forceinline__ void plain_load_tile(const ImageJob& J, uint8_t* dst, int xs, int ys, int R)
 {
-    const int total = R * p.Cb;
+    const int total = R * J.Cb;
     for (int i = threadIdx.x; i < total; i += blockDim.x) {
-        const int t = i / p.Cb, c = i - t * p.Cb;
+        const int t = i / J.Cb, c = i - t * J.Cb;
         const int Y = ys + t, X = xs + c;
         uint8_t v = 0;
-        if (Y >= 0 && Y < p.H && X >= 0 && X < p.W) v = p.img[(long long)Y * p.pitch + X];
+        if (Y >= 0 && Y < J.H && X >= 0 && X < J.W) v = J.img[(long long)Y * J.pitch + X];
         dst[i] = v;
     }
 }
@@ -193,49 +228,59 @@ __device__ __forceinline__ void warp_sparse_row(uint8_t* row, int Cb, int levels
 }
 
 // ---------------------------------------------------------------------------
-// The fused kernel.
+// One output tile (tx, ty) of image J.  smem must hold fused_smem_bytes();
+// its first 8 bytes are the CTA's mbarrier (initialised by the caller when
+// J.use_tma).  Returns false if the tile copy timed out (status already set).
 // ---------------------------------------------------------------------------
-template <int N>
-__global__ void __launch_bounds__(kThreads, 2)
-    fabf_fused_kernel(const __grid_constant__ CUtensorMap tmap, const FusedParams p)
+template <int N, int PREC>
+__device__ __forceinline__ bool fabf_tile(const CUtensorMap* tmap, const ImageJob& J, int tx, int ty,
+                                          uint8_t* smem, uint32_t& phase, unsigned* status,
+                                          unsigned long long* n_fallback, const DebugPlanes& dbg)
 {
+    // pixels recomputed on the FP64 path by the binary32 forms' guard: the
+    // word after the fallback counter
+    unsigned long long* redo_count = n_fallback ? n_fallback + 1 : nullptr;
     constexpr int K = N < 1 ? 1 : N;           // power sums kept: k = 1..K
     constexpr int n32 = K < 2 ? K : 2;         // k = 1, 2 in 32 bits
     constexpr int n64 = K > 2 ? K - 2 : 0;     // k = 3..K in 64 bits
-    extern __shared__ __align__(128) uint8_t smem[];
 
-    const int w = p.w, Cb = p.Cb, off = p.off;
-    const int R = kTileH + 2 * w;
-    const int x0 = blockIdx.x * kTileW, y0 = blockIdx.y * kTileH;
+    const int w = J.w, Cb = J.Cb, off = J.off, TH = J.TH;
+    const int R = TH + 2 * w;
+    const int x0 = tx * kTileW, y0 = ty * TH;
     const int xs = x0 - w - off;               // image column of tile column 0
     const int ys = y0 - w;                     // image row of tile row 0
 
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
     uint8_t* tile = smem + 128;
-    size_t tile_bytes = ((size_t)R * Cb + 127) & ~(size_t)127;
+    const size_t tile_bytes = ((size_t)R * Cb + 127) & ~(size_t)127;
     uint8_t* vmin = tile + tile_bytes;
     uint8_t* vmax = vmin + kChunk * Cb;
     uint32_t* v32 = reinterpret_cast<uint32_t*>(vmax + kChunk * Cb);    // [n32][kChunk][Cb]
-    size_t v32_bytes = (size_t)n32 * kChunk * Cb * 4;
-    uint64_t* v64 = reinterpret_cast<uint64_t*>(
-        reinterpret_cast<uint8_t*>(v32) + ((v32_bytes + 7) & ~(size_t)7));   // [n64][kChunk][Cb]
+    const size_t v32_bytes = (size_t)n32 * kChunk * Cb * 4;
+    uint64_t* v64 = reinterpret_cast<uint64_t*>(reinterpret_cast<uint8_t*>(v32) +
+                                                ((v32_bytes + 7) & ~(size_t)7));   // [n64][kChunk][Cb]
+    const size_t v_bytes = (size_t)kChunk * Cb * (2 + 4 * n32) + (size_t)kChunk * Cb * 8 * n64;
+    unsigned* redo_n = reinterpret_cast<unsigned*>(vmin + ((v_bytes + 15) & ~(size_t)15));
+    uint16_t* redo_list = reinterpret_cast<uint16_t*>(reinterpret_cast<uint8_t*>(redo_n) + 16);
 
     // 1. Stage tile + halo.
-    if (p.use_tma) {
-        if (!tma_load_tile(&tmap, tile, bar, xs, ys, (uint32_t)(R * Cb))) {
-            if (threadIdx.x == 0 && p.status) atomicOr(p.status, kStatusTimeout);
-            return;
+    if (J.use_tma) {
+        const bool ok = tma_load_tile(tmap, tile, bar, xs, ys, (uint32_t)(R * Cb), phase);
+        phase ^= 1u;
+        if (!ok) {
+            if (threadIdx.x == 0 && status) atomicOr(status, kStatusTimeout);
+            return false;
         }
     } else {
-        plain_load_tile(p, tile, xs, ys, R);
+        plain_load_tile(J, tile, xs, ys, R);
         __syncthreads();
     }
 
     const int rowlo = ys < 0 ? -ys : 0;                           // first in-image tile row
-    const int rowhi = min(R - 1, p.H - 1 - ys);                    // last in-image tile row
+    const int rowhi = min(R - 1, J.H - 1 - ys);                    // last in-image tile row
     const int c = threadIdx.x;                                     // vertical phase column
     const int X = xs + c;
-    const bool col_in = (c < Cb) && X >= 0 && X < p.W;
+    const bool col_in = (c < Cb) && X >= 0 && X < J.W;
 
     // Running vertical sums for column c, initialised for output row 0.
     uint32_t s32[n32 > 0 ? n32 : 1];
@@ -262,9 +307,10 @@ __global__ void __launch_bounds__(kThreads, 2)
     while ((2 << levels) <= 2 * w + 1) ++levels;                   // floor(log2(2w+1))
     const int span = 1 << levels;
 
-    for (int r0 = 0; r0 < kTileH; r0 += kChunk) {
-        if (y0 + r0 >= p.H) break;
+    for (int r0 = 0; r0 < TH; r0 += kChunk) {
+        if (y0 + r0 >= J.H) break;                                 // uniform per CTA
         // 2. Vertical phase for output rows r0 .. r0+7.
+        if (threadIdx.x == 0) *redo_n = 0u;
         if (c < Cb) {
             if (col_in) {
                 // common core of the 8 windows [r, r + 2w], r = r0..r0+7
@@ -340,97 +386,217 @@ __global__ void __launch_bounds__(kThreads, 2)
         __syncthreads();
 
         // 3. Horizontal phase: warp `warp` owns chunk row `warp`.
+        // Window statistics of the pixel at chunk row rr, tile column x (rows
+        // of the chunk are prefix sums / sparse-table levels by now).
+        auto stats = [&](int rr, int x, int& alpha, int& beta, int64_t (&m)[K + 1], int& fi) {
+            const int Y = y0 + r0 + rr, Xo = x0 + x;
+            const int a = x + off, b = a + 2 * w;          // tile columns of the window
+            const uint8_t* rmin = vmin + rr * Cb;
+            const uint8_t* rmax = vmax + rr * Cb;
+            alpha = min(rmin[a], rmin[b - span + 1]);
+            beta = max(rmax[a], rmax[b - span + 1]);
+            const int ry0 = max(Y - w, 0), ry1 = min(Y + w, J.H - 1);
+            const int rx0 = max(Xo - w, 0), rx1 = min(Xo + w, J.W - 1);
+            m[0] = (int64_t)(ry1 - ry0 + 1) * (rx1 - rx0 + 1);
+#pragma unroll
+            for (int k = 0; k < n32; ++k) {
+                const uint32_t* P = v32 + (k * kChunk + rr) * Cb;
+                m[1 + k] = (int64_t)(uint32_t)(P[b] - (a > 0 ? P[a - 1] : 0u));
+            }
+#pragma unroll
+            for (int k = 0; k < n64; ++k) {
+                const uint64_t* P = v64 + (k * kChunk + rr) * Cb;
+                m[3 + k] = (int64_t)(P[b] - (a > 0 ? P[a - 1] : 0ull));
+            }
+            fi = tile[(r0 + rr + w) * Cb + a + w];
+        };
+        auto store = [&](long long pix, double g) {
+            if (J.out_f64) static_cast<double*>(J.out)[pix] = g;
+            else static_cast<float*>(J.out)[pix] = (float)g;
+        };
         {
             const int rr = warp;
-            const int r = r0 + rr;
-            const int Y = y0 + r;
+            const int Y = y0 + r0 + rr;
 #pragma unroll
             for (int k = 0; k < n32; ++k) warp_prefix_row<uint32_t>(v32 + (k * kChunk + rr) * Cb, Cb, lane);
 #pragma unroll
             for (int k = 0; k < n64; ++k) warp_prefix_row<uint64_t>(v64 + (k * kChunk + rr) * Cb, Cb, lane);
             warp_sparse_row<true>(vmin + rr * Cb, Cb, levels, lane);
             warp_sparse_row<false>(vmax + rr * Cb, Cb, levels, lane);
-            if (Y < p.H) {
-                const int ry0 = max(Y - w, 0), ry1 = min(Y + w, p.H - 1);
+            if (Y < J.H) {
 #pragma unroll
                 for (int h = 0; h < kTileW / 32; ++h) {
                     const int x = lane + 32 * h;
                     const int Xo = x0 + x;
-                    if (Xo >= p.W) continue;
-                    const int a = x + off, b = a + 2 * w;    // tile columns of the window
-                    const uint8_t* rmin = vmin + rr * Cb;
-                    const uint8_t* rmax = vmax + rr * Cb;
-                    const int alpha = min(rmin[a], rmin[b - span + 1]);
-                    const int beta = max(rmax[a], rmax[b - span + 1]);
+                    if (Xo >= J.W) continue;
+                    int alpha, beta, fi;
                     int64_t m[K + 1];
-                    const int rx0 = max(Xo - w, 0), rx1 = min(Xo + w, p.W - 1);
-                    m[0] = (int64_t)(ry1 - ry0 + 1) * (rx1 - rx0 + 1);
-#pragma unroll
-                    for (int k = 0; k < n32; ++k) {
-                        const uint32_t* P = v32 + (k * kChunk + rr) * Cb;
-                        m[1 + k] = (int64_t)(uint32_t)(P[b] - (a > 0 ? P[a - 1] : 0u));
-                    }
-#pragma unroll
-                    for (int k = 0; k < n64; ++k) {
-                        const uint64_t* P = v64 + (k * kChunk + rr) * Cb;
-                        m[3 + k] = (int64_t)(P[b] - (a > 0 ? P[a - 1] : 0ull));
-                    }
-                    const int fi = tile[(r + w) * Cb + a + w];
-                    const long long pix = (long long)Y * p.W + Xo;
-                    const float th = p.theta[pix], sg = p.sigma[pix];
+                    stats(rr, x, alpha, beta, m, fi);
+                    const long long pix = (long long)Y * J.W + Xo;
+                    const float th = J.theta[pix], sg = J.sigma[pix];
                     double g;
                     int fb = 0;
                     PixelTrace tr;
-                    PixelTrace* trp = p.dbg.mu ? &tr : nullptr;
+                    PixelTrace* trp = (PREC == kPrecFP64 && dbg.mu) ? &tr : nullptr;
                     if (!(sg > 0.0f) || !isfinite(sg) || !isfinite(th)) {
                         g = __longlong_as_double(0x7ff8000000000000LL);
-                        if (p.status) atomicOr(p.status, kStatusBadInput);
+                        if (status) atomicOr(status, kStatusBadInput);
                         trp = nullptr;
                     } else {
-                        g = fabf_pixel_fp64<N>(c_ainv, alpha, beta, fi, m, th, sg, fb, trp);
-                        if (fb && p.n_fallback) atomicAdd(p.n_fallback, 1ull);
+                        if constexpr (PREC == kPrecFP64) {
+                            g = fabf_pixel_fp64<N>(c_ainv, alpha, beta, fi, m, th, sg, fb, trp);
+                        } else {
+                            bool redo = false;
+                            if constexpr (PREC == kPrecFP64Fit)
+                                g = (double)fabf_pixel_fp64fit<N>(c_ainv, alpha, beta, fi, m, th, sg, fb, redo);
+                            else
+                                g = (double)fabf_pixel_cfp32<N>(c_ainv_split, alpha, beta, fi, m, th, sg, fb, redo);
+                            if (redo) {   // binary32 not accurate enough here: queue for the FP64 pass
+                                const unsigned slot = atomicAdd(redo_n, 1u);
+                                redo_list[slot] = (uint16_t)((rr << 8) | x);
+                                continue;
+                            }
+                        }
+                        if (fb && n_fallback) atomicAdd(n_fallback, 1ull);
                     }
-                    if (p.out_f64) static_cast<double*>(p.out)[pix] = g;
-                    else static_cast<float*>(p.out)[pix] = (float)g;
-                    if (p.dbg.alpha) {
-                        const long long plane = (long long)p.H * p.W;
-                        p.dbg.alpha[pix] = (uint8_t)alpha;
-                        p.dbg.beta[pix] = (uint8_t)beta;
-                        if (p.dbg.m)
-                            for (int k = 0; k <= N; ++k) p.dbg.m[k * plane + pix] = m[k];
-                        if (p.dbg.flags) p.dbg.flags[pix] = (alpha == beta ? 1 : 0) | (fb ? 2 : 0);
+                    store(pix, g);
+                    if (dbg.alpha) {
+                        const long long plane = (long long)J.H * J.W;
+                        dbg.alpha[pix] = (uint8_t)alpha;
+                        dbg.beta[pix] = (uint8_t)beta;
+                        if (dbg.m)
+                            for (int k = 0; k <= N; ++k) dbg.m[k * plane + pix] = m[k];
+                        if (dbg.flags) dbg.flags[pix] = (alpha == beta ? 1 : 0) | (fb ? 2 : 0);
                         if (trp && alpha != beta) {
                             for (int k = 0; k <= N; ++k) {
-                                p.dbg.M[k * plane + pix] = tr.M[k];
-                                p.dbg.mu[k * plane + pix] = tr.mu[k];
-                                p.dbg.c[k * plane + pix] = tr.c[k];
+                                dbg.M[k * plane + pix] = tr.M[k];
+                                dbg.mu[k * plane + pix] = tr.mu[k];
+                                dbg.c[k * plane + pix] = tr.c[k];
                             }
-                            for (int k = 0; k <= N + 1; ++k) p.dbg.I[k * plane + pix] = tr.I[k];
-                            p.dbg.t0lam[pix] = tr.t0;
-                            p.dbg.t0lam[plane + pix] = tr.lam;
-                            p.dbg.T[pix] = tr.T1;
-                            p.dbg.T[plane + pix] = tr.T2;
+                            for (int k = 0; k <= N + 1; ++k) dbg.I[k * plane + pix] = tr.I[k];
+                            dbg.t0lam[pix] = tr.t0;
+                            dbg.t0lam[plane + pix] = tr.lam;
+                            dbg.T[pix] = tr.T1;
+                            dbg.T[plane + pix] = tr.T2;
                         }
                     }
                 }
             }
         }
+        if constexpr (PREC != kPrecFP64) {
+            // 4. The queued pixels on the FP64 path, packed into full warps.
+            __syncthreads();
+            const unsigned nr = *redo_n;
+            for (unsigned i = threadIdx.x; i < nr; i += blockDim.x) {
+                const int e = redo_list[i];
+                const int rr = e >> 8, x = e & 255;
+                int alpha, beta, fi, fb = 0;
+                int64_t m[K + 1];
+                stats(rr, x, alpha, beta, m, fi);
+                const long long pix = (long long)(y0 + r0 + rr) * J.W + (x0 + x);
+                const double g = fabf_pixel_fp64<N>(c_ainv, alpha, beta, fi, m, J.theta[pix], J.sigma[pix], fb,
+                                                    nullptr);
+                store(pix, g);
+                if (fb && n_fallback) atomicAdd(n_fallback, 1ull);
+                if (redo_count) atomicAdd(redo_count, 1ull);
+            }
+        }
         __syncthreads();
+    }
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// Single image: one tile per CTA, grid (tiles_x, tiles_y).
+// ---------------------------------------------------------------------------
+template <int N, int PREC>
+__global__ void __launch_bounds__(kThreads, 2)
+    fabf_fused_kernel(const __grid_constant__ CUtensorMap tmap, const FusedParams p)
+{
+    extern __shared__ __align__(128) uint8_t smem[];
+    uint32_t phase = 0;
+    if (p.job.use_tma) mbar_init(reinterpret_cast<uint64_t*>(smem));
+    fabf_tile<N, PREC>(&tmap, p.job, blockIdx.x, blockIdx.y, smem, phase, p.status, p.n_fallback, p.dbg);
+}
+
+// ---------------------------------------------------------------------------
+// Batch: persistent CTAs pop tiles of many images from a device counter.
+// Tiles are numbered image by image (jobs sorted by tile_begin); a CTA finds
+// its tile's image by binary search and dispatches on that image's N.
+// ---------------------------------------------------------------------------
+template <int PREC>
+__device__ __forceinline__ bool batch_dispatch(const BatchParams& p, const ImageJob& J, int j, int tx, int ty,
+                                               uint8_t* smem, uint32_t& phase)
+{
+    const DebugPlanes none{};
+    const CUtensorMap* tm = p.tmaps + j;
+    switch (J.N) {
+    case 0: return fabf_tile<0, PREC>(tm, J, tx, ty, smem, phase, p.status, p.n_fallback, none);
+    case 1: return fabf_tile<1, PREC>(tm, J, tx, ty, smem, phase, p.status, p.n_fallback, none);
+    case 2: return fabf_tile<2, PREC>(tm, J, tx, ty, smem, phase, p.status, p.n_fallback, none);
+    case 3: return fabf_tile<3, PREC>(tm, J, tx, ty, smem, phase, p.status, p.n_fallback, none);
+    case 4: return fabf_tile<4, PREC>(tm, J, tx, ty, smem, phase, p.status, p.n_fallback, none);
+    case 5: return fabf_tile<5, PREC>(tm, J, tx, ty, smem, phase, p.status, p.n_fallback, none);
+    default: return fabf_tile<6, PREC>(tm, J, tx, ty, smem, phase, p.status, p.n_fallback, none);
+    }
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(kThreads, 2) fabf_batch_kernel(const BatchParams p)
+{
+    extern __shared__ __align__(128) uint8_t smem[];
+    __shared__ long long s_tile;
+    __shared__ int s_job;
+    uint32_t phase = 0;
+    mbar_init(reinterpret_cast<uint64_t*>(smem));
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const long long t = (long long)atomicAdd(p.next_tile, 1ull);
+            int j = -1;
+            if (t < p.total_tiles) {
+                int lo = 0, hi = p.njobs - 1;
+                while (lo < hi) {          // last job with tile_begin <= t
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (p.jobs[mid].tile_begin <= t) lo = mid;
+                    else hi = mid - 1;
+                }
+                j = lo;
+            }
+            s_tile = t;
+            s_job = j;
+        }
+        __syncthreads();
+        const int j = s_job;
+        const long long t = s_tile;
+        __syncthreads();                   // s_tile / s_job are rewritten next round
+        if (j < 0) break;
+        const ImageJob J = p.jobs[j];
+        const long long local = t - J.tile_begin;
+        const int ty = (int)(local / J.tiles_x), tx = (int)(local - (long long)ty * J.tiles_x);
+        if (!batch_dispatch<PREC>(p, J, j, tx, ty, smem, phase)) break;
     }
 }
 
 // ---------------------------------------------------------------------------
-// Test kernel: the integral engine alone, I_0..I_K for n (lambda, t0) pairs.
+// Test kernel: the integral engine alone, I_0..I_K for n (lambda, t0) pairs,
+// in binary64 (fp32 == 0) or binary32.
 // ---------------------------------------------------------------------------
 template <int K>
-__global__ void integrals_kernel(const double* lam, const double* t0, long long n, double* out)
+__global__ void integrals_kernel(const double* lam, const double* t0, long long n, int fp32, double* out)
 {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;   // whole warps past the end exit together
-    double I[K + 1];
-    integrals_fp64<K>(lam[i], t0[i], I);
+    if (i >= n) return;
+    if (fp32) {
+        float I[K + 1];
+        integrals_fp32<K>((float)lam[i], (float)t0[i], I);
 #pragma unroll
-    for (int k = 0; k <= K; ++k) out[i * (K + 1) + k] = I[k];
+        for (int k = 0; k <= K; ++k) out[i * (K + 1) + k] = (double)I[k];
+    } else {
+        double I[K + 1];
+        integrals_fp64<K>(lam[i], t0[i], I);
+#pragma unroll
+        for (int k = 0; k <= K; ++k) out[i * (K + 1) + k] = I[k];
+    }
 }
 
 // ---------------------------------------------------------------------------

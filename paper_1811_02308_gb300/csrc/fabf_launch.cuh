@@ -1,0 +1,58 @@
+// Kernel launch helpers, instantiated once per precision in
+// fabf_inst_fp64.cu, fabf_inst_fp64fit.cu and fabf_inst_cfp32.cu (separate
+// translation units so that nvcc compiles them in parallel).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "fabf_kernels.cuh"
+
+namespace fabf {
+
+constexpr int kMaxDynSmem = 110 * 1024;   // >= fused_smem_bytes for every (w <= 40, N <= 6, TH <= 64)
+
+template <int N, int PREC>
+cudaError_t launch_fused_one(const CUtensorMap& tm, const FusedParams& p, dim3 grid, size_t smem, cudaStream_t s)
+{
+    static bool attr_set = false;
+    if (!attr_set) {
+        const cudaError_t e =
+            cudaFuncSetAttribute(fabf_fused_kernel<N, PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    fabf_fused_kernel<N, PREC><<<grid, kThreads, smem, s>>>(tm, p);
+    return cudaGetLastError();
+}
+
+template <int PREC>
+cudaError_t launch_fused_impl(int N, const CUtensorMap& tm, const FusedParams& p, dim3 grid, size_t smem,
+                              cudaStream_t s)
+{
+    switch (N) {
+    case 0: return launch_fused_one<0, PREC>(tm, p, grid, smem, s);
+    case 1: return launch_fused_one<1, PREC>(tm, p, grid, smem, s);
+    case 2: return launch_fused_one<2, PREC>(tm, p, grid, smem, s);
+    case 3: return launch_fused_one<3, PREC>(tm, p, grid, smem, s);
+    case 4: return launch_fused_one<4, PREC>(tm, p, grid, smem, s);
+    case 5: return launch_fused_one<5, PREC>(tm, p, grid, smem, s);
+    case 6: return launch_fused_one<6, PREC>(tm, p, grid, smem, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int PREC>
+cudaError_t launch_batch_impl(const BatchParams& p, int grid, size_t smem, cudaStream_t s)
+{
+    static bool attr_set = false;
+    if (!attr_set) {
+        const cudaError_t e =
+            cudaFuncSetAttribute(fabf_batch_kernel<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    fabf_batch_kernel<PREC><<<grid, kThreads, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace fabf

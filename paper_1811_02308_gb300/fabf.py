@@ -71,11 +71,15 @@ def load(path: str | None = None):
         "fabf_set_precision": ([vp, i], i),
         "fabf_filter": ([vp, vp, vp, vp, i, i, sz, i, i, vp, i, vp], i),
         "fabf_get_status": ([vp, vp, C.POINTER(i), C.POINTER(C.c_uint64)], i),
+        "fabf_get_status_ex": ([vp, vp, C.POINTER(i), C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)], i),
         "fabf_filter_batch": ([vp, C.POINTER(Request), i, vp], i),
         "fabf_serve_submit": ([vp, C.POINTER(Request), C.POINTER(C.c_uint64)], i),
         "fabf_serve_poll": ([vp, C.c_uint64, i, C.POINTER(i)], i),
         "fabf_status_str": ([i], C.c_char_p),
         "fabf_filter_noalloc": ([vp, vp, vp, i, i, sz, i, i, vp, i, vp, C.POINTER(C.c_uint64)], i),
+        "fabf_serve_stats": ([vp, C.POINTER(C.c_uint64), C.POINTER(i)], i),
+        "fabf_batch_stats": ([vp, C.POINTER(i), C.POINTER(i)], i),
+        "fabf_tile_rows": ([vp, i, i, i, C.POINTER(i)], i),
         "fabf_hilbert_inverse": ([i, vp], i),
         "fabf_fused_smem_bytes": ([i, i, C.POINTER(sz)], i),
         "fabf_debug_stages": ([vp, vp, vp, vp, i, i, sz, i, i] + [vp] * 11, i),
@@ -218,6 +222,17 @@ def fabf_get_status(ctx: Context, stream: int = 0):
     return st.value, nf.value
 
 
+def fabf_get_status_ex(ctx: Context, stream: int = 0):
+    """(status, n_fallback, n_fp64_redo) of the stream-ordered calls since the
+    last query."""
+    st = C.c_int(0)
+    nf = C.c_uint64(0)
+    nr = C.c_uint64(0)
+    _check(load().fabf_get_status_ex(ctx.handle, stream, C.byref(st), C.byref(nf), C.byref(nr)),
+           "fabf_get_status_ex")
+    return st.value, nf.value, nr.value
+
+
 def fabf_hilbert_inverse(N: int) -> np.ndarray:
     out = np.zeros((N + 1, N + 1), dtype=np.int64)
     _check(load().fabf_hilbert_inverse(int(N), out.ctypes.data), "fabf_hilbert_inverse")
@@ -307,3 +322,27 @@ def fabf_serve_poll(ctx: Context, ticket: int, timeout_us: int = 0):
     r = C.c_int(0)
     rc = load().fabf_serve_poll(ctx.handle, C.c_uint64(ticket), int(timeout_us), C.byref(r))
     return rc, r.value
+
+
+def fabf_serve_stats(ctx: Context):
+    """(device bytes held by admitted requests, requests still running)."""
+    b = C.c_uint64(0)
+    n = C.c_int(0)
+    _check(load().fabf_serve_stats(ctx.handle, C.byref(b), C.byref(n)), "fabf_serve_stats")
+    return b.value, n.value
+
+
+def fabf_batch_stats(ctx: Context):
+    """(CUDA graph captures, graph launches) of fabf_filter_batch so far."""
+    c = C.c_int(0)
+    n = C.c_int(0)
+    _check(load().fabf_batch_stats(ctx.handle, C.byref(c), C.byref(n)), "fabf_batch_stats")
+    return c.value, n.value
+
+
+def fabf_tile_rows(ctx: Context, w: int, N: int, precision: int = FABF_FP64) -> int:
+    """Output rows per tile used for (w, N, precision) (autotuned if enabled)."""
+    t = C.c_int(0)
+    _check(load().fabf_tile_rows(ctx.handle, int(w), int(N), int(precision), C.byref(t)),
+           "fabf_tile_rows")
+    return t.value
