@@ -409,14 +409,17 @@ __device__ __forceinline__ float fabf_pixel_fp64fit(const AinvTable& A, int alph
     const int d = beta - alpha;
     int64_t M[K + 1];
     shifted_moments<K>(alpha, m, M);
-    // mu_k = M_k (1/d)^k: one division; the few ulps this costs are far below
-    // what the binary32 stages keep.
-    const double rd = 1.0 / (double)d;
-    double mu[K + 1], p = 1.0;
+    // Scaled moments mu'_k = d^N mu_k = M_k d^(N-k): exact integers
+    // (<= m_0 255^6 < 2^63), so no division; the common factor d^N cancels
+    // in the ratio of Eq. (29).
+    double mu[K + 1];
+    {
+        int64_t dp = 1;
 #pragma unroll
-    for (int k = 0; k <= K; ++k) {
-        mu[k] = (double)M[k] * p;
-        p *= rd;
+        for (int k = K; k >= 0; --k) {
+            mu[k] = (double)(M[k] * dp);
+            dp *= d;
+        }
     }
     float c[N + 1];
 #pragma unroll
@@ -444,11 +447,26 @@ __device__ __forceinline__ void two_prod(float a, float b, float& p, float& e)
     e = fmaf(a, b, -p);
 }
 
-// int64 -> unevaluated sum hi + lo of two floats (exact to 2^-48 relative).
-__device__ __forceinline__ void ll_to_ff(int64_t v, float& hi, float& lo)
+// Exact float of an integer 0 <= x < 2^23 from its bits (2^23 + x has the
+// exponent of 2^23 and x as mantissa), without a conversion instruction.
+__device__ __forceinline__ float u23_to_float(uint32_t x)
 {
-    hi = __ll2float_rn(v);
-    lo = __ll2float_rn(v - __float2ll_rn(hi));
+    return __int_as_float(0x4B000000u | x) - 8388608.0f;
+}
+
+// 0 <= v < 2^63 as an unevaluated float-float hi + lo (error below 2^-47
+// relative): three exact 23-bit chunks summed with TwoSum.
+__device__ __forceinline__ void u63_to_ff(uint64_t v, float& hi, float& lo)
+{
+    const float f0 = u23_to_float((uint32_t)v & 0x7FFFFFu);
+    const float f1 = u23_to_float((uint32_t)(v >> 23) & 0x7FFFFFu) * 8388608.0f;       // x 2^23
+    const float f2 = u23_to_float((uint32_t)(v >> 46)) * 70368744177664.0f;            // x 2^46
+    float s1, e1, s2, e2;
+    two_sum(f2, f1, s1, e1);
+    two_sum(s1, f0, s2, e2);
+    const float t = e1 + e2;
+    hi = s2 + t;
+    lo = t - (hi - s2);
 }
 
 // FABF_CFP32: no binary64.  mu_k as float-float quotients of the exact
@@ -469,22 +487,17 @@ __device__ __forceinline__ float fabf_pixel_cfp32(const AinvSplitTable& A, int a
     const int d = beta - alpha;
     int64_t M[K + 1];
     shifted_moments<K>(alpha, m, M);
+    // Scaled moments mu'_k = M_k d^(N-k) (exact integers, see above) as
+    // float-float values, converted in 23-bit chunks without a 64-bit
+    // conversion instruction.
     float muh[K + 1], mul[K + 1];
-    int64_t dk = 1;
+    {
+        int64_t dp = 1;
 #pragma unroll
-    for (int k = 0; k <= K; ++k) {
-        float Mh, Ml, Dh, Dl;
-        ll_to_ff(M[k], Mh, Ml);
-        ll_to_ff(dk, Dh, Dl);
-        // (Mh + Ml) / (Dh + Dl) in float-float: q1 = Mh / Dh, then one
-        // correction from the exact residual.
-        const float q1 = Mh / Dh;
-        float ph, pl;
-        two_prod(q1, Dh, ph, pl);
-        const float r = (((Mh - ph) - pl) + Ml) - q1 * Dl;
-        muh[k] = q1;
-        mul[k] = r / Dh;
-        dk *= d;
+        for (int k = K; k >= 0; --k) {
+            u63_to_ff((uint64_t)(M[k] * dp), muh[k], mul[k]);
+            dp *= d;
+        }
     }
     float c[N + 1];
 #pragma unroll

@@ -509,8 +509,16 @@ __device__ __forceinline__ bool fabf_tile(const CUtensorMap* tmap, const ImageJo
 // ---------------------------------------------------------------------------
 // Single image: one tile per CTA, grid (tiles_x, tiles_y).
 // ---------------------------------------------------------------------------
+// Resident CTAs per SM the register budget is sized for: the FP64 form is
+// bound by the FP64 pipe (two CTAs saturate it); the binary32 forms are
+// latency bound and gain from a third CTA.
+template <int PREC>
+struct MinBlocks {
+    static constexpr int value = PREC == kPrecFP64 ? 2 : 3;
+};
+
 template <int N, int PREC>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, MinBlocks<PREC>::value)
     fabf_fused_kernel(const __grid_constant__ CUtensorMap tmap, const FusedParams p)
 {
     extern __shared__ __align__(128) uint8_t smem[];
@@ -542,7 +550,7 @@ __device__ __forceinline__ bool batch_dispatch(const BatchParams& p, const Image
 }
 
 template <int PREC>
-__global__ void __launch_bounds__(kThreads, 2) fabf_batch_kernel(const BatchParams p)
+__global__ void __launch_bounds__(kThreads, MinBlocks<PREC>::value) fabf_batch_kernel(const BatchParams p)
 {
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ long long s_tile;
