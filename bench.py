@@ -44,6 +44,7 @@ WORKLOAD = ("1920x1080 uint8 synthetic (200 blobs, 4 step edges, noise 10), box 
 # workload, from the ncu capture in profiles/ (scaled from 4096x4096 by pixel
 # count); set to None whenever the kernel changes until it is re-captured.
 NCU_TRAFFIC_BYTES = None
+NCU_TRAFFIC_BYTES_CFP32 = None
 SM_COUNT, SM_MAX_MHZ = 152, 2070.0
 FP64_FLOP_PER_SM_CLK = 4.0        # 2 DFMA per clock per SM (nominal 1.25 TFLOP/s FP64)
 FORM_NAMES = {0: "fp64", 1: "fp64fit_fp32rec", 2: "cfp32"}
@@ -60,6 +61,19 @@ def fp64_flops_per_pixel(N: int, form: int = 0) -> float:
     if form == 2:
         return 0.0
     return (N + 1) + 2 * (N + 1) ** 2 + 5 + 95 + 4 * N + 4 * (N + 1) + 3
+
+
+def fp32_flops_per_pixel(N: int) -> float:
+    """Algorithmic binary32 work of one non-flat pixel of the compensated
+    form (FMA = 2 flops, erf/exp = 20): float-float moments 20 (N+1),
+    compensated fit 14 (N+1)^2 (TwoProduct 3, TwoSum 6, cross terms 3,
+    accumulation 2), t0 and lambda 6, I_0 and I_1 with 2 erf + 2 exp 90,
+    recursion 4N, T1/T2 and the guard's |c||I| sums 8(N+1), estimate and
+    ratio 12."""
+    return 20 * (N + 1) + 14 * (N + 1) ** 2 + 6 + 90 + 4 * N + 8 * (N + 1) + 12
+
+
+FP32_FLOP_PER_SM_CLK = 256.0      # 128 FP32 lanes x FMA
 
 
 def dist_env():
@@ -336,6 +350,45 @@ def run_serve(R, prec, seconds, rate=200.0, seed=4000, pool_size=16):
             "eagain_retries": eagain[0], "budget_bytes": 16 << 30}
 
 
+def precision_report(n_sample=20000):
+    """Config 3: 4096x4096 (2000 blobs), w = 20, N in {5, 6}, sigma in
+    [5, 60]; every form's max / RMS error against the FP64 CPU oracle on a
+    random pixel sample, and PSNR of the whole image against the GPU FP64
+    brute-force filter."""
+    import torch
+
+    import oracle
+    from paper_1811_02308_gb300 import build, fabf, synth
+    build.build()
+    oracle.build()
+    f, th, s = synth.make_inputs(4096, 4096, synth.config_seed(3, 0), n_blobs=2000, zeta_range=None,
+                                 sigma_range=(5, 60))
+    d = [torch.from_numpy(a).cuda() for a in (f, th, s)]
+    rng = np.random.default_rng(3)
+    ys, xs = rng.integers(0, 4096, n_sample), rng.integers(0, 4096, n_sample)
+    rep = {"workload": "4096x4096 uint8 synthetic (2000 blobs), box w=20, theta=f, sigma in [5,60]",
+           "sample_pixels": n_sample}
+    with fabf.Context(device=0) as ctx:
+        bf = fabf.fabf_bruteforce(ctx, d[0], d[1], d[2], 20, use_f64=True).cpu().numpy()
+        for N in (5, 6):
+            ref, _ = oracle.fabf_pixels(f, th, s, 20, N, ys, xs)
+            row = {}
+            for prec in (0, 1, 2):
+                fabf.fabf_set_precision(ctx, prec)
+                g = fabf.fabf_filter(ctx, d[0], d[1], d[2], 20, N, out_is_f64=(prec == 0)).cpu().numpy()
+                st, nfb, nredo = fabf.fabf_get_status_ex(ctx)
+                e = np.abs(g[ys, xs].astype(np.float64) - ref)
+                row[FORM_NAMES[prec]] = {"max_abs_vs_oracle": float(e.max()),
+                                         "rms_vs_oracle": float(np.sqrt(np.mean(e * e))),
+                                         "max_rel_vs_oracle": float(np.max(e / np.maximum(np.abs(ref), 1))),
+                                         "psnr_vs_bruteforce_db": psnr(g, bf),
+                                         "fallback_frac": nfb / g.size, "fp64_redo_frac": nredo / g.size,
+                                         "status": st}
+            rep["N=%d" % N] = row
+    print(json.dumps({"precision_report": rep}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -350,11 +403,16 @@ def main():
     ap.add_argument("--profile-precision", type=int, default=0, choices=[0, 1, 2])
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--no-extra", action="store_true", help="skip the batch and serve legs")
+    ap.add_argument("--precision-report", action="store_true",
+                    help="4096x4096 w=20 N in {5,6}: each form's error against the FP64 oracle "
+                         "(sampled pixels) and PSNR against the GPU brute force; prints one JSON line")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return reference_arm(args)
+    if args.precision_report:
+        return precision_report()
 
     import torch
 
@@ -476,7 +534,14 @@ def main():
                     "peak_source": "nominal FP64 (152 SM x 4 flop/clk x 2070 MHz)",
                     "flops_per_pixel": fl, "kernel_ms": kern_ms, "form": FORM_NAMES[best]}
     else:
-        roofline = None
+        fl32 = fp32_flops_per_pixel(NDEG)
+        achieved = fl32 * npix / (kern_ms / 1e3) / 1e12
+        peak32 = SM_COUNT * SM_MAX_MHZ * 1e6 * FP32_FLOP_PER_SM_CLK / 1e12
+        roofline = {"bound": "alu", "pipe": "fp32", "achieved": achieved, "peak": peak32,
+                    "unit": "TFLOP/s", "frac": achieved / peak32,
+                    "traffic": args.traffic_bytes if args.traffic_bytes is not None else NCU_TRAFFIC_BYTES_CFP32,
+                    "peak_source": "nominal FP32 FMA (152 SM x 256 flop/clk x 2070 MHz)",
+                    "flops_per_pixel": fl32, "kernel_ms": kern_ms, "form": FORM_NAMES[best]}
 
     # ---- end to end through the C ABI with pinned host buffers --------------
     f, th, s = host[0]

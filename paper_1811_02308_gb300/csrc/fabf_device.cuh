@@ -57,12 +57,16 @@ __host__ __device__ constexpr AinvTable make_ainv_table()
 
 struct RecipTable {
     double v[64];   // v[j] = 1 / j (v[0] unused)
+    float f[64];    // the same in binary32
 };
 
 __host__ __device__ constexpr RecipTable make_recip_table()
 {
     RecipTable t{};
-    for (int j = 1; j < 64; ++j) t.v[j] = 1.0 / (double)j;
+    for (int j = 1; j < 64; ++j) {
+        t.v[j] = 1.0 / (double)j;
+        t.f[j] = (float)(1.0 / (double)j);
+    }
     return t;
 }
 
@@ -308,7 +312,10 @@ __device__ __forceinline__ void integrals_fp32(float lam, float t0, float (&I)[K
         if (t0 < 0.0f) E1s = expf(lam * (2.0f * t0 - 1.0f));
         else if (t0 > 1.0f) E1s = 1.0f;
         else E1s = expf(-lam * (1.0f - t0) * (1.0f - t0));
-        constexpr int Kp = 48;
+        // start index by lambda (binary32 needs ~1e-7, so fewer steps than
+        // the binary64 engine), made warp-uniform
+        int Kp = lam <= 0.1f ? 16 : (lam <= 0.3f ? 20 : (lam <= 0.7f ? 24 : (lam <= 1.0f ? 28 : 48)));
+        Kp = __reduce_max_sync(__activemask(), (unsigned)Kp);
         const float l2 = 2.0f * lam;
         const float q = l2 * (t0 - 1.0f);
         const float r1 = (float)(Kp + 2) + q, r0 = (float)(Kp + 1) + q;
@@ -316,7 +323,7 @@ __device__ __forceinline__ void integrals_fp32(float lam, float t0, float (&I)[K
         float lo = __fdividef(E1s, r0 > 1.0f ? r0 : (float)(Kp + 1));
 #pragma unroll 4
         for (int k = Kp + 1; k >= K + 2; --k) {
-            const float nx = fmaf(l2, fmaf(-t0, lo, hi), E1s) * (1.0f / (float)(k - 1));
+            const float nx = fmaf(l2, fmaf(-t0, lo, hi), E1s) * c_recip.f[k - 1];
             hi = lo;
             lo = nx;
         }
