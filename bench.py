@@ -43,8 +43,8 @@ WORKLOAD = ("1920x1080 uint8 synthetic (200 blobs, 4 step edges, noise 10), box 
 # DRAM bytes (read + write) per launch of the fused FP64 kernel on this
 # workload, from the ncu capture in profiles/ (scaled from 4096x4096 by pixel
 # count); set to None whenever the kernel changes until it is re-captured.
-NCU_TRAFFIC_BYTES = None
-NCU_TRAFFIC_BYTES_CFP32 = None
+NCU_TRAFFIC_BYTES = 31.0e6         # FP64 form kernel (profiles/)
+NCU_TRAFFIC_BYTES_CFP32 = 24.3e6   # compensated FP32 kernel (profiles/)
 SM_COUNT, SM_MAX_MHZ = 152, 2070.0
 FP64_FLOP_PER_SM_CLK = 4.0        # 2 DFMA per clock per SM (nominal 1.25 TFLOP/s FP64)
 FORM_NAMES = {0: "fp64", 1: "fp64fit_fp32rec", 2: "cfp32"}
@@ -74,6 +74,23 @@ def fp32_flops_per_pixel(N: int) -> float:
 
 
 FP32_FLOP_PER_SM_CLK = 256.0      # 128 FP32 lanes x FMA
+
+
+def max_over_ranks(ms: float, device) -> float:
+    """Timing of a replicated step: the slowest rank's milliseconds (the
+    whole job finishes when the last replica does)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(ms)
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(n_ranks: int, pixels_per_step: int, steps: int, max_ms: float) -> float:
+    """Whole-job Mpix/s: the pixels every rank filtered over the max-over-ranks time."""
+    return n_ranks * pixels_per_step * steps / (max_ms / 1e3) / 1e6
 
 
 def dist_env():
@@ -350,6 +367,46 @@ def run_serve(R, prec, seconds, rate=200.0, seed=4000, pool_size=16):
             "eagain_retries": eagain[0], "budget_bytes": 16 << 30}
 
 
+def sweep(args):
+    """Config 1: 1920x1080 (200 blobs), theta = f + zeta, sigma in [5, 60];
+    Mpix/s of every form for w in {5, 10, 20, 40} x N in {3, 4, 5, 6} (inputs
+    rotating over 8 slots), and the GPU brute-force filter (FP64 and FP32)
+    at each w."""
+    import torch
+
+    from paper_1811_02308_gb300 import build, fabf
+    build.build()
+    dev = torch.device("cuda", 0)
+    host = [make_inputs(H_, W_, 1000 + i, N_BLOBS) for i in range(4)]
+    d_in = [tuple(torch.from_numpy(a).to(dev) for a in h) for h in host]
+    outs = {0: [torch.empty((H_, W_), dtype=torch.float64, device=dev) for _ in range(8)],
+            1: [torch.empty((H_, W_), dtype=torch.float32, device=dev) for _ in range(8)]}
+    res = {}
+    with fabf.Context(device=0) as ctx:
+        R = Runner(torch, fabf, ctx, dev)
+        steps = max(20, args.steps // 4)
+        for w in (5, 10, 20, 40):
+            for N in (3, 4, 5, 6):
+                row = {}
+                for prec in (0, 1, 2):
+                    fabf.fabf_set_precision(ctx, prec)
+                    o = outs[0 if prec == 0 else 1]
+                    ms, _ = R.timed(lambda i: R.filt((*d_in[i % 4], o[i % 8]), w, N), steps, 3)
+                    row[FORM_NAMES[prec]] = H_ * W_ * steps / (ms / 1e3) / 1e6
+                res["w=%d,N=%d" % (w, N)] = row
+            fabf.fabf_set_precision(ctx, 0)
+            f0, th0, s0 = d_in[0]
+            bfo = torch.empty((H_, W_), dtype=torch.float64, device=dev)
+            for use64 in (True, False):
+                n = 2 if use64 else 10
+                ms, _ = R.timed(lambda i, u=use64: fabf.fabf_bruteforce(ctx, f0, th0, s0, w, out=bfo, use_f64=u,
+                                                                          stream=R.sh), n, 1)
+                res["bruteforce w=%d %s" % (w, "fp64" if use64 else "fp32")] = H_ * W_ * n / (ms / 1e3) / 1e6
+    print(json.dumps({"sweep_mpix_per_s": res, "workload": "1920x1080, theta=f+zeta, sigma in [5,60]"}),
+          flush=True)
+    return 0
+
+
 def precision_report(n_sample=20000):
     """Config 3: 4096x4096 (2000 blobs), w = 20, N in {5, 6}, sigma in
     [5, 60]; every form's max / RMS error against the FP64 CPU oracle on a
@@ -403,6 +460,9 @@ def main():
     ap.add_argument("--profile-precision", type=int, default=0, choices=[0, 1, 2])
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--no-extra", action="store_true", help="skip the batch and serve legs")
+    ap.add_argument("--sweep", action="store_true",
+                    help="1920x1080: every form for w in {5,10,20,40} x N in {3..6}, plus the GPU "
+                         "brute force per w; prints one JSON line")
     ap.add_argument("--precision-report", action="store_true",
                     help="4096x4096 w=20 N in {5,6}: each form's error against the FP64 oracle "
                          "(sampled pixels) and PSNR against the GPU brute force; prints one JSON line")
@@ -413,6 +473,8 @@ def main():
         return reference_arm(args)
     if args.precision_report:
         return precision_report()
+    if args.sweep:
+        return sweep(args)
 
     import torch
 
@@ -473,9 +535,7 @@ def main():
     if ws > 1:
         torch.distributed.barrier()
         for prec in forms:
-            t = torch.tensor([forms[prec]["total_ms"]], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            forms[prec]["total_ms"] = float(t.item())
+            forms[prec]["total_ms"] = max_over_ranks(forms[prec]["total_ms"], dev)
     npix = H_ * W_
 
     # accuracy of each form: against FP64 and against the GPU brute force
@@ -504,7 +564,7 @@ def main():
     form_rows = {}
     for prec, r in forms.items():
         n_calls = args.steps + args.warmup
-        row = {"value": ws * npix * args.steps / (r["total_ms"] / 1e3) / 1e6, "unit": "Mpix/s",
+        row = {"value": job_throughput(ws, npix, args.steps, r["total_ms"]), "unit": "Mpix/s",
                "kernel_ms": r["kernel_ms"], "status": r["status"],
                "fallback_frac": r["fallback"] / (n_calls * npix),
                "fp64_redo_frac": r["redo"] / (n_calls * npix)}
