@@ -36,9 +36,15 @@ def build(force: bool = False) -> str:
 
 def _load():
     global _lib
-    if _lib is not None:
-        return _lib
-    lib = C.CDLL(build())
+    if _lib is None:
+        _lib = load_library(build())
+    return _lib
+
+
+def load_library(path: str):
+    """Load an oracle shared library and declare its signatures (the tests
+    also load deliberately broken builds of the same source through this)."""
+    lib = C.CDLL(path)
     u8p = C.POINTER(C.c_uint8)
     f32p = C.POINTER(C.c_float)
     f64p = C.POINTER(C.c_double)
@@ -64,8 +70,25 @@ def _load():
                lib.oracle_fabf_pixels, lib.oracle_fabf_trace, lib.oracle_bruteforce,
                lib.oracle_bruteforce_pixels):
         fn.restype = C.c_int
-    _lib = lib
     return lib
+
+
+class use_library:
+    """Context manager: route this module's functions to another build of the
+    oracle (used only by the tests that plant mistakes)."""
+
+    def __init__(self, lib):
+        self.lib = lib
+
+    def __enter__(self):
+        global _lib
+        self.saved = _lib
+        _lib = self.lib
+        return self
+
+    def __exit__(self, *exc):
+        global _lib
+        _lib = self.saved
 
 
 def _ptr(a, t):

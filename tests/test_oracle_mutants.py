@@ -1,0 +1,233 @@
+"""The oracle's pins catch plausible mistakes (no GPU).
+
+Each case plants one mistake in a temporary copy of oracle/fabf_oracle.c
+(a dropped factor, a flipped sign, an off-by-one index, a swapped operand,
+a wrong bound), builds it, routes the oracle wrapper to that build and runs
+a quick battery of the same checks as tests/test_oracle_pins.py.  Every
+mutant must fail at least one check; the unmodified source must pass them
+all.  The planted mistakes live only in this file and in temporary builds.
+"""
+import math
+import os
+import subprocess
+import tempfile
+from fractions import Fraction
+
+import mpmath as mp
+import numpy as np
+import pytest
+import scipy.linalg
+import scipy.stats
+
+import oracle
+from paper_1811_02308_gb300 import synth
+
+SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "oracle",
+                   "fabf_oracle.c")
+
+MUTANTS = {
+    "window end off by one": ("*y1 = y + w > H - 1 ? H - 1 : y + w;",
+                              "*y1 = y + w > H - 1 ? H - 1 : y + w - 1;"),
+    "min with the wrong comparison": ("if (v < a) a = v;", "if (v > a) a = v;"),
+    "power index shifted": ("{ m[k] += p; p *= v; }", "{ p *= v; m[k] += p; }"),
+    "shift by alpha - 1": ("- alpha, p = 1;", "- alpha + 1, p = 1;"),
+    "Hilbert inverse sign": ("((m + n) % 2 == 0) ? 1 : -1", "((m + n) % 2 == 1) ? 1 : -1"),
+    "Hilbert inverse binomials transposed": (
+        "binom(N + m, N + 1 - n) * binom(N + n, N + 1 - m)",
+        "binom(N + m, N + 1 - m) * binom(N + n, N + 1 - n)"),
+    "Gauss-Legendre weight doubled": ("wt[i] = 1 / ((1 - x * x) * dp * dp);",
+                                      "wt[i] = 2 / ((1 - x * x) * dp * dp);"),
+    "erfc branch sign": ("diff = erfcf128(v) - erfcf128(u);", "diff = erfcf128(u) - erfcf128(v);"),
+    "I_0 missing 1/2": ("I[0] = sqrtf128(pi / lam) / 2 * diff;", "I[0] = sqrtf128(pi / lam) * diff;"),
+    "I_1 sign": ("(E0 - E1) / (2 * lam)", "(E1 - E0) / (2 * lam)"),
+    "recursion index": ("((q128)(k - 1)) / (2 * lam)", "((q128)(k)) / (2 * lam)"),
+    "recursion boundary sign": ("I[k - 2] - E1 / (2 * lam);", "I[k - 2] + E1 / (2 * lam);"),
+    "E_1 square dropped": ("expf128(-lam * (1 - t0) * (1 - t0))", "expf128(-lam * (1 - t0))"),
+    "scale sign": ("q128 s = expf128(lam * d * d);", "q128 s = expf128(-lam * d * d);"),
+    "mu divisor": ("dk *= d;", "dk *= d + 1;"),
+    "fit index": ("acc = fma((double)Ainv[n * (N + 1) + k], mu[k], acc);",
+                  "acc = fma((double)Ainv[n * (N + 1) + k], mu[n], acc);"),
+    "t0 from beta": ("- (double)alpha) / (double)d;", "- (double)beta) / (double)d;"),
+    "lambda without the 2": ("(double)(d * d) / (2.0 * s * s)", "(double)(d * d) / (s * s)"),
+    "T1 index": ("T1 = fma(c[k - 1], I[k], T1);", "T1 = fma(c[k - 1], I[k - 1], T1);"),
+    "ratio from beta": ("*g_out = (double)alpha + (double)d * F;", "*g_out = (double)beta + (double)d * F;"),
+    "fallback inverted": ("F = mu[1] / mu[0];", "F = mu[0] / mu[1];"),
+    "brute force kernel width": ("exp(-(v - th) * (v - th) / (2.0 * s * s))",
+                                 "exp(-(v - th) * (v - th) / (s * s))"),
+    "brute force numerator": ("num += phi * v;", "num += phi * th;"),
+    "flat branch skipped": ("if (alpha == beta) {", "if (alpha == beta && alpha < 0) {"),
+}
+
+# ---------------------------------------------------------------------------
+# quick battery (references computed once, independently of the oracle)
+# ---------------------------------------------------------------------------
+_REF = {}
+
+
+def _refs():
+    if _REF:
+        return _REF
+    mp.mp.dps = 40
+    pts = [(3e-5, 0.4), (0.02, -2.0), (0.3, 0.6), (2.0, 1.3), (40.0, 0.2), (40.0, -0.3)]
+    ints = {}
+    for lam, t0 in pts:
+        L, T = mp.mpf(lam), mp.mpf(t0)
+        d = -T if T < 0 else (T - 1 if T > 1 else mp.mpf(0))
+        ints[(lam, t0)] = [float(mp.quad(lambda t: t ** k * mp.exp(-L * (t - T) ** 2 + L * d * d),
+                                         [0, min(max(T, 0), 1), 1])) for k in range(8)]
+    _REF["ints"] = ints
+    f, th, s = synth.make_inputs(11, 13, 5, n_blobs=3, zeta_range=(-20, 20), sigma_range=(5, 60))
+    _REF["tiny"] = (f, th, s)
+    return _REF
+
+
+def _window(f, y, x, w):
+    return f[max(0, y - w):y + w + 1, max(0, x - w):x + w + 1].astype(np.int64).ravel()
+
+
+def battery():
+    """Run every check; return the names of those that fail."""
+    R = _refs()
+    fails = []
+
+    def check(name, fn):
+        try:
+            fn()
+        except Exception:     # noqa: BLE001 - a broken build may raise anything
+            fails.append(name)
+
+    def hilbert():
+        for N in range(7):
+            ref = scipy.linalg.invhilbert(N + 1, exact=True)
+            assert oracle.hilbert_inverse(N).tolist() == [[int(v) for v in r] for r in ref]
+
+    def window_stats():
+        f, _, _ = R["tiny"]
+        a, b = oracle.bounds(f, 2)
+        m = oracle.moments(f, 2, 6)
+        M = oracle.shifted_moments(f, 2, 6)
+        for y in range(f.shape[0]):
+            for x in range(f.shape[1]):
+                v = _window(f, y, x, 2)
+                assert a[y, x] == v.min() and b[y, x] == v.max()
+                for k in range(7):
+                    assert m[k, y, x] == int((v ** k).sum())
+                    assert M[k, y, x] == int(((v - v.min()) ** k).sum())
+
+    def integrals():
+        for (lam, t0), ref in R["ints"].items():
+            got = oracle.integrals(lam, t0, 7)
+            assert np.allclose(got, ref, rtol=1e-13, atol=0)
+
+    def fit_moments():
+        f, th, s = R["tiny"]
+        for N in (2, 5):
+            Ainv = scipy.linalg.invhilbert(N + 1, exact=True)
+            for y, x in ((3, 4), (7, 9), (0, 0)):
+                tr = oracle.fabf_trace(f, th, s, 3, N, y, x)
+                if tr["flat"]:
+                    continue
+                d = tr["beta"] - tr["alpha"]
+                v = _window(f, y, x, 3)
+                assert tr["alpha"] == v.min() and tr["beta"] == v.max()
+                mu = [Fraction(int(((v - v.min()) ** k).sum()), d ** k) for k in range(N + 1)]
+                for n in range(N + 1):
+                    c_ex = sum(Fraction(int(Ainv[n][k])) * mu[k] for k in range(N + 1))
+                    scale = sum(abs(int(Ainv[n][k])) * mu[k] for k in range(N + 1))
+                    assert abs(Fraction(tr["c"][n]) - c_ex) <= Fraction(2 ** -48) * scale
+                assert tr["t0"] == pytest.approx((float(th[y, x]) - tr["alpha"]) / d, rel=1e-15)
+                assert tr["lam"] == pytest.approx(d * d / (2.0 * float(s[y, x]) ** 2), rel=1e-15)
+
+    def constant_image():
+        f = np.full((9, 12), 77, np.uint8)
+        g, _ = oracle.fabf(f, f.astype(np.float32) + 2, np.full(f.shape, 9.0, np.float32), 2, 4)
+        assert np.array_equal(g, f.astype(np.float64))
+
+    def box_mean_limit():
+        f, th, _ = R["tiny"]
+        s = np.full(f.shape, 1e9, np.float32)
+        g, _ = oracle.fabf(f, th, s, 2, 3)
+        for y in range(f.shape[0]):
+            for x in range(f.shape[1]):
+                v = _window(f, y, x, 2)
+                if v.min() != v.max():
+                    assert g[y, x] == pytest.approx(v.mean(), rel=1e-9)
+
+    def truncated_normal():
+        f, th, s = R["tiny"]
+        g, _ = oracle.fabf(f, th, s, 2, 0)
+        for y, x in ((2, 2), (5, 8), (10, 12)):
+            v = _window(f, y, x, 2)
+            al, d = int(v.min()), int(v.max() - v.min())
+            if d == 0:
+                continue
+            t0 = (float(th[y, x]) - al) / d
+            sd = float(s[y, x]) / d
+            mean = scipy.stats.truncnorm.mean(-t0 / sd, (1 - t0) / sd, loc=t0, scale=sd)
+            assert g[y, x] == pytest.approx(al + d * mean, rel=1e-10, abs=1e-9)
+
+    def bruteforce():
+        f, th, s = R["tiny"]
+        g = oracle.bruteforce(f, th, s, 2)
+        for y, x in ((1, 1), (6, 7), (10, 12)):
+            v = _window(f, y, x, 2).astype(np.float64)
+            wgt = np.exp(-(v - float(th[y, x])) ** 2 / (2 * float(s[y, x]) ** 2))
+            assert g[y, x] == pytest.approx((wgt * v).sum() / wgt.sum(), rel=1e-13)
+
+    def fallback_rule():
+        # pixels whose T2 <= 0 return the box mean alpha + d mu_1/mu_0 (R5)
+        f, th, s = synth.make_inputs(64, 80, 3, n_blobs=20, zeta_range=None, sigma_range=(10, 40))
+        _, nf = oracle.fabf(f, th, s, 5, 5)
+        assert nf > 0
+        found = 0
+        for y in range(64):
+            for x in range(80):
+                tr = oracle.fabf_trace(f, th, s, 5, 5, y, x)
+                if tr["fallback"]:
+                    v = _window(f, y, x, 5)
+                    assert tr["g"] == pytest.approx(v.mean(), rel=1e-12)
+                    found += 1
+                    if found == 2:
+                        return
+        assert found > 0
+
+    for name, fn in [("hilbert", hilbert), ("window", window_stats), ("integrals", integrals),
+                     ("fit", fit_moments), ("constant", constant_image), ("box mean", box_mean_limit),
+                     ("truncated normal", truncated_normal), ("bruteforce", bruteforce),
+                     ("fallback", fallback_rule)]:
+        check(name, fn)
+    return fails
+
+
+def _build(src_text, tmpdir, tag):
+    c = os.path.join(tmpdir, "m_%s.c" % tag)
+    so = os.path.join(tmpdir, "m_%s.so" % tag)
+    with open(c, "w") as fh:
+        fh.write(src_text)
+    subprocess.check_call(["gcc", "-O1", "-std=gnu11", "-ffp-contract=off", "-fPIC", "-shared", "-o", so, c,
+                           "-lm"])
+    return oracle.load_library(so)
+
+
+@pytest.fixture(scope="module")
+def source():
+    oracle.build()
+    return open(SRC).read()
+
+
+def test_unmodified_oracle_passes_the_battery(source):
+    with tempfile.TemporaryDirectory() as d:
+        lib = _build(source, d, "orig")
+        with oracle.use_library(lib):
+            assert battery() == []
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_mutant_is_caught(source, name):
+    old, new = MUTANTS[name]
+    assert source.count(old) == 1, "mutation site no longer unique: %r" % old
+    with tempfile.TemporaryDirectory() as d:
+        lib = _build(source.replace(old, new), d, "mut")
+        with oracle.use_library(lib):
+            fails = battery()
+    assert fails, "planted mistake '%s' was not caught by any pin" % name
