@@ -127,30 +127,30 @@ __device__ __forceinline__ void integrals_fp64(double lam, double t0, double (&I
         const double rl = rsqrt(lam);
         const double sl = lam * rl;                               // sqrt(lambda)
         const double h = 0.88622692545275801364908374167057 * rl; // 1/2 sqrt(pi/lambda)
-        double E0s, E1s, I0;
-        if (t0 < 0.0) {
-            E0s = 1.0;
-            E1s = exp(lam * (2.0 * t0 - 1.0));
-            I0 = h * (erfcx(-sl * t0) - E1s * erfcx(sl * (1.0 - t0)));
-        } else if (t0 > 1.0) {
-            E1s = 1.0;
-            E0s = exp(lam * (1.0 - 2.0 * t0));
-            I0 = h * (erfcx(sl * (t0 - 1.0)) - E0s * erfcx(sl * t0));
-        } else {
-            E0s = exp(-lam * t0 * t0);
-            E1s = exp(-lam * (1.0 - t0) * (1.0 - t0));
-            I0 = h * (erf(sl * (1.0 - t0)) + erf(sl * t0));
-        }
+        // One path for the three positions of t0 (no divergence): with d the
+        // distance from t0 to [0, 1], E0 and E1 carry the common factor
+        // exp(lambda d^2), and Eq. (31) is written with the scaled erfc,
+        //   inside  [0, 1]: erf(a) + erf(b) = 2 - E1 erfcx(a) - E0 erfcx(b),
+        //   outside [0, 1]: erfcx(sqrt(lambda) d) - E erfcx(sqrt(lambda)(1 + d)),
+        // a = sqrt(lambda)(1 - t0), b = sqrt(lambda) t0, E = E1 (t0 < 0) or E0.
+        const double d = t0 < 0.0 ? -t0 : (t0 > 1.0 ? t0 - 1.0 : 0.0);
+        const double E0s = exp(-lam * ((t0 - d) * (t0 + d)));
+        const double E1s = exp(-lam * ((1.0 - t0 - d) * (1.0 - t0 + d)));
+        const bool inside = d == 0.0;
+        const double S = inside ? 2.0 : 0.0;
+        const double ca = inside ? E1s : -1.0;
+        const double xa = inside ? sl * (1.0 - t0) : sl * d;
+        const double cb = inside ? E0s : (t0 < 0.0 ? E1s : E0s);
+        const double xb = inside ? sl * t0 : sl * (1.0 + d);
+        const double I0 = h * (S - ca * erfcx(xa) - cb * erfcx(xb));
         const double e1 = E1s * inv2l;
         I[0] = I0;
         I[1] = fma(t0, I0, (E0s - E1s) * inv2l);
 #pragma unroll
         for (int k = 2; k <= K; ++k) I[k] = fma(t0, I[k - 1], fma((double)(k - 1) * inv2l, I[k - 2], -e1));
     } else {
-        double E1s;
-        if (t0 < 0.0) E1s = exp(lam * (2.0 * t0 - 1.0));
-        else if (t0 > 1.0) E1s = 1.0;
-        else E1s = exp(-lam * (1.0 - t0) * (1.0 - t0));
+        const double d = t0 < 0.0 ? -t0 : (t0 > 1.0 ? t0 - 1.0 : 0.0);
+        const double E1s = exp(-lam * ((1.0 - t0 - d) * (1.0 - t0 + d)));   // exp(-lam (1-t0)^2 + lam d^2)
         int Kp = backward_start_index(lam);
         Kp = __reduce_max_sync(__activemask(), (unsigned)Kp);
         const double l2 = 2.0 * lam;
@@ -288,30 +288,25 @@ __device__ __forceinline__ void integrals_fp32(float lam, float t0, float (&I)[K
         const float rl = rsqrtf(lam);
         const float sl = lam * rl;
         const float h = 0.886226925452758f * rl;
-        float E0s, E1s, I0;
-        if (t0 < 0.0f) {
-            E0s = 1.0f;
-            E1s = expf(lam * (2.0f * t0 - 1.0f));
-            I0 = h * (erfcxf(-sl * t0) - E1s * erfcxf(sl * (1.0f - t0)));
-        } else if (t0 > 1.0f) {
-            E1s = 1.0f;
-            E0s = expf(lam * (1.0f - 2.0f * t0));
-            I0 = h * (erfcxf(sl * (t0 - 1.0f)) - E0s * erfcxf(sl * t0));
-        } else {
-            E0s = expf(-lam * t0 * t0);
-            E1s = expf(-lam * (1.0f - t0) * (1.0f - t0));
-            I0 = h * (erff(sl * (1.0f - t0)) + erff(sl * t0));
-        }
+        // branch-free over the position of t0, as in the binary64 engine
+        const float d = t0 < 0.0f ? -t0 : (t0 > 1.0f ? t0 - 1.0f : 0.0f);
+        const float E0s = expf(-lam * ((t0 - d) * (t0 + d)));
+        const float E1s = expf(-lam * ((1.0f - t0 - d) * (1.0f - t0 + d)));
+        const bool inside = d == 0.0f;
+        const float S = inside ? 2.0f : 0.0f;
+        const float ca = inside ? E1s : -1.0f;
+        const float xa = inside ? sl * (1.0f - t0) : sl * d;
+        const float cb = inside ? E0s : (t0 < 0.0f ? E1s : E0s);
+        const float xb = inside ? sl * t0 : sl * (1.0f + d);
+        const float I0 = h * (S - ca * erfcxf(xa) - cb * erfcxf(xb));
         const float e1 = E1s * inv2l;
         I[0] = I0;
         I[1] = fmaf(t0, I0, (E0s - E1s) * inv2l);
 #pragma unroll
         for (int k = 2; k <= K; ++k) I[k] = fmaf(t0, I[k - 1], fmaf((float)(k - 1) * inv2l, I[k - 2], -e1));
     } else {
-        float E1s;
-        if (t0 < 0.0f) E1s = expf(lam * (2.0f * t0 - 1.0f));
-        else if (t0 > 1.0f) E1s = 1.0f;
-        else E1s = expf(-lam * (1.0f - t0) * (1.0f - t0));
+        const float d = t0 < 0.0f ? -t0 : (t0 > 1.0f ? t0 - 1.0f : 0.0f);
+        const float E1s = expf(-lam * ((1.0f - t0 - d) * (1.0f - t0 + d)));
         // start index by lambda (binary32 needs ~1e-7, so fewer steps than
         // the binary64 engine), made warp-uniform
         int Kp = lam <= 0.1f ? 16 : (lam <= 0.3f ? 20 : (lam <= 0.7f ? 24 : (lam <= 1.0f ? 28 : 48)));

@@ -424,7 +424,9 @@ __device__ __forceinline__ bool fabf_tile(const CUtensorMap* tmap, const ImageJo
             warp_sparse_row<true>(vmin + rr * Cb, Cb, levels, lane);
             warp_sparse_row<false>(vmax + rr * Cb, Cb, levels, lane);
             if (Y < J.H) {
-#pragma unroll
+                // one copy of the per-pixel code for both pixels of the lane
+                // (keeps the hot loop small in the instruction cache)
+#pragma unroll 1
                 for (int h = 0; h < kTileW / 32; ++h) {
                     const int x = lane + 32 * h;
                     const int Xo = x0 + x;
