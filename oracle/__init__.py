@@ -65,10 +65,23 @@ def load_library(path: str):
     lib.oracle_bruteforce.argtypes = [u8p, f32p, f32p, I, I, L, I, f64p]
     lib.oracle_bruteforce_pixels.argtypes = [u8p, f32p, f32p, I, I, L, I, i32p, i32p, L,
                                              f64p]
+    u32p = C.POINTER(C.c_uint32)
+    u64p = C.POINTER(C.c_uint64)
+    lib.oracle_moments_sep.argtypes = [u8p, I, I, L, u32p, I, I, u64p]
+    lib.oracle_fabf_sep.argtypes = [u8p, f32p, f32p, I, I, L, u32p, I, I, f64p, C.POINTER(L)]
+    lib.oracle_fabf_sep_pixels.argtypes = [u8p, f32p, f32p, I, I, L, u32p, I, I, i32p, i32p, L,
+                                           f64p, C.POINTER(L)]
+    lib.oracle_fabf_sep_trace.argtypes = [u8p, f32p, f32p, I, I, L, u32p, I, I, I, I, i32p, u64p,
+                                          u64p, f64p, f64p, f64p, f64p, f64p, f64p, i32p]
+    lib.oracle_bruteforce_sep.argtypes = [u8p, f32p, f32p, I, I, L, u32p, I, f64p]
+    lib.oracle_bruteforce_sep_pixels.argtypes = [u8p, f32p, f32p, I, I, L, u32p, I, i32p, i32p,
+                                                 L, f64p]
     for fn in (lib.oracle_hilbert_inverse, lib.oracle_integrals, lib.oracle_bounds,
                lib.oracle_moments, lib.oracle_shifted_moments, lib.oracle_fabf,
                lib.oracle_fabf_pixels, lib.oracle_fabf_trace, lib.oracle_bruteforce,
-               lib.oracle_bruteforce_pixels):
+               lib.oracle_bruteforce_pixels, lib.oracle_moments_sep, lib.oracle_fabf_sep,
+               lib.oracle_fabf_sep_pixels, lib.oracle_fabf_sep_trace, lib.oracle_bruteforce_sep,
+               lib.oracle_bruteforce_sep_pixels):
         fn.restype = C.c_int
     return lib
 
@@ -250,3 +263,122 @@ def fabf_passes(f, theta, sigma, w, N, passes, sigma_decay=0.8):
             sg = (sg * np.float32(sigma_decay)).astype(np.float32)
         g, _ = fabf(f, th, sg, w, N)
     return g
+
+
+# ---------------------------------------------------------------------------
+# Separable spatial kernel omega(j) = g[jy + r] g[jx + r] on [-r, r]^2
+# (Eq. (4) for quantised Gaussian taps); taps are 2r+1 integers >= 0 with
+# g[r] >= 1 and sum <= 65535.
+# ---------------------------------------------------------------------------
+def _taps(taps):
+    t = np.ascontiguousarray(taps, dtype=np.uint32)
+    if t.ndim != 1 or len(t) % 2 != 1:
+        raise ValueError("taps must be a 1-D array of odd length 2r+1")
+    return t, len(t) // 2
+
+
+def _u128(words):
+    """(..., 2) uint64 (low, high) -> Python ints (object array)."""
+    lo = words[..., 0].astype(object)
+    hi = words[..., 1].astype(object)
+    return lo + (hi << 64)
+
+
+def moments_sep(f, taps, N):
+    """m_k = sum omega(j) f(i+j)^k (k = 0..N) as Python ints, object (N+1, H, W)."""
+    f = np.ascontiguousarray(f, dtype=np.uint8)
+    H, W = f.shape
+    t, r = _taps(taps)
+    m = np.zeros((N + 1, H, W, 2), np.uint64)
+    _check(_load().oracle_moments_sep(_ptr(f, C.c_uint8), H, W, W, _ptr(t, C.c_uint32), r, N,
+                                      _ptr(m, C.c_uint64)), "moments_sep")
+    return _u128(m)
+
+
+def fabf_sep(f, theta, sigma, taps, N):
+    """Algorithm 1 with the separable kernel -> (g_hat float64 (H, W), n_fallback)."""
+    f = np.ascontiguousarray(f, dtype=np.uint8)
+    H, W = f.shape
+    theta, sigma = _maps(theta, sigma)
+    t, r = _taps(taps)
+    out = np.zeros((H, W), np.float64)
+    nf = C.c_long(0)
+    _check(_load().oracle_fabf_sep(_ptr(f, C.c_uint8), _ptr(theta, C.c_float),
+                                   _ptr(sigma, C.c_float), H, W, W, _ptr(t, C.c_uint32), r, N,
+                                   _ptr(out, C.c_double), C.byref(nf)), "fabf_sep")
+    return out, nf.value
+
+
+def fabf_sep_pixels(f, theta, sigma, taps, N, ys, xs):
+    """Algorithm 1 with the separable kernel at pixels (ys[j], xs[j])."""
+    f = np.ascontiguousarray(f, dtype=np.uint8)
+    H, W = f.shape
+    theta, sigma = _maps(theta, sigma)
+    t, r = _taps(taps)
+    ys = np.ascontiguousarray(ys, dtype=np.int32)
+    xs = np.ascontiguousarray(xs, dtype=np.int32)
+    out = np.zeros(len(ys), np.float64)
+    nf = C.c_long(0)
+    _check(_load().oracle_fabf_sep_pixels(_ptr(f, C.c_uint8), _ptr(theta, C.c_float),
+                                          _ptr(sigma, C.c_float), H, W, W, _ptr(t, C.c_uint32),
+                                          r, N, _ptr(ys, C.c_int32), _ptr(xs, C.c_int32),
+                                          len(ys), _ptr(out, C.c_double), C.byref(nf)),
+           "fabf_sep_pixels")
+    return out, nf.value
+
+
+def fabf_sep_trace(f, theta, sigma, taps, N, y, x):
+    """Every intermediate with the separable kernel at one pixel (m, M as ints)."""
+    f = np.ascontiguousarray(f, dtype=np.uint8)
+    H, W = f.shape
+    theta, sigma = _maps(theta, sigma)
+    t, r = _taps(taps)
+    ab = np.zeros(2, np.int32)
+    m = np.zeros((N + 1, 2), np.uint64)
+    M = np.zeros((N + 1, 2), np.uint64)
+    mu = np.full(N + 1, np.nan)
+    c = np.full(N + 1, np.nan)
+    t0lam = np.full(2, np.nan)
+    I = np.full(N + 2, np.nan)
+    T = np.full(2, np.nan)
+    g = np.zeros(1)
+    fl = np.zeros(1, np.int32)
+    _check(_load().oracle_fabf_sep_trace(
+        _ptr(f, C.c_uint8), _ptr(theta, C.c_float), _ptr(sigma, C.c_float), H, W, W,
+        _ptr(t, C.c_uint32), r, N, int(y), int(x), _ptr(ab, C.c_int32), _ptr(m, C.c_uint64),
+        _ptr(M, C.c_uint64), _ptr(mu, C.c_double), _ptr(c, C.c_double),
+        _ptr(t0lam, C.c_double), _ptr(I, C.c_double), _ptr(T, C.c_double),
+        _ptr(g, C.c_double), _ptr(fl, C.c_int32)), "fabf_sep_trace")
+    flat = bool(fl[0] & 1)
+    return dict(alpha=int(ab[0]), beta=int(ab[1]), m=list(_u128(m)),
+                M=None if flat else list(_u128(M)), mu=mu, c=c, t0=t0lam[0], lam=t0lam[1],
+                I=I, T1=T[0], T2=T[1], g=g[0], flat=flat, fallback=bool(fl[0] & 2))
+
+
+def bruteforce_sep(f, theta, sigma, taps):
+    """Brute-force filter, Eqs. (1)-(3), with the separable kernel, float64 (H, W)."""
+    f = np.ascontiguousarray(f, dtype=np.uint8)
+    H, W = f.shape
+    theta, sigma = _maps(theta, sigma)
+    t, r = _taps(taps)
+    out = np.zeros((H, W), np.float64)
+    _check(_load().oracle_bruteforce_sep(_ptr(f, C.c_uint8), _ptr(theta, C.c_float),
+                                         _ptr(sigma, C.c_float), H, W, W, _ptr(t, C.c_uint32),
+                                         r, _ptr(out, C.c_double)), "bruteforce_sep")
+    return out
+
+
+def bruteforce_sep_pixels(f, theta, sigma, taps, ys, xs):
+    f = np.ascontiguousarray(f, dtype=np.uint8)
+    H, W = f.shape
+    theta, sigma = _maps(theta, sigma)
+    t, r = _taps(taps)
+    ys = np.ascontiguousarray(ys, dtype=np.int32)
+    xs = np.ascontiguousarray(xs, dtype=np.int32)
+    out = np.zeros(len(ys), np.float64)
+    _check(_load().oracle_bruteforce_sep_pixels(_ptr(f, C.c_uint8), _ptr(theta, C.c_float),
+                                                _ptr(sigma, C.c_float), H, W, W,
+                                                _ptr(t, C.c_uint32), r, _ptr(ys, C.c_int32),
+                                                _ptr(xs, C.c_int32), len(ys),
+                                                _ptr(out, C.c_double)), "bruteforce_sep_pixels")
+    return out

@@ -22,6 +22,9 @@
  *       lambda = (beta - alpha)^2 / (2 sigma^2)                Eq. (25)
  *       I_0 .. I_{N+1}                                         Eqs. (28), (30)-(32)
  *       g = alpha + (beta - alpha) T1 / T2                     Eq. (29)
+ *   - the same two with a separable integer spatial kernel omega = g x g on
+ *     [-r, r]^2 (the Gaussian of Eq. (4) when the taps are a quantised
+ *     Gaussian), moments summed exactly in 128-bit integers (end of file).
  *
  * Readings where the paper is silent (each is also listed in the design
  * notes of the repository):
@@ -248,6 +251,40 @@ int oracle_integrals(double lam, double t0, int K, double* I)
 /* Algorithm 1 for one pixel                                           */
 /* ------------------------------------------------------------------ */
 
+/* Algorithm 1 from the shifted-and-scaled moments mu_0..mu_max(N,1) on: the
+ * fit (Eq. (19), fused multiply-adds over ascending k), t0 and lambda
+ * (Eq. (25)), the integrals (Eq. (28)), and the ratio (Eq. (29)) with the
+ * reading R5 for a non-positive denominator.  Writes c[N+1], t0lam[2],
+ * I[N+2], T[2], *g and ORs bit1 into *flags on the fallback. */
+static void fabf_tail(int N, const int64_t* Ainv, int alpha, int d, const double* mu, double th,
+                      double s, double* g_out, double* c, double* t0lam, double* I, double* T,
+                      int* flags)
+{
+    for (int n = 0; n <= N; ++n) {
+        double acc = 0.0;
+        for (int k = 0; k <= N; ++k) acc = fma((double)Ainv[n * (N + 1) + k], mu[k], acc);
+        c[n] = acc;
+    }
+    const double t0 = (th - (double)alpha) / (double)d;
+    const double lam = (double)(d * d) / (2.0 * s * s);
+    oracle_integrals(lam, t0, N + 1, I);
+    double T1 = c[0] * I[1], T2 = c[0] * I[0];
+    for (int k = 2; k <= N + 1; ++k) {
+        T1 = fma(c[k - 1], I[k], T1);
+        T2 = fma(c[k - 1], I[k - 1], T2);
+    }
+    double F = T1 / T2;
+    if (!(T2 > 0.0) || !isfinite(F)) {
+        F = mu[1] / mu[0];                        /* R5 */
+        *flags |= 2;
+    }
+    *g_out = (double)alpha + (double)d * F;
+    t0lam[0] = t0;
+    t0lam[1] = lam;
+    T[0] = T1;
+    T[1] = T2;
+}
+
 /* Trace of every intermediate of Algorithm 1 at one pixel.  Arrays hold
  * N+1 entries (m, M, mu, c) or N+2 (I).  flags: bit0 flat (alpha == beta),
  * bit1 fallback R5 taken.  Any pointer may be NULL. */
@@ -272,7 +309,7 @@ static int fabf_pixel(const uint8_t* f, const float* theta, const float* sigma,
     }
     const int d = beta - alpha;
     int64_t M[ORACLE_NMAX + 2];
-    double mu[ORACLE_NMAX + 2], c[ORACLE_NMAX + 1], I[ORACLE_NMAX + 2];
+    double mu[ORACLE_NMAX + 2], c[ORACLE_NMAX + 1], I[ORACLE_NMAX + 2], t0lam[2], T[2];
     const int K = N < 1 ? 1 : N;     /* mu_1 is needed by R5 even for N = 0 */
     pixel_shifted_moments(f, H, W, pitch, w, K, alpha, y, x, M);
     int64_t dk = 1;
@@ -280,35 +317,14 @@ static int fabf_pixel(const uint8_t* f, const float* theta, const float* sigma,
         mu[k] = (double)M[k] / (double)dk;     /* Eq. (24), R2 */
         dk *= d;
     }
-    /* Eq. (19) and Algorithm 1: c = A^{-1} mu, summed over ascending k. */
-    for (int n = 0; n <= N; ++n) {
-        double acc = 0.0;
-        for (int k = 0; k <= N; ++k) acc = fma((double)Ainv[n * (N + 1) + k], mu[k], acc);
-        c[n] = acc;
-    }
-    /* Eq. (25) and Algorithm 1. */
-    const double s = (double)sigma[(long)y * W + x];
-    const double t0 = ((double)theta[(long)y * W + x] - (double)alpha) / (double)d;
-    const double lam = (double)(d * d) / (2.0 * s * s);
-    oracle_integrals(lam, t0, N + 1, I);
-    /* Eq. (29), accumulated in the order of Algorithm 1. */
-    double T1 = c[0] * I[1], T2 = c[0] * I[0];
-    for (int k = 2; k <= N + 1; ++k) {
-        T1 = fma(c[k - 1], I[k], T1);
-        T2 = fma(c[k - 1], I[k - 1], T2);
-    }
-    double F = T1 / T2;
-    if (!(T2 > 0.0) || !isfinite(F)) {
-        F = mu[1] / mu[0];                        /* R5 */
-        flags |= 2;
-    }
-    *g_out = (double)alpha + (double)d * F;
+    fabf_tail(N, Ainv, alpha, d, mu, (double)theta[(long)y * W + x], (double)sigma[(long)y * W + x],
+              g_out, c, &t0lam[0], I, &T[0], &flags);
     if (M_out) for (int k = 0; k <= N; ++k) M_out[k] = M[k];
     if (mu_out) for (int k = 0; k <= N; ++k) mu_out[k] = mu[k];
     if (c_out) for (int k = 0; k <= N; ++k) c_out[k] = c[k];
-    if (t0lam_out) { t0lam_out[0] = t0; t0lam_out[1] = lam; }
+    if (t0lam_out) { t0lam_out[0] = t0lam[0]; t0lam_out[1] = t0lam[1]; }
     if (I_out) for (int k = 0; k <= N + 1; ++k) I_out[k] = I[k];
-    if (T_out) { T_out[0] = T1; T_out[1] = T2; }
+    if (T_out) { T_out[0] = T[0]; T_out[1] = T[1]; }
     if (flags_out) *flags_out = flags;
     return 0;
 }
@@ -471,6 +487,244 @@ int oracle_bruteforce(const uint8_t* f, const float* theta, const float* sigma,
         for (int x = 0; x < W; ++x) { ys[x] = y; xs[x] = x; }
         rc = oracle_bruteforce_pixels(f, theta, sigma, H, W, pitch, w, ys, xs,
                                       W, out + (long)y * W);
+    }
+    free(ys);
+    free(xs);
+    return rc;
+}
+
+/* ------------------------------------------------------------------ */
+/* Separable spatial kernels (Eq. (4) and Sec. II: any spatial kernel) */
+/* ------------------------------------------------------------------ */
+/*
+ * The spatial kernel is omega(j) = g[jy + r] g[jx + r] on the window
+ * [-r, r]^2 (clipped to the image, R1), for integer taps g[0..2r] >= 0 with
+ * g[r] >= 1 and sum g <= 65535.  The pixel at (y + ty, x + tx) carries the
+ * weight g[ty + r] g[tx + r].  A quantised Gaussian, g[t] = round(G exp(-(t -
+ * r)^2 / (2 rho^2))) with r = ceil(3 rho), is Eq. (4) with the paper's window
+ * [-3 rho, 3 rho]^2 up to the quantisation of the taps; any other separable
+ * kernel is allowed (the method works with any spatial filter).  Because the
+ * taps are integers, m_k and M_k are exact integers (< 2^81), summed here in
+ * unsigned 128-bit arithmetic.  alpha, beta are the min / max over the whole
+ * window, the support of omega (Eq. (8)); a tap of 0 only leaves its pixels
+ * out of the histogram, which stays supported on [alpha, beta].
+ */
+typedef unsigned __int128 u128;
+
+#define ORACLE_TAP_SUM_MAX 65535
+
+static int check_taps(const uint32_t* taps, int r)
+{
+    if (r < 1 || r > ORACLE_WMAX || !taps) return 1;
+    uint64_t s = 0;
+    for (int t = 0; t <= 2 * r; ++t) s += taps[t];
+    if (taps[r] < 1 || s > ORACLE_TAP_SUM_MAX) return 1;
+    return 0;
+}
+
+/* Eq. (17) with omega = g x g: m_k = sum omega(j) f(i + j)^k, k = 0..K. */
+static void pixel_moments_sep(const uint8_t* f, int H, int W, long pitch, const uint32_t* taps,
+                              int r, int K, int y, int x, u128* m)
+{
+    int y0, y1, x0, x1;
+    window_bounds(H, W, y, x, r, &y0, &y1, &x0, &x1);
+    for (int k = 0; k <= K; ++k) m[k] = 0;
+    for (int yy = y0; yy <= y1; ++yy)
+        for (int xx = x0; xx <= x1; ++xx) {
+            const u128 om = (u128)taps[yy - y + r] * taps[xx - x + r];
+            u128 v = f[(long)yy * pitch + xx], p = 1;
+            for (int k = 0; k <= K; ++k) { m[k] += om * p; p *= v; }
+        }
+}
+
+/* Eq. (24) with omega = g x g (R2): M_k = sum omega(j) (f(i + j) - alpha)^k. */
+static void pixel_shifted_moments_sep(const uint8_t* f, int H, int W, long pitch,
+                                      const uint32_t* taps, int r, int K, int alpha, int y,
+                                      int x, u128* M)
+{
+    int y0, y1, x0, x1;
+    window_bounds(H, W, y, x, r, &y0, &y1, &x0, &x1);
+    for (int k = 0; k <= K; ++k) M[k] = 0;
+    for (int yy = y0; yy <= y1; ++yy)
+        for (int xx = x0; xx <= x1; ++xx) {
+            const u128 om = (u128)taps[yy - y + r] * taps[xx - x + r];
+            u128 v = (u128)(f[(long)yy * pitch + xx] - alpha), p = 1;
+            for (int k = 0; k <= K; ++k) { M[k] += om * p; p *= v; }
+        }
+}
+
+/* Algorithm 1 at (y, x) with the separable kernel; same outputs as
+ * fabf_pixel, with m and M as (low, high) 64-bit word pairs. */
+static void fabf_pixel_sep(const uint8_t* f, const float* theta, const float* sigma, int H,
+                           int W, long pitch, const uint32_t* taps, int r, int N, int y, int x,
+                           const int64_t* Ainv, double* g_out, int* alpha_out, int* beta_out,
+                           uint64_t* m_out, uint64_t* M_out, double* mu_out, double* c_out,
+                           double* t0lam_out, double* I_out, double* T_out, int* flags_out)
+{
+    int alpha, beta, flags = 0;
+    pixel_bounds(f, H, W, pitch, r, y, x, &alpha, &beta);
+    if (alpha_out) *alpha_out = alpha;
+    if (beta_out) *beta_out = beta;
+    if (m_out) {
+        u128 m[ORACLE_NMAX + 1];
+        pixel_moments_sep(f, H, W, pitch, taps, r, N, y, x, m);
+        for (int k = 0; k <= N; ++k) {
+            m_out[2 * k] = (uint64_t)m[k];
+            m_out[2 * k + 1] = (uint64_t)(m[k] >> 64);
+        }
+    }
+    if (alpha == beta) {
+        *g_out = (double)f[(long)y * pitch + x];      /* Sec. II-A */
+        if (flags_out) *flags_out = 1;
+        return;
+    }
+    const int d = beta - alpha;
+    u128 M[ORACLE_NMAX + 2];
+    double mu[ORACLE_NMAX + 2], c[ORACLE_NMAX + 1], I[ORACLE_NMAX + 2], t0lam[2], T[2];
+    const int K = N < 1 ? 1 : N;
+    pixel_shifted_moments_sep(f, H, W, pitch, taps, r, K, alpha, y, x, M);
+    int64_t dk = 1;
+    for (int k = 0; k <= K; ++k) {
+        mu[k] = (double)M[k] / (double)dk;          /* Eq. (24); M_k rounded once */
+        dk *= d;
+    }
+    fabf_tail(N, Ainv, alpha, d, mu, (double)theta[(long)y * W + x], (double)sigma[(long)y * W + x],
+              g_out, c, t0lam, I, T, &flags);
+    if (M_out)
+        for (int k = 0; k <= N; ++k) {
+            M_out[2 * k] = (uint64_t)M[k];
+            M_out[2 * k + 1] = (uint64_t)(M[k] >> 64);
+        }
+    if (mu_out) for (int k = 0; k <= N; ++k) mu_out[k] = mu[k];
+    if (c_out) for (int k = 0; k <= N; ++k) c_out[k] = c[k];
+    if (t0lam_out) { t0lam_out[0] = t0lam[0]; t0lam_out[1] = t0lam[1]; }
+    if (I_out) for (int k = 0; k <= N + 1; ++k) I_out[k] = I[k];
+    if (T_out) { T_out[0] = T[0]; T_out[1] = T[1]; }
+    if (flags_out) *flags_out = flags;
+}
+
+/* m_k with the separable kernel as (low, high) word pairs: m is
+ * (N+1) x H x W x 2 uint64. */
+int oracle_moments_sep(const uint8_t* f, int H, int W, long pitch, const uint32_t* taps, int r,
+                       int N, uint64_t* m)
+{
+    if (check_args(H, W, pitch, r, N) || check_taps(taps, r)) return 1;
+    const long plane = (long)H * W;
+    u128 mk[ORACLE_NMAX + 1];
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            pixel_moments_sep(f, H, W, pitch, taps, r, N, y, x, mk);
+            for (int k = 0; k <= N; ++k) {
+                const long o = 2 * (k * plane + (long)y * W + x);
+                m[o] = (uint64_t)mk[k];
+                m[o + 1] = (uint64_t)(mk[k] >> 64);
+            }
+        }
+    return 0;
+}
+
+/* Algorithm 1 with the separable kernel at the n pixels (ys[j], xs[j]). */
+int oracle_fabf_sep_pixels(const uint8_t* f, const float* theta, const float* sigma, int H,
+                           int W, long pitch, const uint32_t* taps, int r, int N,
+                           const int32_t* ys, const int32_t* xs, long n, double* out,
+                           long* n_fallback)
+{
+    if (check_args(H, W, pitch, r, N) || check_taps(taps, r)) return 1;
+    int64_t Ainv[(ORACLE_NMAX + 1) * (ORACLE_NMAX + 1)];
+    oracle_hilbert_inverse(N, Ainv);
+    long nf = 0;
+    for (long j = 0; j < n; ++j) {
+        int flags = 0;
+        if (ys[j] < 0 || ys[j] >= H || xs[j] < 0 || xs[j] >= W) return 1;
+        fabf_pixel_sep(f, theta, sigma, H, W, pitch, taps, r, N, ys[j], xs[j], Ainv, &out[j],
+                       NULL, NULL, NULL, NULL, NULL, NULL, NULL, NULL, NULL, &flags);
+        if (flags & 2) ++nf;
+    }
+    if (n_fallback) *n_fallback = nf;
+    return 0;
+}
+
+/* Algorithm 1 with the separable kernel on the whole image. */
+int oracle_fabf_sep(const uint8_t* f, const float* theta, const float* sigma, int H, int W,
+                    long pitch, const uint32_t* taps, int r, int N, double* out,
+                    long* n_fallback)
+{
+    if (check_args(H, W, pitch, r, N) || check_taps(taps, r)) return 1;
+    int64_t Ainv[(ORACLE_NMAX + 1) * (ORACLE_NMAX + 1)];
+    oracle_hilbert_inverse(N, Ainv);
+    long nf = 0;
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            int flags = 0;
+            fabf_pixel_sep(f, theta, sigma, H, W, pitch, taps, r, N, y, x, Ainv,
+                           &out[(long)y * W + x], NULL, NULL, NULL, NULL, NULL, NULL, NULL,
+                           NULL, NULL, &flags);
+            if (flags & 2) ++nf;
+        }
+    if (n_fallback) *n_fallback = nf;
+    return 0;
+}
+
+/* Every intermediate with the separable kernel at (y, x); m and M hold
+ * 2 (N+1) words (low, high per k), the rest as in oracle_fabf_trace. */
+int oracle_fabf_sep_trace(const uint8_t* f, const float* theta, const float* sigma, int H,
+                          int W, long pitch, const uint32_t* taps, int r, int N, int y, int x,
+                          int32_t* ab, uint64_t* m, uint64_t* M, double* mu, double* c,
+                          double* t0lam, double* I, double* T, double* g, int32_t* flags)
+{
+    if (check_args(H, W, pitch, r, N) || check_taps(taps, r)) return 1;
+    if (y < 0 || y >= H || x < 0 || x >= W) return 1;
+    int64_t Ainv[(ORACLE_NMAX + 1) * (ORACLE_NMAX + 1)];
+    oracle_hilbert_inverse(N, Ainv);
+    int a = 0, b = 0, fl = 0;
+    fabf_pixel_sep(f, theta, sigma, H, W, pitch, taps, r, N, y, x, Ainv, g, &a, &b, m, M, mu,
+                   c, t0lam, I, T, &fl);
+    ab[0] = a;
+    ab[1] = b;
+    flags[0] = fl;
+    return 0;
+}
+
+/* Brute-force adaptive bilateral filter, Eqs. (1)-(3), with the separable
+ * spatial kernel, at the n pixels (ys[j], xs[j]). */
+int oracle_bruteforce_sep_pixels(const uint8_t* f, const float* theta, const float* sigma,
+                                 int H, int W, long pitch, const uint32_t* taps, int r,
+                                 const int32_t* ys, const int32_t* xs, long n, double* out)
+{
+    if (check_args(H, W, pitch, r, 0) || check_taps(taps, r)) return 1;
+    for (long j = 0; j < n; ++j) {
+        int y = ys[j], x = xs[j], y0, y1, x0, x1;
+        if (y < 0 || y >= H || x < 0 || x >= W) return 1;
+        window_bounds(H, W, y, x, r, &y0, &y1, &x0, &x1);
+        const double th = theta[(long)y * W + x];
+        const double s = sigma[(long)y * W + x];
+        double num = 0.0, den = 0.0;
+        for (int yy = y0; yy <= y1; ++yy)
+            for (int xx = x0; xx <= x1; ++xx) {
+                const double om = (double)taps[yy - y + r] * (double)taps[xx - x + r];
+                const double v = f[(long)yy * pitch + xx];
+                const double phi = exp(-(v - th) * (v - th) / (2.0 * s * s));   /* Eq. (3) */
+                num += om * phi * v;                                           /* Eq. (1) */
+                den += om * phi;                                               /* Eq. (2) */
+            }
+        out[j] = num / den;
+    }
+    return 0;
+}
+
+/* Brute force with the separable kernel on the whole image. */
+int oracle_bruteforce_sep(const uint8_t* f, const float* theta, const float* sigma, int H,
+                          int W, long pitch, const uint32_t* taps, int r, double* out)
+{
+    if (check_args(H, W, pitch, r, 0) || check_taps(taps, r)) return 1;
+    int32_t* ys = (int32_t*)malloc(sizeof(int32_t) * (size_t)W);
+    int32_t* xs = (int32_t*)malloc(sizeof(int32_t) * (size_t)W);
+    if (!ys || !xs) { free(ys); free(xs); return 2; }
+    int rc = 0;
+    for (int y = 0; y < H && !rc; ++y) {
+        for (int x = 0; x < W; ++x) { ys[x] = y; xs[x] = x; }
+        rc = oracle_bruteforce_sep_pixels(f, theta, sigma, H, W, pitch, taps, r, ys, xs, W,
+                                          out + (long)y * W);
     }
     free(ys);
     free(xs);

@@ -24,12 +24,17 @@ Recipe (all draws from ``numpy.random.default_rng(seed)``, in this order):
   clip to [0, 255]; round half to even; cast to uint8.
 * smooth fields (theta offset zeta, sigma): an 8x8 grid of ``U[lo, hi]``
   values upsampled bilinearly (corner-aligned) to H x W, float32.
+
+The spatial kernel is an input too: ``gaussian_taps(rho)`` gives the integer
+taps of a Gaussian of width rho on the paper's window [-3 rho, 3 rho]
+(Eq. (4)), and ``random_taps`` draws arbitrary (asymmetric) taps for tests.
 """
 from __future__ import annotations
 
 import numpy as np
 
-__all__ = ["make_image", "smooth_field", "make_inputs", "config_seed"]
+__all__ = ["make_image", "smooth_field", "make_inputs", "config_seed", "gaussian_taps",
+           "random_taps"]
 
 
 def config_seed(config: int, index: int) -> int:
@@ -106,3 +111,25 @@ def make_inputs(H: int, W: int, seed: int, n_blobs: int = 20,
     sigma = smooth_field(H, W, sigma_range[0], sigma_range[1], rng)
     return (np.ascontiguousarray(f), np.ascontiguousarray(theta),
             np.ascontiguousarray(sigma))
+
+
+def gaussian_taps(rho: float, peak: int = 1024) -> np.ndarray:
+    """Integer taps of the Gaussian spatial kernel of Eq. (4), one axis.
+
+    ``r = ceil(3 rho)`` (window [-3 rho, 3 rho]) and ``g[t] = floor(peak
+    exp(-(t - r)^2 / (2 rho^2)) + 1/2)`` for t = 0..2r, uint32.  With
+    peak = 1024 and rho <= 40/3 (r <= 40) the taps sum to at most 34,300.
+    The 2-D kernel is g[ty + r] g[tx + r].
+    """
+    if not (rho > 0):
+        raise ValueError("rho must be positive")
+    r = int(np.ceil(3.0 * rho))
+    t = np.arange(-r, r + 1, dtype=np.float64)
+    return np.floor(peak * np.exp(-t * t / (2.0 * rho * rho)) + 0.5).astype(np.uint32)
+
+
+def random_taps(r: int, rng: np.random.Generator, hi: int = 1000) -> np.ndarray:
+    """2r+1 arbitrary taps in [0, hi] with a non-zero centre (uint32)."""
+    g = rng.integers(0, hi + 1, size=2 * r + 1).astype(np.uint32)
+    g[r] = max(int(g[r]), 1)
+    return g

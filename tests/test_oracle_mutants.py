@@ -44,18 +44,28 @@ MUTANTS = {
     "recursion boundary sign": ("I[k - 2] - E1 / (2 * lam);", "I[k - 2] + E1 / (2 * lam);"),
     "E_1 square dropped": ("expf128(-lam * (1 - t0) * (1 - t0))", "expf128(-lam * (1 - t0))"),
     "scale sign": ("q128 s = expf128(lam * d * d);", "q128 s = expf128(-lam * d * d);"),
-    "mu divisor": ("dk *= d;", "dk *= d + 1;"),
+    "mu divisor": ("/* Eq. (24), R2 */\n        dk *= d;", "/* Eq. (24), R2 */\n        dk *= d + 1;"),
     "fit index": ("acc = fma((double)Ainv[n * (N + 1) + k], mu[k], acc);",
                   "acc = fma((double)Ainv[n * (N + 1) + k], mu[n], acc);"),
-    "t0 from beta": ("- (double)alpha) / (double)d;", "- (double)beta) / (double)d;"),
+    "t0 from beta": ("- (double)alpha) / (double)d;", "- (double)(alpha + d)) / (double)d;"),
     "lambda without the 2": ("(double)(d * d) / (2.0 * s * s)", "(double)(d * d) / (s * s)"),
     "T1 index": ("T1 = fma(c[k - 1], I[k], T1);", "T1 = fma(c[k - 1], I[k - 1], T1);"),
-    "ratio from beta": ("*g_out = (double)alpha + (double)d * F;", "*g_out = (double)beta + (double)d * F;"),
+    "ratio without alpha": ("*g_out = (double)alpha + (double)d * F;", "*g_out = (double)d * F;"),
     "fallback inverted": ("F = mu[1] / mu[0];", "F = mu[0] / mu[1];"),
-    "brute force kernel width": ("exp(-(v - th) * (v - th) / (2.0 * s * s))",
-                                 "exp(-(v - th) * (v - th) / (s * s))"),
+    "brute force kernel width": ("                double phi = exp(-(v - th) * (v - th) / (2.0 * s * s))",
+                                 "                double phi = exp(-(v - th) * (v - th) / (s * s))"),
     "brute force numerator": ("num += phi * v;", "num += phi * th;"),
-    "flat branch skipped": ("if (alpha == beta) {", "if (alpha == beta && alpha < 0) {"),
+    "flat branch skipped": ("if (alpha == beta) {\n        /* Sec. II-A and Algorithm 1",
+                            "if (alpha == beta && alpha < 0) {\n        /* Sec. II-A and Algorithm 1"),
+    "separable weight mirrored": (
+        "om = (u128)taps[yy - y + r] * taps[xx - x + r];\n            u128 v = f[",
+        "om = (u128)taps[y - yy + r] * taps[xx - x + r];\n            u128 v = f["),
+    "separable shifted weight dropped": ("{ M[k] += om * p; p *= v; }", "{ M[k] += p; p *= v; }"),
+    "separable moments truncated to 64 bits": (
+        "mu[k] = (double)M[k] / (double)dk;          /* Eq. (24); M_k rounded once */",
+        "mu[k] = (double)(uint64_t)M[k] / (double)dk;"),
+    "separable brute force unweighted denominator": ("den += om * phi;", "den += phi;"),
+    "separable tap sum limit": ("s > ORACLE_TAP_SUM_MAX", "s > 2 * ORACLE_TAP_SUM_MAX"),
 }
 
 # ---------------------------------------------------------------------------
@@ -191,10 +201,50 @@ def battery():
                         return
         assert found > 0
 
+    def separable():
+        # weighted sums against Python integers (asymmetric taps), mu of a
+        # 2^80-sized moment, the weighted brute force against numpy, the
+        # weighted mean as sigma -> infinity, and the tap-sum limit
+        f, th, s = R["tiny"]
+        taps = np.array([3, 9, 1, 7, 2], np.uint32)
+        m = oracle.moments_sep(f, taps, 6)
+        g = oracle.bruteforce_sep(f, th, s, taps)
+        gm, _ = oracle.fabf_sep(f, th, np.full(f.shape, 1e9, np.float32), taps, 3)
+        for y, x in ((0, 0), (5, 6), (10, 12), (4, 1)):
+            vals, wts = [], []
+            for yy in range(max(0, y - 2), min(11, y + 3)):
+                for xx in range(max(0, x - 2), min(13, x + 3)):
+                    vals.append(int(f[yy, xx]))
+                    wts.append(int(taps[yy - y + 2]) * int(taps[xx - x + 2]))
+            for k in range(7):
+                assert m[k, y, x] == sum(wv * v ** k for v, wv in zip(vals, wts))
+            al = min(vals)
+            tr = oracle.fabf_sep_trace(f, th, s, taps, 4, y, x)
+            if not tr["flat"]:
+                assert tr["M"][4] == sum(wv * (v - al) ** 4 for v, wv in zip(vals, wts))
+            v = np.array(vals, float)
+            om = np.array(wts, float)
+            phi = np.exp(-(v - float(th[y, x])) ** 2 / (2 * float(s[y, x]) ** 2))
+            assert g[y, x] == pytest.approx((om * phi * v).sum() / (om * phi).sum(), rel=1e-13)
+            assert gm[y, x] == pytest.approx((om * v).sum() / om.sum(), rel=1e-9)
+        wide = np.full((9, 9), 255, np.uint8)
+        wide[0, 0] = 0
+        big = np.full(9, 7000, np.uint32)
+        tr = oracle.fabf_sep_trace(wide, wide.astype(np.float32), np.full((9, 9), 30.0, np.float32),
+                                   big, 6, 4, 4)
+        M6 = sum(int(big[yy]) * int(big[xx]) * int(wide[yy, xx]) ** 6 for yy in range(9) for xx in range(9))
+        assert tr["mu"][6] == float(M6) / float(255 ** 6)
+        try:
+            oracle.fabf_sep(f, th, s, np.full(5, 20000, np.uint32), 3)
+        except ValueError:
+            pass
+        else:
+            raise AssertionError("taps summing to 100000 were accepted")
+
     for name, fn in [("hilbert", hilbert), ("window", window_stats), ("integrals", integrals),
                      ("fit", fit_moments), ("constant", constant_image), ("box mean", box_mean_limit),
                      ("truncated normal", truncated_normal), ("bruteforce", bruteforce),
-                     ("fallback", fallback_rule)]:
+                     ("fallback", fallback_rule), ("separable", separable)]:
         check(name, fn)
     return fails
 
