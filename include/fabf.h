@@ -205,6 +205,32 @@ int fabf_filter_noalloc(const uint8_t* img, const float* theta, const float* sig
                         size_t pitch, int w, int N, void* out, int out_is_f64, void* cuda_stream,
                         uint64_t* n_fallback);
 
+/* ---- separable spatial kernel (Gaussian, Eq. (4)) ------------------------ */
+
+/* fabf_filter with the spatial kernel omega(j) = taps[jy + r] * taps[jx + r]
+ * on the window [-r, r]^2 (clipped to the image) instead of the box: Eqs.
+ * (1)-(3) with a general omega, and Algorithm 1 with the moments of Eq. (17)
+ * weighted by omega.  With Gaussian taps (fabf_gaussian_taps) this is the
+ * paper's own setting, Eq. (4) with the window [-3 rho, 3 rho]^2.
+ *   taps  HOST array of 2r+1 integers read during the call: taps[t] >= 0,
+ *         taps[r] >= 1, sum <= 65535 (so every moment is an exact integer
+ *         below 2^81, summed in 64/128-bit arithmetic);
+ *   r     1..40;  N 0..6;  the other arguments, the pointer kinds, the
+ *         synchronisation and the status reporting are those of fabf_filter.
+ * Always computed in binary64 (the context's precision is not used).
+ * Errors: FABF_EINVAL (NULL pointers, taps[r] == 0, bad sizes),
+ * FABF_EUNSUPPORTED (r > 40, N > 6, tap sum > 65535), FABF_ECUDA. */
+int fabf_filter_sep(fabf_ctx* ctx, const uint8_t* img, const float* theta, const float* sigma,
+                    int H, int W, size_t pitch, const uint32_t* taps, int r, int N, void* out,
+                    int out_is_f64, void* cuda_stream);
+
+/* Integer taps of the Gaussian spatial kernel of Eq. (4) along one axis:
+ * r = max(1, ceil(3 rho)) and taps[t] = floor(1024 exp(-(t - r)^2 / (2 rho^2))
+ * + 1/2), t = 0..2r (host only, no GPU).  Their sum stays below 34,300 for
+ * every allowed rho.  Errors: FABF_EINVAL (rho <= 0 or not finite, NULL
+ * pointers, capacity < 2r+1), FABF_EUNSUPPORTED (3 rho > 40). */
+int fabf_gaussian_taps(double rho, uint32_t* taps, int capacity, int* r);
+
 /* ---- host-side helpers (no GPU needed) ---------------------------------- */
 
 /* The exact inverse of the (N+1) x (N+1) Hilbert matrix of Eq. (18), by the
@@ -247,6 +273,22 @@ int fabf_debug_integrals(fabf_ctx* ctx, const double* lambda, const double* t0, 
 int fabf_bruteforce(fabf_ctx* ctx, const uint8_t* img, const float* theta, const float* sigma,
                     int H, int W, size_t pitch, int w, void* out, int out_is_f64, int use_f64,
                     void* cuda_stream);
+
+/* fabf_debug_stages for the separable kernel: the same planes, except m and M
+ * hold 2 (N+1) uint64 words per pixel ((N+1) planes of H x W x 2, low word
+ * first), since weighted moments reach 2^81.  M, mu, c, t0lam, I, T are left
+ * untouched at flat pixels. */
+int fabf_debug_stages_sep(fabf_ctx* ctx, const uint8_t* img, const float* theta,
+                          const float* sigma, int H, int W, size_t pitch, const uint32_t* taps,
+                          int r, int N, uint8_t* alpha, uint8_t* beta, uint64_t* m, uint64_t* M,
+                          double* mu, double* c, double* t0lam, double* I, double* T,
+                          int32_t* flags, double* out);
+
+/* Brute-force filter, Eqs. (1)-(3), with the separable kernel (O(r^2) per
+ * pixel); arguments as fabf_bruteforce plus taps and r as fabf_filter_sep. */
+int fabf_bruteforce_sep(fabf_ctx* ctx, const uint8_t* img, const float* theta,
+                        const float* sigma, int H, int W, size_t pitch, const uint32_t* taps,
+                        int r, void* out, int out_is_f64, int use_f64, void* cuda_stream);
 
 #ifdef __cplusplus
 }

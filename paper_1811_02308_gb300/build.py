@@ -20,6 +20,7 @@ SOURCES = [
     "fabf_api.cu",
     "fabf_batch_serve.cu",
     "fabf_noalloc.cu",
+    "fabf_sep.cu",
 ]
 HEADERS = ["fabf_device.cuh", "fabf_kernels.cuh", "fabf_launch.cuh", "fabf_internal.h"]
 

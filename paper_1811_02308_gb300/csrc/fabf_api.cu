@@ -143,7 +143,7 @@ size_t make_job(ImageJob* J, CUtensorMap* tm, const uint8_t* img, size_t pitch, 
 
 namespace fabf {
 
-static int ensure_stage(fabf_ctx* ctx, size_t bytes)
+int ensure_stage(fabf_ctx* ctx, size_t bytes)
 {
     if (bytes <= ctx->stage_bytes) return FABF_OK;
     if (ctx->stage) cudaFree(ctx->stage);
@@ -277,52 +277,11 @@ int fabf_filter(fabf_ctx* ctx, const uint8_t* img, const float* theta, const flo
     if (rc) return rc;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return FABF_ECUDA;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-    const bool di = is_device_ptr(img), dt = is_device_ptr(theta), ds = is_device_ptr(sigma),
-               dout = is_device_ptr(out);
-    const size_t npix = (size_t)H * W;
-    const size_t osz = out_is_f64 ? 8 : 4;
-    if (di && dt && ds && dout)
-        return run_fused(ctx, img, pitch, theta, sigma, H, W, w, N, out, out_is_f64, nullptr, s);
-
-    // Host buffers: stage through one device allocation (16-byte aligned parts).
-    const size_t ipitch = ((size_t)W + 15) & ~(size_t)15;
-    size_t o_img = 0, o_th = o_img + ((ipitch * H + 255) & ~(size_t)255);
-    size_t o_sg = o_th + ((npix * 4 + 255) & ~(size_t)255);
-    size_t o_out = o_sg + ((npix * 4 + 255) & ~(size_t)255);
-    size_t total = o_out + npix * osz;
-    rc = ensure_stage(ctx, total);
-    if (rc) return rc;
-    uint8_t* base = static_cast<uint8_t*>(ctx->stage);
-    const uint8_t* d_img = img;
-    size_t d_pitch = pitch;
-    const float* d_th = theta;
-    const float* d_sg = sigma;
-    void* d_out = out;
-    cudaError_t e = cudaSuccess;
-    if (!di) {
-        e = cudaMemcpy2DAsync(base + o_img, ipitch, img, pitch, W, H, cudaMemcpyHostToDevice, s);
-        d_img = base + o_img;
-        d_pitch = ipitch;
-    }
-    if (e == cudaSuccess && !dt) {
-        e = cudaMemcpyAsync(base + o_th, theta, npix * 4, cudaMemcpyHostToDevice, s);
-        d_th = reinterpret_cast<const float*>(base + o_th);
-    }
-    if (e == cudaSuccess && !ds) {
-        e = cudaMemcpyAsync(base + o_sg, sigma, npix * 4, cudaMemcpyHostToDevice, s);
-        d_sg = reinterpret_cast<const float*>(base + o_sg);
-    }
-    if (!dout) d_out = base + o_out;
-    if (e != cudaSuccess) return cuda_status(e);
-    rc = run_fused(ctx, d_img, d_pitch, d_th, d_sg, H, W, w, N, d_out, out_is_f64, nullptr, s);
-    if (rc) return rc;
-    if (!dout) {
-        e = cudaMemcpyAsync(out, d_out, npix * osz, cudaMemcpyDeviceToHost, s);
-        if (e != cudaSuccess) return cuda_status(e);
-    }
-    int st = FABF_OK;
-    rc = read_and_clear_status(ctx, s, &st, nullptr, nullptr);
-    return rc ? rc : st;
+    return with_device_buffers(
+        ctx, img, theta, sigma, H, W, pitch, out, out_is_f64, s,
+        [&](const uint8_t* d_img, size_t d_pitch, const float* d_th, const float* d_sg, void* d_out) {
+            return run_fused(ctx, d_img, d_pitch, d_th, d_sg, H, W, w, N, d_out, out_is_f64, nullptr, s);
+        });
 }
 
 int fabf_get_status(fabf_ctx* ctx, void* cuda_stream, int* status, uint64_t* n_fallback)

@@ -188,6 +188,60 @@ struct PixelTrace {       // optional per-pixel export of every stage
     int fallback;
 };
 
+// Algorithm 1 from mu_k = M_k / (beta - alpha)^k on: the fit, the kernel
+// parameters, the integrals and the ratio, in binary64 (shared by the box and
+// the separable spatial kernels).
+template <int N>
+__device__ __forceinline__ double fabf_tail_fp64(const AinvTable& A, int alpha, int d,
+                                                 const double (&mu)[(N < 1 ? 1 : N) + 1], float theta_f,
+                                                 float sigma_f, int& fallback, PixelTrace* tr)
+{
+    // c = A^{-1} mu, Eq. (19) and Algorithm 1, fused multiply-adds over
+    // ascending k starting from zero.
+    double c[N + 1];
+#pragma unroll
+    for (int n = 0; n <= N; ++n) {
+        double acc = 0.0;
+#pragma unroll
+        for (int k = 0; k <= N; ++k) acc = fma(A.v[N][n][k], mu[k], acc);
+        c[n] = acc;
+    }
+    // Eq. (25) and Algorithm 1.
+    const double sg = (double)sigma_f;
+    const double t0 = ((double)theta_f - (double)alpha) / (double)d;
+    const double lam = (double)(d * d) / (2.0 * sg * sg);
+    double I[N + 2];
+    integrals_fp64<N + 1>(lam, t0, I);
+    // Eq. (29), accumulated in the order of Algorithm 1.
+    double T1 = c[0] * I[1], T2 = c[0] * I[0];
+#pragma unroll
+    for (int k = 2; k <= N + 1; ++k) {
+        T1 = fma(c[k - 1], I[k], T1);
+        T2 = fma(c[k - 1], I[k - 1], T2);
+    }
+    double F = T1 / T2;
+    fallback = 0;
+    if (!(T2 > 0.0) || !isfinite(F)) {   // fitted polynomial not positive enough
+        F = mu[1] / mu[0];                // sigma -> infinity limit (spatial-kernel mean)
+        fallback = 1;
+    }
+    if (tr) {
+#pragma unroll
+        for (int k = 0; k <= N; ++k) {
+            tr->mu[k] = mu[k];
+            tr->c[k] = c[k];
+        }
+#pragma unroll
+        for (int k = 0; k <= N + 1; ++k) tr->I[k] = I[k];
+        tr->t0 = t0;
+        tr->lam = lam;
+        tr->T1 = T1;
+        tr->T2 = T2;
+        tr->fallback = fallback;
+    }
+    return (double)alpha + (double)d * F;
+}
+
 template <int N>
 __device__ __forceinline__ double fabf_pixel_fp64(const AinvTable& A, int alpha, int beta, int fi,
                                                   const int64_t (&m)[(N < 1 ? 1 : N) + 1],
@@ -222,50 +276,11 @@ __device__ __forceinline__ double fabf_pixel_fp64(const AinvTable& A, int alpha,
         mu[k] = (double)M[k] / (double)dk;
         dk *= d;
     }
-    // c = A^{-1} mu, Eq. (19) and Algorithm 1, fused multiply-adds over
-    // ascending k starting from zero.
-    double c[N + 1];
-#pragma unroll
-    for (int n = 0; n <= N; ++n) {
-        double acc = 0.0;
-#pragma unroll
-        for (int k = 0; k <= N; ++k) acc = fma(A.v[N][n][k], mu[k], acc);
-        c[n] = acc;
-    }
-    // Eq. (25) and Algorithm 1.
-    const double sg = (double)sigma_f;
-    const double t0 = ((double)theta_f - (double)alpha) / (double)d;
-    const double lam = (double)(d * d) / (2.0 * sg * sg);
-    double I[N + 2];
-    integrals_fp64<N + 1>(lam, t0, I);
-    // Eq. (29), accumulated in the order of Algorithm 1.
-    double T1 = c[0] * I[1], T2 = c[0] * I[0];
-#pragma unroll
-    for (int k = 2; k <= N + 1; ++k) {
-        T1 = fma(c[k - 1], I[k], T1);
-        T2 = fma(c[k - 1], I[k - 1], T2);
-    }
-    double F = T1 / T2;
-    if (!(T2 > 0.0) || !isfinite(F)) {   // fitted polynomial not positive enough
-        F = mu[1] / mu[0];                // sigma -> infinity limit (box mean)
-        fallback = 1;
-    }
     if (tr) {
 #pragma unroll
-        for (int k = 0; k <= N; ++k) {
-            tr->M[k] = M[k];
-            tr->mu[k] = mu[k];
-            tr->c[k] = c[k];
-        }
-#pragma unroll
-        for (int k = 0; k <= N + 1; ++k) tr->I[k] = I[k];
-        tr->t0 = t0;
-        tr->lam = lam;
-        tr->T1 = T1;
-        tr->T2 = T2;
-        tr->fallback = fallback;
+        for (int k = 0; k <= N; ++k) tr->M[k] = M[k];
     }
-    return (double)alpha + (double)d * F;
+    return fabf_tail_fp64<N>(A, alpha, d, mu, theta_f, sigma_f, fallback, tr);
 }
 
 

@@ -92,6 +92,61 @@ int tile_rows_for(fabf_ctx* ctx, int w, int N, int prec);
 constexpr int kDefaultTileRows = 32;
 
 int read_and_clear_status(fabf_ctx* ctx, cudaStream_t s, int* status, uint64_t* nfb, uint64_t* nredo);
+
+// Grow the context's staging buffer to at least `bytes`.
+int ensure_stage(fabf_ctx* ctx, size_t bytes);
+
+// Run `launch(d_img, d_pitch, d_theta, d_sigma, d_out)` on device buffers.
+// All-device arguments are passed through (the call stays stream-ordered; the
+// status words are read by fabf_get_status).  Host buffers are staged through
+// the context's buffer (16-byte aligned image rows), the output copied back,
+// and the call synchronises and returns the kernels' status.
+template <typename Launch>
+int with_device_buffers(fabf_ctx* ctx, const uint8_t* img, const float* theta, const float* sigma, int H, int W,
+                        size_t pitch, void* out, int out_is_f64, cudaStream_t s, Launch&& launch)
+{
+    const bool di = is_device_ptr(img), dt = is_device_ptr(theta), ds = is_device_ptr(sigma),
+               dout = is_device_ptr(out);
+    if (di && dt && ds && dout) return launch(img, pitch, theta, sigma, out);
+    const size_t npix = (size_t)H * W;
+    const size_t osz = out_is_f64 ? 8 : 4;
+    const size_t ipitch = ((size_t)W + 15) & ~(size_t)15;
+    const size_t o_img = 0, o_th = o_img + ((ipitch * H + 255) & ~(size_t)255);
+    const size_t o_sg = o_th + ((npix * 4 + 255) & ~(size_t)255);
+    const size_t o_out = o_sg + ((npix * 4 + 255) & ~(size_t)255);
+    int rc = ensure_stage(ctx, o_out + npix * osz);
+    if (rc) return rc;
+    uint8_t* base = static_cast<uint8_t*>(ctx->stage);
+    const uint8_t* d_img = img;
+    size_t d_pitch = pitch;
+    const float* d_th = theta;
+    const float* d_sg = sigma;
+    void* d_out = dout ? out : base + o_out;
+    cudaError_t e = cudaSuccess;
+    if (!di) {
+        e = cudaMemcpy2DAsync(base + o_img, ipitch, img, pitch, W, H, cudaMemcpyHostToDevice, s);
+        d_img = base + o_img;
+        d_pitch = ipitch;
+    }
+    if (e == cudaSuccess && !dt) {
+        e = cudaMemcpyAsync(base + o_th, theta, npix * 4, cudaMemcpyHostToDevice, s);
+        d_th = reinterpret_cast<const float*>(base + o_th);
+    }
+    if (e == cudaSuccess && !ds) {
+        e = cudaMemcpyAsync(base + o_sg, sigma, npix * 4, cudaMemcpyHostToDevice, s);
+        d_sg = reinterpret_cast<const float*>(base + o_sg);
+    }
+    if (e != cudaSuccess) return cuda_status(e);
+    rc = launch(d_img, d_pitch, d_th, d_sg, d_out);
+    if (rc) return rc;
+    if (!dout) {
+        e = cudaMemcpyAsync(out, d_out, npix * osz, cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    int st = 0;
+    rc = read_and_clear_status(ctx, s, &st, nullptr, nullptr);
+    return rc ? rc : st;
+}
 void serve_destroy(ServeState* s);
 void batch_destroy(BatchState* b);
 

@@ -85,6 +85,10 @@ def load(path: str | None = None):
         "fabf_debug_stages": ([vp, vp, vp, vp, i, i, sz, i, i] + [vp] * 11, i),
         "fabf_debug_integrals": ([vp, vp, vp, C.c_int64, i, i, vp], i),
         "fabf_bruteforce": ([vp, vp, vp, vp, i, i, sz, i, vp, i, i, vp], i),
+        "fabf_filter_sep": ([vp, vp, vp, vp, i, i, sz, vp, i, i, vp, i, vp], i),
+        "fabf_gaussian_taps": ([C.c_double, vp, i, C.POINTER(i)], i),
+        "fabf_debug_stages_sep": ([vp, vp, vp, vp, i, i, sz, vp, i, i] + [vp] * 11, i),
+        "fabf_bruteforce_sep": ([vp, vp, vp, vp, i, i, sz, vp, i, vp, i, i, vp], i),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -291,6 +295,82 @@ def fabf_bruteforce(ctx: Context, img, theta, sigma, w: int, out=None, out_is_f6
     _check(load().fabf_bruteforce(ctx.handle, _ptr(img), _ptr(theta), _ptr(sigma), H, W,
                                   int(img.shape[1]), int(w), _ptr(out), 1 if out_is_f64 else 0,
                                   1 if use_f64 else 0, s), "fabf_bruteforce")
+    return out
+
+
+def _taps(taps) -> np.ndarray:
+    t = np.ascontiguousarray(np.asarray(taps), dtype=np.uint32)
+    if t.ndim != 1 or len(t) % 2 != 1:
+        raise ValueError("taps must be a 1-D array of odd length 2r+1")
+    return t
+
+
+def fabf_gaussian_taps(rho: float) -> np.ndarray:
+    """Integer taps of the Gaussian spatial kernel of Eq. (4) (``fabf_gaussian_taps``)."""
+    buf = np.zeros(2 * 40 + 1, np.uint32)
+    r = C.c_int(0)
+    _check(load().fabf_gaussian_taps(float(rho), buf.ctypes.data, len(buf), C.byref(r)),
+           "fabf_gaussian_taps")
+    return buf[:2 * r.value + 1].copy()
+
+
+def fabf_filter_sep(ctx: Context, img, theta, sigma, taps, N: int, out=None, out_is_f64: bool = True,
+                    pitch: int | None = None, stream: int | None = None, check: bool = True):
+    """Algorithm 1 with the separable spatial kernel taps x taps (``fabf_filter_sep``)."""
+    t = _taps(taps)
+    H, W = int(theta.shape[0]), int(theta.shape[1])
+    p = int(pitch) if pitch is not None else int(img.shape[1])
+    if out is None:
+        out = _empty_like_out(theta, H, W, out_is_f64)
+    s = _stream_of(img, theta, sigma, out) if stream is None else stream
+    rc = load().fabf_filter_sep(ctx.handle, _ptr(img), _ptr(theta), _ptr(sigma), H, W, p, t.ctypes.data,
+                                len(t) // 2, int(N), _ptr(out), 1 if out_is_f64 else 0, s)
+    if check:
+        _check(rc, "fabf_filter_sep")
+        return out
+    return out, rc
+
+
+def fabf_debug_stages_sep(ctx: Context, img, theta, sigma, taps, N: int):
+    """Every intermediate with the separable kernel; m and M are (N+1, H, W, 2)
+    uint64 word pairs held in int64 tensors (low word first)."""
+    import torch
+    t = _taps(taps)
+    H, W = int(theta.shape[0]), int(theta.shape[1])
+    dev = theta.device
+    o = dict(
+        alpha=torch.zeros((H, W), dtype=torch.uint8, device=dev),
+        beta=torch.zeros((H, W), dtype=torch.uint8, device=dev),
+        m=torch.zeros((N + 1, H, W, 2), dtype=torch.int64, device=dev),
+        M=torch.zeros((N + 1, H, W, 2), dtype=torch.int64, device=dev),
+        mu=torch.full((N + 1, H, W), float("nan"), dtype=torch.float64, device=dev),
+        c=torch.full((N + 1, H, W), float("nan"), dtype=torch.float64, device=dev),
+        t0lam=torch.full((2, H, W), float("nan"), dtype=torch.float64, device=dev),
+        I=torch.full((N + 2, H, W), float("nan"), dtype=torch.float64, device=dev),
+        T=torch.full((2, H, W), float("nan"), dtype=torch.float64, device=dev),
+        flags=torch.zeros((H, W), dtype=torch.int32, device=dev),
+        out=torch.zeros((H, W), dtype=torch.float64, device=dev),
+    )
+    rc = load().fabf_debug_stages_sep(ctx.handle, _ptr(img), _ptr(theta), _ptr(sigma), H, W,
+                                      int(img.shape[1]), t.ctypes.data, len(t) // 2, int(N),
+                                      *[_ptr(o[k]) for k in ("alpha", "beta", "m", "M", "mu", "c",
+                                                             "t0lam", "I", "T", "flags", "out")])
+    _check(rc, "fabf_debug_stages_sep")
+    return o
+
+
+def fabf_bruteforce_sep(ctx: Context, img, theta, sigma, taps, out=None, out_is_f64: bool = True,
+                        use_f64: bool = True, stream: int | None = None):
+    """Brute-force filter with the separable kernel on the GPU (device tensors)."""
+    t = _taps(taps)
+    H, W = int(theta.shape[0]), int(theta.shape[1])
+    if out is None:
+        out = _empty_like_out(theta, H, W, out_is_f64)
+    s = _stream_of(img, theta, sigma, out) if stream is None else stream
+    _check(load().fabf_bruteforce_sep(ctx.handle, _ptr(img), _ptr(theta), _ptr(sigma), H, W,
+                                      int(img.shape[1]), t.ctypes.data, len(t) // 2, _ptr(out),
+                                      1 if out_is_f64 else 0, 1 if use_f64 else 0, s),
+           "fabf_bruteforce_sep")
     return out
 
 

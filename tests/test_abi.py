@@ -72,3 +72,20 @@ def test_status_strings(lib):
     for s in range(8):
         assert fabf.status_str(s)
     assert "unknown" in fabf.status_str(99)
+
+
+def test_gaussian_taps_helper_matches_the_input_generator(lib):
+    from paper_1811_02308_gb300 import synth
+    for rho in (0.2, 0.5, 1.0, 1.7, 3.0, 5.0, 7.5, 10.0, 13.0, 40.0 / 3.0):
+        assert np.array_equal(fabf.fabf_gaussian_taps(rho), synth.gaussian_taps(rho)), rho
+
+
+def test_separable_argument_checks_without_gpu(lib):
+    buf = np.zeros(81, np.uint32)
+    r = C.c_int(0)
+    assert lib.fabf_gaussian_taps(0.0, buf.ctypes.data, 81, C.byref(r)) == fabf.FABF_EINVAL
+    assert lib.fabf_gaussian_taps(float("nan"), buf.ctypes.data, 81, C.byref(r)) == fabf.FABF_EINVAL
+    assert lib.fabf_gaussian_taps(13.4, buf.ctypes.data, 81, C.byref(r)) == fabf.FABF_EUNSUPPORTED
+    assert lib.fabf_gaussian_taps(3.0, buf.ctypes.data, 18, C.byref(r)) == fabf.FABF_EINVAL
+    null = C.c_void_p(0)
+    assert lib.fabf_filter_sep(null, 0, 0, 0, 4, 4, 4, buf.ctypes.data, 1, 1, 0, 1, 0) == fabf.FABF_EINVAL

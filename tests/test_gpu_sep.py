@@ -1,0 +1,195 @@
+"""Parity of the separable-spatial-kernel CUDA path (Gaussian of Eq. (4))
+with the CPU oracle, through the C ABI.
+
+Bar: alpha, beta, the weighted moments m_k and M_k (128-bit integers)
+bit-exact; mu_k, c, t0, lambda bit-exact; I_k within 1e-12 relative; the
+output within 1e-9 relative (floor 1 gray level), as for the box kernel.
+With all-ones taps the path must equal the box path bit for bit."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_1811_02308_gb300 import build, fabf, synth  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+RTOL_G = 1e-9
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    c = fabf.Context(device=0)
+    yield c
+    c.close()
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def g_err(got, ref):
+    got = np.asarray(got, np.float64)
+    ref = np.asarray(ref, np.float64)
+    err = np.abs(got - ref) / np.maximum(np.abs(ref), 1.0)
+    return float(err.max()) if err.size else 0.0
+
+
+def inputs(H, W, seed, n_blobs=20, zeta=(-20, 20), sigma=(5, 60)):
+    return synth.make_inputs(H, W, seed, n_blobs=n_blobs, zeta_range=zeta, sigma_range=sigma)
+
+
+def words_to_int(a):
+    """(..., 2) int64 word pairs (low, high) -> Python ints."""
+    a = np.asarray(a).view(np.uint64)
+    return a[..., 0].astype(object) + (a[..., 1].astype(object) << 64)
+
+
+def taps_for(kind, r_or_rho, seed):
+    if kind == "gauss":
+        return synth.gaussian_taps(r_or_rho)
+    rng = np.random.default_rng(seed)
+    return synth.random_taps(int(r_or_rho), rng, hi=min(1000, 65535 // (2 * int(r_or_rho) + 1)))
+
+
+STAGE_CASES = [
+    # H, W, kind, rho or r, N, seed
+    (1, 1, "gauss", 1.0, 5, 1),
+    (1, 77, "rand", 4, 4, 2),
+    (53, 1, "gauss", 1.5, 6, 3),
+    (67, 131, "gauss", 1.0, 5, 4),     # several tiles, ragged tails
+    (67, 131, "gauss", 3.0, 6, 5),
+    (67, 131, "rand", 7, 3, 6),        # asymmetric taps
+    (40, 70, "gauss", 40 / 3, 5, 7),   # r = 40: window larger than the image
+    (33, 65, "rand", 1, 0, 8),
+    (96, 200, "gauss", 5.0, 2, 9),
+    (70, 150, "rand", 40, 6, 10),      # largest tap sum and radius
+]
+
+
+@pytest.mark.parametrize("H,W,kind,rr,N,seed", STAGE_CASES)
+def test_sep_stages_match_oracle(ctx, oracle_mod, H, W, kind, rr, N, seed):
+    f, th, s = inputs(H, W, seed)
+    taps = taps_for(kind, rr, seed)
+    r = len(taps) // 2
+    o = fabf.fabf_debug_stages_sep(ctx, dev(f), dev(th), dev(s), taps, N)
+    a_ref, b_ref = oracle_mod.bounds(f, r)
+    assert np.array_equal(o["alpha"].cpu().numpy(), a_ref)
+    assert np.array_equal(o["beta"].cpu().numpy(), b_ref)
+    m_ref = oracle_mod.moments_sep(f, taps, N)
+    m_got = words_to_int(o["m"].cpu().numpy())
+    assert (m_got == m_ref).all()
+    flat = a_ref == b_ref
+    flags = o["flags"].cpu().numpy()
+    assert np.array_equal((flags & 1) != 0, flat)
+    M = words_to_int(o["M"].cpu().numpy())
+    mu, c = o["mu"].cpu().numpy(), o["c"].cpu().numpy()
+    t0lam, I = o["t0lam"].cpu().numpy(), o["I"].cpu().numpy()
+    out = o["out"].cpu().numpy()
+    ys, xs = np.nonzero(~flat)
+    rng = np.random.default_rng(seed)
+    if len(ys) > 400:
+        pick = rng.choice(len(ys), 400, replace=False)
+        ys, xs = ys[pick], xs[pick]
+    for y, x in zip(ys, xs):
+        tr = oracle_mod.fabf_sep_trace(f, th, s, taps, N, y, x)
+        assert list(M[:, y, x]) == tr["M"], (y, x)
+        assert np.array_equal(mu[:, y, x], tr["mu"]), (y, x)
+        assert np.array_equal(c[:, y, x], tr["c"]), (y, x)
+        assert t0lam[0, y, x] == tr["t0"] and t0lam[1, y, x] == tr["lam"]
+        np.testing.assert_allclose(I[:, y, x], tr["I"], rtol=1e-12, atol=0)
+        assert bool(flags[y, x] & 2) == tr["fallback"], (y, x)
+        assert g_err(out[y, x], tr["g"]) <= RTOL_G, (y, x, out[y, x], tr["g"])
+    g_ref, _ = oracle_mod.fabf_sep(f, th, s, taps, N)
+    assert g_err(out, g_ref) <= RTOL_G
+
+
+@pytest.mark.parametrize("w,N", [(1, 0), (5, 5), (20, 6), (40, 3)])
+def test_all_ones_taps_equal_box_path(ctx, w, N):
+    f, th, s = inputs(131, 197, 40 + w)
+    taps = np.ones(2 * w + 1, np.uint32)
+    g_sep = fabf.fabf_filter_sep(ctx, dev(f), dev(th), dev(s), taps, N)
+    g_box = fabf.fabf_filter(ctx, dev(f), dev(th), dev(s), w, N)
+    torch.cuda.synchronize()
+    assert torch.equal(g_sep, g_box)
+
+
+@pytest.mark.parametrize("rho,N", [(3.0, 5), (5.0, 5), (10.0, 6)])
+def test_sep_full_size_sampled(ctx, oracle_mod, rho, N):
+    # 1920 x 1080 frame with the Gaussian kernel, every pixel computed on the
+    # GPU, 3000 sampled pixels (and the image corners) recomputed by the oracle
+    H, W = 1080, 1920
+    f, th, s = inputs(H, W, 1001, n_blobs=200)
+    taps = synth.gaussian_taps(rho)
+    out = fabf.fabf_filter_sep(ctx, dev(f), dev(th), dev(s), taps, N, out_is_f64=True)
+    st, _ = fabf.fabf_get_status(ctx)
+    assert st == fabf.FABF_OK
+    g = out.cpu().numpy()
+    rng = np.random.default_rng(7)
+    ys = np.concatenate([rng.integers(0, H, 3000), [0, 0, H - 1, H - 1]])
+    xs = np.concatenate([rng.integers(0, W, 3000), [0, W - 1, 0, W - 1]])
+    ref, _ = oracle_mod.fabf_sep_pixels(f, th, s, taps, N, ys, xs)
+    assert g_err(g[ys, xs], ref) <= RTOL_G
+
+
+def test_sep_float32_output_and_host_buffers(ctx, oracle_mod):
+    f, th, s = inputs(45, 99, 77)
+    taps = synth.gaussian_taps(2.0)
+    ref, _ = oracle_mod.fabf_sep(f, th, s, taps, 5)
+    # host numpy buffers: staged, synchronous, status returned
+    out = np.zeros((45, 99), np.float32)
+    fabf.fabf_filter_sep(ctx, f, th, s, taps, 5, out=out, out_is_f64=False)
+    # binary64 result within 1e-9, then one rounding to binary32 (2^-24)
+    assert g_err(out, ref) <= 2.0 ** -24 + RTOL_G
+
+
+def test_sep_unaligned_pitch_takes_plain_load(ctx, oracle_mod):
+    # an image whose rows are 3 bytes apart from 16-byte alignment cannot use
+    # TMA; the plain cooperative load must give identical results
+    H, W = 50, 83
+    f, th, s = inputs(H, W, 78)
+    pitch = 87
+    buf = np.zeros((H, pitch), np.uint8)
+    buf[:, :W] = f
+    taps = synth.gaussian_taps(3.0)
+    out = fabf.fabf_filter_sep(ctx, dev(buf), dev(th), dev(s), taps, 4, pitch=pitch)
+    ref, _ = oracle_mod.fabf_sep(f, th, s, taps, 4)
+    assert g_err(out.cpu().numpy(), ref) <= RTOL_G
+
+
+def test_sep_constant_image_and_bad_sigma(ctx):
+    f = np.full((40, 70), 99, np.uint8)
+    th = f.astype(np.float32)
+    s = np.full(f.shape, 20.0, np.float32)
+    taps = synth.gaussian_taps(4.0)
+    out = fabf.fabf_filter_sep(ctx, dev(f), dev(th), dev(s), taps, 5)
+    torch.cuda.synchronize()
+    assert torch.equal(out, torch.full_like(out, 99.0))
+    s[3, 4] = 0.0
+    f2, th2, _ = inputs(40, 70, 3)
+    _, rc = fabf.fabf_filter_sep(ctx, f2, th2, s, taps, 5, check=False)
+    assert rc == fabf.FABF_EINVAL
+
+
+def test_sep_rejects_bad_taps(ctx):
+    f, th, s = inputs(8, 8, 1)
+    for taps, code in ((np.array([1, 0, 1], np.uint32), fabf.FABF_EINVAL),
+                       (np.full(5, 20000, np.uint32), fabf.FABF_EUNSUPPORTED),
+                       (np.ones(83, np.uint32), fabf.FABF_EUNSUPPORTED)):
+        _, rc = fabf.fabf_filter_sep(ctx, dev(f), dev(th), dev(s), taps, 3, check=False)
+        assert rc == code
+
+
+@pytest.mark.parametrize("use_f64", [True, False])
+def test_sep_bruteforce_matches_oracle(ctx, oracle_mod, use_f64):
+    f, th, s = inputs(61, 133, 91)
+    rng = np.random.default_rng(91)
+    taps = synth.random_taps(6, rng)
+    out = fabf.fabf_bruteforce_sep(ctx, dev(f), dev(th), dev(s), taps, use_f64=use_f64)
+    torch.cuda.synchronize()
+    ref = oracle_mod.bruteforce_sep(f, th, s, taps)
+    tol = 1e-12 if use_f64 else 2e-5
+    assert g_err(out.cpu().numpy(), ref) <= tol
