@@ -43,8 +43,8 @@ WORKLOAD = ("1920x1080 uint8 synthetic (200 blobs, 4 step edges, noise 10), box 
 # DRAM bytes (read + write) per launch of the fused FP64 kernel on this
 # workload, from the ncu capture in profiles/ (scaled from 4096x4096 by pixel
 # count); set to None whenever the kernel changes until it is re-captured.
-NCU_TRAFFIC_BYTES = 31.0e6         # FP64 form kernel (profiles/)
-NCU_TRAFFIC_BYTES_CFP32 = 24.3e6   # compensated FP32 kernel (profiles/)
+NCU_TRAFFIC_BYTES = None           # FP64 form kernel (profiles/)
+NCU_TRAFFIC_BYTES_CFP32 = None     # compensated FP32 kernel (profiles/)
 SM_COUNT, SM_MAX_MHZ = 152, 2070.0
 FP64_FLOP_PER_SM_CLK = 4.0        # 2 DFMA per clock per SM (nominal 1.25 TFLOP/s FP64)
 FORM_NAMES = {0: "fp64", 1: "fp64fit_fp32rec", 2: "cfp32"}
@@ -367,6 +367,53 @@ def run_serve(R, prec, seconds, rate=200.0, seed=4000, pool_size=16):
             "eagain_retries": eagain[0], "budget_bytes": 16 << 30}
 
 
+def run_gaussian(R, slot, steps, rhos=(3.0, 5.0), N=NDEG):
+    """The paper's own spatial kernel (Eq. (4), window [-3 rho, 3 rho]^2) on
+    the same 1920x1080 inputs: Mpix/s of the separable FABF kernel (FP64),
+    of the GPU brute-force filter with the same kernel (FP32 and FP64) and
+    PSNR of FABF against the FP64 brute force (Tables I and II)."""
+    torch, fabf, ctx = R.torch, R.fabf, R.ctx
+    from paper_1811_02308_gb300 import synth
+    f0, th0, s0, _ = slot[0]
+    npix = H_ * W_
+    peak = SM_COUNT * SM_MAX_MHZ * 1e6 * FP64_FLOP_PER_SM_CLK / 1e12
+    out = {}
+    for rho in rhos:
+        taps = synth.gaussian_taps(rho)
+        tp = np.ascontiguousarray(taps, np.uint32)
+        r = len(taps) // 2
+
+        def step(i):
+            f, th, sg, o = slot[i % len(slot)]
+            rc = R.lib.fabf_filter_sep(ctx.handle, f.data_ptr(), th.data_ptr(), sg.data_ptr(), H_, W_,
+                                       f.shape[1], tp.ctypes.data, r, N, o.data_ptr(), 1, R.sh)
+            if rc != 0:
+                raise fabf.FabfError(rc, "fabf_filter_sep")
+
+        total_ms, kern_ms = R.timed(step, steps, 3)
+        st, _ = fabf.fabf_get_status(ctx, R.sh)
+        g = fabf.fabf_filter_sep(ctx, f0, th0, s0, taps, N).cpu().numpy()
+        bf64 = fabf.fabf_bruteforce_sep(ctx, f0, th0, s0, taps, use_f64=True)
+        bf = bf64.cpu().numpy()
+        bf_rate = {}
+        for use64, n in ((True, 2), (False, 5)):
+            ms, _ = R.timed(lambda i, u=use64: fabf.fabf_bruteforce_sep(ctx, f0, th0, s0, taps, out=bf64, use_f64=u,
+                                                                         stream=R.sh), n, 1)
+            bf_rate["fp64" if use64 else "fp32"] = npix * n / (ms / 1e3) / 1e6
+        fl = fp64_flops_per_pixel(N, 0)
+        a = fl * npix / (kern_ms / 1e3) / 1e12
+        val = npix * steps / (total_ms / 1e3) / 1e6
+        out["rho=%g" % rho] = {
+            "r": r, "value": val, "unit": "Mpix/s", "kernel_ms": kern_ms, "status": st,
+            "psnr_vs_bruteforce_db": psnr(g, bf),
+            "bruteforce_gpu_mpix_per_s": bf_rate,
+            "speedup_vs_bruteforce_fp32": val / bf_rate["fp32"],
+            "fp64_roofline": {"achieved": a, "peak": peak, "unit": "TFLOP/s", "frac": a / peak,
+                              "flops_per_pixel": fl}}
+    return {"workload": "1920x1080 as above, Gaussian spatial kernel (integer taps, peak 1024), N=%d, FP64" % N,
+            **out}
+
+
 def sweep(args):
     """Config 1: 1920x1080 (200 blobs), theta = f + zeta, sigma in [5, 60];
     Mpix/s of every form for w in {5, 10, 20, 40} x N in {3, 4, 5, 6} (inputs
@@ -402,6 +449,20 @@ def sweep(args):
                 ms, _ = R.timed(lambda i, u=use64: fabf.fabf_bruteforce(ctx, f0, th0, s0, w, out=bfo, use_f64=u,
                                                                           stream=R.sh), n, 1)
                 res["bruteforce w=%d %s" % (w, "fp64" if use64 else "fp32")] = H_ * W_ * n / (ms / 1e3) / 1e6
+        # the Gaussian spatial kernel of Eq. (4): FABF (FP64) and the FP32 brute force
+        from paper_1811_02308_gb300 import synth
+        fabf.fabf_set_precision(ctx, 0)
+        for rho in (1.0, 3.0, 5.0, 10.0, 40.0 / 3.0):
+            taps = synth.gaussian_taps(rho)
+            for N in (3, 4, 5, 6):
+                ms, _ = R.timed(lambda i: fabf.fabf_filter_sep(ctx, *d_in[i % 4], taps, N, out=outs[0][i % 8],
+                                                                stream=R.sh), steps, 3)
+                res["gauss rho=%.3g,N=%d fp64" % (rho, N)] = H_ * W_ * steps / (ms / 1e3) / 1e6
+            f0, th0, s0 = d_in[0]
+            bfo = torch.empty((H_, W_), dtype=torch.float64, device=dev)
+            ms, _ = R.timed(lambda i: fabf.fabf_bruteforce_sep(ctx, f0, th0, s0, taps, out=bfo, use_f64=False,
+                                                                stream=R.sh), 3, 1)
+            res["gauss bruteforce rho=%.3g fp32" % rho] = H_ * W_ * 3 / (ms / 1e3) / 1e6
     print(json.dumps({"sweep_mpix_per_s": res, "workload": "1920x1080, theta=f+zeta, sigma in [5,60]"}),
           flush=True)
     return 0
@@ -458,6 +519,8 @@ def main():
     ap.add_argument("--profile", default=None, metavar="HxW",
                     help="profiling case: one input of this size, FP64 form only, no other legs")
     ap.add_argument("--profile-precision", type=int, default=0, choices=[0, 1, 2])
+    ap.add_argument("--profile-rho", type=float, default=None,
+                    help="with --profile: the separable Gaussian kernel of this rho instead of the box")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--no-extra", action="store_true", help="skip the batch and serve legs")
     ap.add_argument("--sweep", action="store_true",
@@ -510,10 +573,17 @@ def main():
 
     if args.profile:
         fabf.fabf_set_precision(ctx, args.profile_precision)
-        total_ms, _ = R.timed(lambda i: R.filt(slots[args.profile_precision][0], WR, NDEG), args.steps,
-                              args.warmup)
+        if args.profile_rho is not None:
+            from paper_1811_02308_gb300 import synth
+            taps = synth.gaussian_taps(args.profile_rho)
+            f, th, sg, o = slots[0][0]
+            total_ms, _ = R.timed(lambda i: fabf.fabf_filter_sep(ctx, f, th, sg, taps, NDEG, out=o, stream=R.sh),
+                                  args.steps, args.warmup)
+        else:
+            total_ms, _ = R.timed(lambda i: R.filt(slots[args.profile_precision][0], WR, NDEG), args.steps,
+                                  args.warmup)
         st, _ = fabf.fabf_get_status(ctx, R.sh)
-        print(json.dumps({"profile": args.profile, "precision": args.profile_precision,
+        print(json.dumps({"profile": args.profile, "precision": args.profile_precision, "rho": args.profile_rho,
                           "ms_per_step": total_ms / args.steps, "status": st}), flush=True)
         ctx.close()
         return 0
@@ -642,6 +712,7 @@ def main():
             "bruteforce_gpu": {k: {"ms_per_frame": v, "value": npix / (v / 1e3) / 1e6, "unit": "Mpix/s"}
                                for k, v in bf_ms.items()}}
     if rank == 0 and not args.no_extra and ws == 1:
+        line["gaussian"] = run_gaussian(R, slots[0], max(10, args.steps // 10))
         line["batch"] = {FORM_NAMES[p]: run_batch(R, p, max(5, args.steps // 20)) for p in (0, best)}
         line["serve"] = run_serve(R, best, args.serve_seconds)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

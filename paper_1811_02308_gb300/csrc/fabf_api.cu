@@ -195,7 +195,7 @@ int run_fused(fabf_ctx* ctx, const uint8_t* img, size_t pitch, const float* thet
               cudaStream_t s)
 {
     const int prec = dbg ? kPrecFP64 : ctx->precision;
-    const int TH = dbg ? kDefaultTileRows : tile_rows_for(ctx, w, N, prec);
+    const int TH = dbg ? kDefaultTileRows : tile_rows_for(ctx, w, N, prec, H, W);
     return run_fused_prec(ctx, prec, img, pitch, theta, sigma, H, W, w, N, out, out_f64, TH, dbg,
                           ctx->d_status, ctx->d_nfb, s);
 }
@@ -207,7 +207,7 @@ int launch_fused_scratch(const uint8_t* img, size_t pitch, const float* theta, c
                          unsigned long long* n_fallback, cudaStream_t s)
 {
     return run_fused_prec(nullptr, kPrecFP64, img, pitch, theta, sigma, H, W, w, N, out, out_f64,
-                          kDefaultTileRows, nullptr, status, n_fallback, s);
+                          tile_rows_for(nullptr, w, N, kPrecFP64, H, W), nullptr, status, n_fallback, s);
 }
 
 }  // namespace fabf

@@ -26,8 +26,9 @@ namespace fabf {
 // ===========================================================================
 namespace {
 
-constexpr int kTuneH = 512, kTuneW = 1024;
-constexpr int kTuneCandidates[] = {8, 16, 32, 64};
+// Large enough that the tallest candidate still gives several waves of CTAs,
+// so the measurement is the steady-state cost per tile height.
+constexpr int kTuneH = 2048, kTuneW = 4096;
 
 struct TuneImage {
     uint8_t* img = nullptr;
@@ -110,9 +111,10 @@ void load_tune_cache(fabf_ctx* ctx)
 
 }  // namespace
 
-int tile_rows_for(fabf_ctx* ctx, int w, int N, int prec)
+static int steady_tile_rows(fabf_ctx* ctx, int w, int N, int prec)
 {
-    if (!ctx || !ctx->autotune) return kDefaultTileRows;
+    const int dflt = kSteadyTileRows[prec < 0 || prec > 2 ? 0 : prec];
+    if (!ctx || !ctx->autotune) return dflt;
     load_tune_cache(ctx);
     std::lock_guard<std::mutex> g(ctx->tune_lock);
     auto it = ctx->tune.find(tune_key(w, N, prec));
@@ -122,16 +124,16 @@ int tile_rows_for(fabf_ctx* ctx, int w, int N, int prec)
     {
         std::lock_guard<std::mutex> gi(g_tune_img_lock);
         t = &g_tune_img[ctx->device];
-        if (ensure_tune_image(*t) != FABF_OK) return kDefaultTileRows;
+        if (ensure_tune_image(*t) != FABF_OK) return dflt;
     }
     cudaStream_t s;
-    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return kDefaultTileRows;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return dflt;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    int best = kDefaultTileRows;
+    int best = dflt;
     float best_ms = 1e30f;
-    for (int TH : kTuneCandidates) {
+    for (int TH : kTileCandidates) {
         float ms = 1e30f;
         bool ok = true;
         for (int rep = 0; rep < 4 && ok; ++rep) {
@@ -160,6 +162,34 @@ int tile_rows_for(fabf_ctx* ctx, int w, int N, int prec)
             std::fprintf(fp, "%d %d %d %d %.5f\n", w, N, prec, best, best_ms);
             std::fclose(fp);
         }
+    }
+    return best;
+}
+
+int tile_rows_for(fabf_ctx* ctx, int w, int N, int prec, int H, int W)
+{
+    const int steady = steady_tile_rows(ctx, w, N, prec);
+    if (H <= 0 || W <= 0 || steady <= kTileCandidates[0]) return steady;
+    int num_sms = ctx ? ctx->num_sms : 0;
+    if (num_sms <= 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return kTileCandidates[0];
+        }
+    }
+    const int pc = prec < 0 || prec > 2 ? 0 : prec;
+    int off, Cb;
+    fused_geometry(w, &off, &Cb);
+    const long long tiles_x = (W + kTileW - 1) / kTileW;
+    int best = kTileCandidates[0];
+    for (int TH : kTileCandidates) {
+        if (TH > steady) break;
+        const size_t smem = fused_smem_bytes(N, w, Cb, TH) + 1024;      // + the per-CTA reservation
+        const int per_sm = std::max(1, std::min(pc == kPrecFP64 ? 2 : 3, (int)((size_t)228 * 1024 / smem)));
+        const long long tiles = tiles_x * ((H + TH - 1) / TH);
+        if (tiles >= (long long)kMinWaves[pc] * num_sms * per_sm) best = TH;
     }
     return best;
 }
@@ -209,7 +239,7 @@ static int batch_build(fabf_ctx* ctx, const fabf_request* reqs, int n)
     size_t smem = 0;
     for (int i = 0; i < n; ++i) {
         const fabf_request& r = reqs[order[i]];
-        const int TH = tile_rows_for(ctx, r.w, r.N, prec);
+        const int TH = tile_rows_for(ctx, r.w, r.N, prec, 0, 0);
         const size_t sm = make_job(&jobs[i], &tmaps[i], r.img, r.pitch, r.theta, r.sigma, r.H, r.W, r.w, r.N,
                                    r.out, r.out_is_f64, TH);
         jobs[i].tile_begin = tiles;
@@ -516,7 +546,7 @@ static int serve_enqueue(fabf_ctx* ctx, ServeState* S, ServeReq* q)
             rc = cuda_status(cudaGetLastError());
             if (rc) break;
         }
-        const int TH = tile_rows_for(ctx, r.w, r.N, ctx->precision);
+        const int TH = tile_rows_for(ctx, r.w, r.N, ctx->precision, r.H, r.W);
         rc = run_fused_prec(ctx, ctx->precision, q->d_img, (size_t)r.W, q->d_theta, q->d_sigma, r.H, r.W, r.w,
                             r.N, q->d_out, r.out_is_f64, TH, nullptr, q->d_status, q->d_nfb, s);
     }
@@ -664,7 +694,7 @@ int fabf_tile_rows(fabf_ctx* ctx, int w, int N, int precision, int* tile_rows)
     if (!ctx || !tile_rows || w < 1 || N < 0 || precision < FABF_FP64 || precision > FABF_CFP32) return FABF_EINVAL;
     if (w > kWMax || N > kNMax) return FABF_EUNSUPPORTED;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return FABF_ECUDA;
-    *tile_rows = tile_rows_for(ctx, w, N, precision);
+    *tile_rows = tile_rows_for(ctx, w, N, precision, 0, 0);
     return FABF_OK;
 }
 

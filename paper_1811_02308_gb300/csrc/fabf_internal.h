@@ -86,10 +86,19 @@ int launch_fused_scratch(const uint8_t* img, size_t pitch, const float* theta, c
                          int W, int w, int N, void* out, int out_f64, unsigned* status,
                          unsigned long long* n_fallback, cudaStream_t s);
 
-// Output rows per tile for (w, N, prec): the autotuner's choice when the
-// context has autotune on (measured once and cached), else the default.
-int tile_rows_for(fabf_ctx* ctx, int w, int N, int prec);
-constexpr int kDefaultTileRows = 32;
+// Output rows per tile (a multiple of 8).  The steady-state choice for
+// (w, N, prec) -- the autotuner's measurement when the context has autotune
+// on, else kSteadyTileRows[prec] -- holds when many tiles are in flight (H = W
+// = 0: batches).  For one H x W image the choice is the tallest candidate
+// no taller than the steady one that still leaves kMinWaves[prec] waves of
+// resident CTAs across the SMs, else the shortest candidate: a short image
+// with tall tiles leaves SMs idle in the last wave.  Measured at 720p, 1080p
+// and 4096^2 for w in {5, 10, 20, 40}.
+int tile_rows_for(fabf_ctx* ctx, int w, int N, int prec, int H, int W);
+constexpr int kTileCandidates[] = {8, 16, 24, 32, 40};
+constexpr int kSteadyTileRows[3] = {8, 16, 32};   // FP64, FP64 fit + FP32, compensated FP32
+constexpr int kMinWaves[3] = {1, 20, 4};
+constexpr int kDefaultTileRows = 32;               // stage-export runs of the tests
 
 int read_and_clear_status(fabf_ctx* ctx, cudaStream_t s, int* status, uint64_t* nfb, uint64_t* nredo);
 

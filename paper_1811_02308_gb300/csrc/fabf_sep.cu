@@ -404,8 +404,7 @@ __global__ void __launch_bounds__(256)
     else static_cast<float*>(out)[pix] = (float)g;
 }
 
-constexpr int kSepTileRows = 32;
-constexpr int kSepMaxDynSmem = 110 * 1024;   // >= sep_smem_bytes for every r <= 40, N <= 6 at 32 rows
+constexpr int kSepMaxDynSmem = 110 * 1024;   // >= sep_smem_bytes for every r <= 40, N <= 6, TH <= 40
 
 template <int N>
 static cudaError_t launch_sep_one(const CUtensorMap& tm, const SepParams& p, dim3 grid, size_t smem, cudaStream_t s)
@@ -455,18 +454,18 @@ static int make_taps(const uint32_t* taps, int r, SepTaps* T)
 }
 
 static int run_sep(const SepTaps& T, const uint8_t* img, size_t pitch, const float* theta, const float* sigma, int H,
-                   int W, int N, void* out, int out_f64, const SepDebug* dbg, unsigned* status,
+                   int W, int N, void* out, int out_f64, int TH, const SepDebug* dbg, unsigned* status,
                    unsigned long long* nfb, cudaStream_t s)
 {
     SepParams p;
     std::memset(&p, 0, sizeof(p));
     CUtensorMap tm;
-    (void)make_job(&p.job, &tm, img, pitch, theta, sigma, H, W, T.r, N, out, out_f64, kSepTileRows);
+    (void)make_job(&p.job, &tm, img, pitch, theta, sigma, H, W, T.r, N, out, out_f64, TH);
     p.taps = T;
     p.status = status;
     p.n_fallback = nfb;
     if (dbg) p.dbg = *dbg;
-    const size_t smem = sep_smem_bytes(N, T.r, p.job.Cb, kSepTileRows);
+    const size_t smem = sep_smem_bytes(N, T.r, p.job.Cb, TH);
     dim3 grid(p.job.tiles_x, p.job.tiles_y);
     return cuda_status(launch_sep(N, tm, p, grid, smem, s));
 }
@@ -505,7 +504,9 @@ int fabf_filter_sep(fabf_ctx* ctx, const uint8_t* img, const float* theta, const
     return with_device_buffers(
         ctx, img, theta, sigma, H, W, pitch, out, out_is_f64, s,
         [&](const uint8_t* d_img, size_t d_pitch, const float* d_th, const float* d_sg, void* d_out) {
-            return run_sep(T, d_img, d_pitch, d_th, d_sg, H, W, N, d_out, out_is_f64, nullptr, ctx->d_status,
+            // binary64 throughout: the FP64 form's tile rule (8 rows)
+            const int TH = tile_rows_for(nullptr, r, N, kPrecFP64, H, W);
+            return run_sep(T, d_img, d_pitch, d_th, d_sg, H, W, N, d_out, out_is_f64, TH, nullptr, ctx->d_status,
                            ctx->d_nfb, s);
         });
 }
@@ -524,7 +525,7 @@ int fabf_debug_stages_sep(fabf_ctx* ctx, const uint8_t* img, const float* theta,
     if (rc) return rc;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return FABF_ECUDA;
     SepDebug d{alpha, beta, m, M, mu, c, t0lam, I, T, flags};
-    rc = run_sep(tp, img, pitch, theta, sigma, H, W, N, out, 1, &d, ctx->d_status, ctx->d_nfb, 0);
+    rc = run_sep(tp, img, pitch, theta, sigma, H, W, N, out, 1, kDefaultTileRows, &d, ctx->d_status, ctx->d_nfb, 0);
     if (rc) return rc;
     int st = FABF_OK;
     rc = read_and_clear_status(ctx, 0, &st, nullptr, nullptr);

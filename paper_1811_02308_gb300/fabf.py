@@ -131,6 +131,45 @@ def _ptr(a) -> int:
     raise TypeError("expected a torch tensor or numpy array, got %r" % type(a))
 
 
+def _check_out(out, H: int, W: int, f64: bool) -> None:
+    """The output buffer must hold H x W elements of the type out_is_f64 names
+    (the kernels write H x W float64 or float32 values through its pointer)."""
+    if out is None:
+        raise ValueError("an output buffer is required")
+    if _is_torch(out):
+        esize, n = out.element_size(), out.numel()
+        if not out.dtype.is_floating_point:
+            raise ValueError("output must be float32 or float64")
+    else:
+        esize, n = out.dtype.itemsize, out.size
+        if out.dtype.kind != "f":
+            raise ValueError("output must be float32 or float64")
+    if esize != (8 if f64 else 4):
+        raise ValueError("output element size %d does not match out_is_f64=%s" % (esize, f64))
+    if n < H * W:
+        raise ValueError("output holds %d elements, %d needed" % (n, H * W))
+
+
+def _check_inputs(img, theta, sigma, H: int, W: int, pitch: int) -> None:
+    """img must be uint8 with at least (H-1) pitch + W bytes; theta and sigma
+    float32 with H x W elements (what the kernels read through the pointers)."""
+    def info(a):
+        if _is_torch(a):
+            return a.element_size(), a.numel(), str(a.dtype)
+        return a.dtype.itemsize, a.size, str(a.dtype)
+    e, n, dt = info(img)
+    if e != 1 or "uint8" not in dt:
+        raise ValueError("img must be uint8, got %s" % dt)
+    if pitch < W or n < (H - 1) * pitch + W:
+        raise ValueError("img holds %d bytes, (H-1)*pitch+W = %d needed" % (n, (H - 1) * pitch + W))
+    for name, a in (("theta", theta), ("sigma", sigma)):
+        e, n, dt = info(a)
+        if "float32" not in dt:
+            raise ValueError("%s must be float32, got %s" % (name, dt))
+        if n < H * W:
+            raise ValueError("%s holds %d elements, %d needed" % (name, n, H * W))
+
+
 def _stream_of(*arrays) -> int:
     for a in arrays:
         if _is_torch(a) and a.is_cuda:
@@ -196,6 +235,8 @@ def fabf_filter(ctx: Context, img, theta, sigma, w: int, N: int, out=None, out_i
     p = int(pitch) if pitch is not None else int(img.shape[1])
     if out is None:
         out = _empty_like_out(theta, H, W, out_is_f64)
+    _check_out(out, H, W, out_is_f64)
+    _check_inputs(img, theta, sigma, H, W, p)
     s = _stream_of(img, theta, sigma, out) if stream is None else stream
     rc = load().fabf_filter(ctx.handle, _ptr(img), _ptr(theta), _ptr(sigma), H, W, p, int(w), int(N),
                             _ptr(out), 1 if out_is_f64 else 0, s)
@@ -211,6 +252,8 @@ def fabf_filter_noalloc(img, theta, sigma, w: int, N: int, out, out_is_f64: bool
     Returns (status, n_fallback)."""
     H, W = int(theta.shape[0]), int(theta.shape[1])
     p = int(pitch) if pitch is not None else int(img.shape[1])
+    _check_out(out, H, W, out_is_f64)
+    _check_inputs(img, theta, sigma, H, W, p)
     s = _stream_of(img, theta, sigma, out) if stream is None else stream
     nf = C.c_uint64(0)
     rc = load().fabf_filter_noalloc(_ptr(img), _ptr(theta), _ptr(sigma), H, W, p, int(w), int(N),
@@ -291,6 +334,8 @@ def fabf_bruteforce(ctx: Context, img, theta, sigma, w: int, out=None, out_is_f6
     H, W = int(theta.shape[0]), int(theta.shape[1])
     if out is None:
         out = _empty_like_out(theta, H, W, out_is_f64)
+    _check_out(out, H, W, out_is_f64)
+    _check_inputs(img, theta, sigma, H, W, int(img.shape[1]))
     s = _stream_of(img, theta, sigma, out) if stream is None else stream
     _check(load().fabf_bruteforce(ctx.handle, _ptr(img), _ptr(theta), _ptr(sigma), H, W,
                                   int(img.shape[1]), int(w), _ptr(out), 1 if out_is_f64 else 0,
@@ -322,6 +367,8 @@ def fabf_filter_sep(ctx: Context, img, theta, sigma, taps, N: int, out=None, out
     p = int(pitch) if pitch is not None else int(img.shape[1])
     if out is None:
         out = _empty_like_out(theta, H, W, out_is_f64)
+    _check_out(out, H, W, out_is_f64)
+    _check_inputs(img, theta, sigma, H, W, p)
     s = _stream_of(img, theta, sigma, out) if stream is None else stream
     rc = load().fabf_filter_sep(ctx.handle, _ptr(img), _ptr(theta), _ptr(sigma), H, W, p, t.ctypes.data,
                                 len(t) // 2, int(N), _ptr(out), 1 if out_is_f64 else 0, s)
@@ -366,6 +413,8 @@ def fabf_bruteforce_sep(ctx: Context, img, theta, sigma, taps, out=None, out_is_
     H, W = int(theta.shape[0]), int(theta.shape[1])
     if out is None:
         out = _empty_like_out(theta, H, W, out_is_f64)
+    _check_out(out, H, W, out_is_f64)
+    _check_inputs(img, theta, sigma, H, W, int(img.shape[1]))
     s = _stream_of(img, theta, sigma, out) if stream is None else stream
     _check(load().fabf_bruteforce_sep(ctx.handle, _ptr(img), _ptr(theta), _ptr(sigma), H, W,
                                       int(img.shape[1]), t.ctypes.data, len(t) // 2, _ptr(out),
@@ -377,8 +426,10 @@ def fabf_bruteforce_sep(ctx: Context, img, theta, sigma, taps, out=None, out_is_
 def make_request(img, theta, sigma, w: int, N: int, out, out_is_f64: bool = True, passes: int = 1,
                  sigma_decay: float = 0.8, pitch: int | None = None) -> Request:
     H, W = int(theta.shape[0]), int(theta.shape[1])
-    return Request(_ptr(img), _ptr(theta), _ptr(sigma), H, W,
-                   int(pitch) if pitch is not None else int(img.shape[1]), int(w), int(N),
+    p = int(pitch) if pitch is not None else int(img.shape[1])
+    _check_out(out, H, W, out_is_f64)
+    _check_inputs(img, theta, sigma, H, W, p)
+    return Request(_ptr(img), _ptr(theta), _ptr(sigma), H, W, p, int(w), int(N),
                    int(passes), float(sigma_decay), _ptr(out), 1 if out_is_f64 else 0)
 
 

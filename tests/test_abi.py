@@ -89,3 +89,25 @@ def test_separable_argument_checks_without_gpu(lib):
     assert lib.fabf_gaussian_taps(3.0, buf.ctypes.data, 18, C.byref(r)) == fabf.FABF_EINVAL
     null = C.c_void_p(0)
     assert lib.fabf_filter_sep(null, 0, 0, 0, 4, 4, 4, buf.ctypes.data, 1, 1, 0, 1, 0) == fabf.FABF_EINVAL
+
+
+def test_binding_rejects_mismatched_buffers():
+    # the binding checks buffer types and sizes before any pointer reaches
+    # a kernel (a float32 output passed with out_is_f64 = True would be
+    # written past its end)
+    H, W = 4, 6
+    img = np.zeros((H, W), np.uint8)
+    th = np.zeros((H, W), np.float32)
+    fabf._check_out(np.zeros((H, W), np.float64), H, W, True)
+    fabf._check_out(np.zeros((H, W), np.float32), H, W, False)
+    fabf._check_inputs(img, th, th, H, W, W)
+    bad_out = [(np.zeros((H, W), np.float32), True), (np.zeros((H, W), np.float64), False),
+               (np.zeros((H, W - 1), np.float64), True), (np.zeros((H, W), np.int64), True)]
+    for out, f64 in bad_out:
+        with pytest.raises(ValueError):
+            fabf._check_out(out, H, W, f64)
+    bad_in = [(np.zeros((H, W), np.int8), th, th, W), (img, th.astype(np.float64), th, W),
+              (img, th, th[:, :-1], W), (img, th, th, W + 1), (img, th, th, W - 1)]
+    for a, b, c, p in bad_in:
+        with pytest.raises(ValueError):
+            fabf._check_inputs(a, b, c, H, W, p)

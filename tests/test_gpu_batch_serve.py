@@ -137,10 +137,44 @@ def test_autotuned_tiles_give_identical_results():
     with fabf.Context(device=0, autotune=1) as tc, fabf.Context(device=0) as dc:
         for w, N in [(5, 5), (20, 6), (40, 3)]:
             th_rows = fabf.fabf_tile_rows(tc, w, N)
-            assert th_rows in (8, 16, 32, 64)
-            assert fabf.fabf_tile_rows(dc, w, N) == 32
+            assert th_rows in (8, 16, 24, 32, 40)
+            assert fabf.fabf_tile_rows(dc, w, N) == 8
+            assert fabf.fabf_tile_rows(dc, w, N, fabf.FABF_FP64FIT_FP32REC) == 16
+            assert fabf.fabf_tile_rows(dc, w, N, fabf.FABF_CFP32) == 32
             a = fabf.fabf_filter(tc, dev(f), dev(th), dev(s), w, N).cpu().numpy()
             b = fabf.fabf_filter(dc, dev(f), dev(th), dev(s), w, N).cpu().numpy()
+            assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("prec", [fabf.FABF_FP64, fabf.FABF_FP64FIT_FP32REC, fabf.FABF_CFP32])
+def test_every_tile_height_gives_identical_results(tmp_path, prec):
+    # the per-pixel arithmetic does not depend on the tiling: forcing each
+    # candidate height (through the tune cache; batches use the steady-state
+    # height as it is) must give the same bits, on images whose row counts
+    # are not multiples of any height; the single-image call (size-aware
+    # height) must agree too
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    imgs = [synth.make_inputs(H, W, 78 + H, n_blobs=30, zeta_range=(-20, 20), sigma_range=(5, 60))
+            for H, W in ((419, 1283), (77, 130))]
+    d = [[dev(a) for a in im] for im in imgs]
+    f64 = prec == fabf.FABF_FP64
+    odt = torch.float64 if f64 else torch.float32
+    results = []
+    for TH in (8, 16, 24, 32, 40):
+        path = tmp_path / ("tune_%d.txt" % TH)
+        path.write_text("20 5 %d %d 0.0\n" % (prec, TH))
+        with fabf.Context(device=0, precision=prec, autotune=1, tune_cache_path=str(path)) as c:
+            assert fabf.fabf_tile_rows(c, 20, 5, prec) == TH
+            outs = [torch.empty(im[1].shape, dtype=odt, device="cuda") for im in d]
+            reqs = [fabf.make_request(*im, 20, 5, o, out_is_f64=f64) for im, o in zip(d, outs)]
+            fabf.fabf_filter_batch(c, reqs)
+            torch.cuda.synchronize()
+            results.append([o.cpu().numpy() for o in outs])
+            single = fabf.fabf_filter(c, *d[0], 20, 5, out_is_f64=f64).cpu().numpy()
+            assert np.array_equal(single, results[-1][0])
+    for r in results[1:]:
+        for a, b in zip(r, results[0]):
             assert np.array_equal(a, b)
 
 
