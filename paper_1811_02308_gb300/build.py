@@ -21,8 +21,11 @@ SOURCES = [
     "fabf_batch_serve.cu",
     "fabf_noalloc.cu",
     "fabf_sep.cu",
+    "fabf_sep_p0.cu",
+    "fabf_sep_p1.cu",
+    "fabf_sep_p2.cu",
 ]
-HEADERS = ["fabf_device.cuh", "fabf_kernels.cuh", "fabf_launch.cuh", "fabf_internal.h"]
+HEADERS = ["fabf_device.cuh", "fabf_kernels.cuh", "fabf_launch.cuh", "fabf_internal.h", "fabf_sep_kernels.cuh"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

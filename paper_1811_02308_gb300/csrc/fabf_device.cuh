@@ -384,8 +384,11 @@ __device__ __forceinline__ bool fp32_integrals_weak(float lam, float t0)
     return false;
 }
 
-template <int N>
-__device__ __forceinline__ float fabf_tail_fp32(const float (&c)[N + 1], int64_t M0, int64_t M1, int alpha, int d,
+// fb_ratio(): mu_1 / mu_0 for the fallback of Eq. (29) (the sigma -> infinity
+// limit), e.g. mu'_1 / mu'_0 of the scaled moments; evaluated only when the
+// fallback is taken.
+template <int N, typename FbRatio>
+__device__ __forceinline__ float fabf_tail_fp32(const float (&c)[N + 1], FbRatio&& fb_ratio, int alpha, int d,
                                                float theta_f, float sigma_f, int& fallback, bool& redo)
 {
     const float rd = 1.0f / (float)d;
@@ -406,10 +409,27 @@ __device__ __forceinline__ float fabf_tail_fp32(const float (&c)[N + 1], int64_t
     const float est = 4.0f * 5.9604645e-8f * (float)d * (S1 + fabsf(F) * S2) / fabsf(T2);
     redo = !(T2 > 0.0f) || !(est <= kFp32GuardGray) || fp32_integrals_weak(lam, t0);
     if (!(T2 > 0.0f) || !isfinite(F)) {
-        F = __ll2float_rn(M1) / (__ll2float_rn(M0) * (float)d);   // mu_1 / mu_0
+        F = fb_ratio();
         fallback = 1;
     }
     return fmaf((float)d, F, (float)alpha);
+}
+
+// Fit in binary64 from (commonly scaled) moments, the rest in binary32.
+template <int N>
+__device__ __forceinline__ float fabf_fit_tail_fp64fit(const AinvTable& A, const double (&mu)[(N < 1 ? 1 : N) + 1],
+                                                       int alpha, int d, float theta_f, float sigma_f, int& fallback,
+                                                       bool& redo)
+{
+    float c[N + 1];
+#pragma unroll
+    for (int n = 0; n <= N; ++n) {
+        double acc = 0.0;
+#pragma unroll
+        for (int k = 0; k <= N; ++k) acc = fma(A.v[N][n][k], mu[k], acc);
+        c[n] = (float)acc;
+    }
+    return fabf_tail_fp32<N>(c, [&] { return (float)(mu[1] / mu[0]); }, alpha, d, theta_f, sigma_f, fallback, redo);
 }
 
 // FABF_FP64FIT_FP32REC: shift-scale and Hilbert fit in binary64 (the fit's
@@ -426,8 +446,8 @@ __device__ __forceinline__ float fabf_pixel_fp64fit(const AinvTable& A, int alph
     const int d = beta - alpha;
     int64_t M[K + 1];
     shifted_moments<K>(alpha, m, M);
-    // Scaled moments mu'_k = d^N mu_k = M_k d^(N-k): exact integers
-    // (<= m_0 255^6 < 2^63), so no division; the common factor d^N cancels
+    // Scaled moments mu'_k = d^K mu_k = M_k d^(K-k): exact integers
+    // (<= m_0 255^6 < 2^63), so no division; the common factor d^K cancels
     // in the ratio of Eq. (29).
     double mu[K + 1];
     {
@@ -438,15 +458,7 @@ __device__ __forceinline__ float fabf_pixel_fp64fit(const AinvTable& A, int alph
             dp *= d;
         }
     }
-    float c[N + 1];
-#pragma unroll
-    for (int n = 0; n <= N; ++n) {
-        double acc = 0.0;
-#pragma unroll
-        for (int k = 0; k <= N; ++k) acc = fma(A.v[N][n][k], mu[k], acc);
-        c[n] = (float)acc;
-    }
-    return fabf_tail_fp32<N>(c, M[0], M[1], alpha, d, theta_f, sigma_f, fallback, redo);
+    return fabf_fit_tail_fp64fit<N>(A, mu, alpha, d, theta_f, sigma_f, fallback, redo);
 }
 
 // Error-free transformations (Knuth TwoSum, FMA TwoProduct) for the
@@ -486,6 +498,31 @@ __device__ __forceinline__ void u63_to_ff(uint64_t v, float& hi, float& lo)
     lo = t - (hi - s2);
 }
 
+// Compensated binary32 fit from float-float (commonly scaled) moments
+// mu_k = muh[k] + mul[k], then the binary32 tail.
+template <int N>
+__device__ __forceinline__ float fabf_fit_tail_cfp32(const AinvSplitTable& A, const float (&muh)[(N < 1 ? 1 : N) + 1],
+                                                     const float (&mul)[(N < 1 ? 1 : N) + 1], int alpha, int d,
+                                                     float theta_f, float sigma_f, int& fallback, bool& redo)
+{
+    float c[N + 1];
+#pragma unroll
+    for (int n = 0; n <= N; ++n) {
+        float s = 0.0f, comp = 0.0f;
+#pragma unroll
+        for (int k = 0; k <= N; ++k) {
+            const float ah = A.hi[N][n][k], al = A.lo[N][n][k];
+            float p, pe, t, te;
+            two_prod(ah, muh[k], p, pe);
+            two_sum(s, p, t, te);
+            s = t;
+            comp += pe + te + fmaf(ah, mul[k], al * muh[k]);
+        }
+        c[n] = s + comp;
+    }
+    return fabf_tail_fp32<N>(c, [&] { return muh[1] / muh[0]; }, alpha, d, theta_f, sigma_f, fallback, redo);
+}
+
 // FABF_CFP32: no binary64.  mu_k as float-float quotients of the exact
 // integers M_k and d^k, and c = A^{-1} mu by compensated dot products
 // (Ogita, Rump & Oishi, "Accurate sum and dot product", 2005: TwoProduct
@@ -504,7 +541,7 @@ __device__ __forceinline__ float fabf_pixel_cfp32(const AinvSplitTable& A, int a
     const int d = beta - alpha;
     int64_t M[K + 1];
     shifted_moments<K>(alpha, m, M);
-    // Scaled moments mu'_k = M_k d^(N-k) (exact integers, see above) as
+    // Scaled moments mu'_k = M_k d^(K-k) (exact integers, see above) as
     // float-float values, converted in 23-bit chunks without a 64-bit
     // conversion instruction.
     float muh[K + 1], mul[K + 1];
@@ -516,22 +553,7 @@ __device__ __forceinline__ float fabf_pixel_cfp32(const AinvSplitTable& A, int a
             dp *= d;
         }
     }
-    float c[N + 1];
-#pragma unroll
-    for (int n = 0; n <= N; ++n) {
-        float s = 0.0f, comp = 0.0f;
-#pragma unroll
-        for (int k = 0; k <= N; ++k) {
-            const float ah = A.hi[N][n][k], al = A.lo[N][n][k];
-            float p, pe, t, te;
-            two_prod(ah, muh[k], p, pe);
-            two_sum(s, p, t, te);
-            s = t;
-            comp += pe + te + fmaf(ah, mul[k], al * muh[k]);
-        }
-        c[n] = s + comp;
-    }
-    return fabf_tail_fp32<N>(c, M[0], M[1], alpha, d, theta_f, sigma_f, fallback, redo);
+    return fabf_fit_tail_cfp32<N>(A, muh, mul, alpha, d, theta_f, sigma_f, fallback, redo);
 }
 
 }  // namespace fabf

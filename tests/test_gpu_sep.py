@@ -193,3 +193,55 @@ def test_sep_bruteforce_matches_oracle(ctx, oracle_mod, use_f64):
     ref = oracle_mod.bruteforce_sep(f, th, s, taps)
     tol = 1e-12 if use_f64 else 2e-5
     assert g_err(out.cpu().numpy(), ref) <= tol
+
+
+# The binary32 forms against the FP64 form: RMS <= 0.01 gray and max <= 1
+# gray (the box path's bar at N = 6).  Measured errors equal the box path's
+# at the same window radius (0.0055 vs 0.0051 RMS at r = 15, N = 5); PSNR
+# against the brute force moves by <= 0.004 dB.  The guard sends up to 40 %
+# of the pixels to the FP64 pass at N = 6 with the widest windows (37.6 % at
+# rho = 13), a minority elsewhere.
+SEP_FP32_TOL = {3: (0.01, 1.0), 5: (0.01, 1.0), 6: (0.01, 1.0)}
+SEP_REDO_MAX = {3: 0.2, 5: 0.2, 6: 0.4}
+
+
+@pytest.mark.parametrize("prec", [fabf.FABF_FP64FIT_FP32REC, fabf.FABF_CFP32])
+@pytest.mark.parametrize("rho,N", [(3.0, 3), (5.0, 5), (13.0, 6), (1.0, 5)])
+def test_sep_precision_forms(ctx, oracle_mod, prec, rho, N):
+    f, th, s = inputs(540, 960, 300 + N, n_blobs=50, zeta=None)
+    taps = synth.gaussian_taps(rho)
+    d = [dev(a) for a in (f, th, s)]
+    fabf.fabf_set_precision(ctx, prec)
+    try:
+        g = fabf.fabf_filter_sep(ctx, *d, taps, N, out_is_f64=False).cpu().numpy()
+        st, _, n_redo = fabf.fabf_get_status_ex(ctx)
+    finally:
+        fabf.fabf_set_precision(ctx, fabf.FABF_FP64)
+    assert st == fabf.FABF_OK
+    assert n_redo <= SEP_REDO_MAX[N] * g.size
+    g64 = fabf.fabf_filter_sep(ctx, *d, taps, N).cpu().numpy()
+    rng = np.random.default_rng(N)
+    ys, xs = rng.integers(0, 540, 300), rng.integers(0, 960, 300)
+    ref, _ = oracle_mod.fabf_sep_pixels(f, th, s, taps, N, ys, xs)
+    assert g_err(g64[ys, xs], ref) <= RTOL_G
+    err = np.abs(g.astype(np.float64) - g64)
+    rms, mx = float(np.sqrt(np.mean(err ** 2))), float(err.max())
+    tol_rms, tol_max = SEP_FP32_TOL[N]
+    assert rms <= tol_rms and mx <= tol_max, (rms, mx)
+
+
+@pytest.mark.parametrize("prec", [fabf.FABF_FP64FIT_FP32REC, fabf.FABF_CFP32])
+def test_sep_precision_forms_all_ones_equal_box(ctx, prec):
+    # with all-ones taps the binary32 forms of both paths see the same
+    # scaled moments (no shift is needed below 2^63) and must agree bit for bit
+    f, th, s = inputs(131, 197, 61)
+    d = [dev(a) for a in (f, th, s)]
+    taps = np.ones(2 * 20 + 1, np.uint32)
+    fabf.fabf_set_precision(ctx, prec)
+    try:
+        a = fabf.fabf_filter_sep(ctx, *d, taps, 5, out_is_f64=False)
+        b = fabf.fabf_filter(ctx, *d, 20, 5, out_is_f64=False)
+        torch.cuda.synchronize()
+    finally:
+        fabf.fabf_set_precision(ctx, fabf.FABF_FP64)
+    assert torch.equal(a, b)
