@@ -505,18 +505,28 @@ __device__ __forceinline__ float fabf_fit_tail_cfp32(const AinvSplitTable& A, co
                                                      const float (&mul)[(N < 1 ? 1 : N) + 1], int alpha, int d,
                                                      float theta_f, float sigma_f, int& fallback, bool& redo)
 {
+    // The entries are compile-time constants after unrolling (immediate
+    // operands); their low halves are zero for N <= 5 (entries < 2^24), and
+    // those products are skipped.  The first product is exact as s + comp.
+    (void)A;
+    constexpr AinvSplitTable kA = make_ainv_split_table();
     float c[N + 1];
 #pragma unroll
     for (int n = 0; n <= N; ++n) {
-        float s = 0.0f, comp = 0.0f;
+        float s, comp;
+        two_prod(kA.hi[N][n][0], muh[0], s, comp);
+        comp = fmaf(kA.hi[N][n][0], mul[0], comp);
+        if (kA.lo[N][n][0] != 0.0f) comp = fmaf(kA.lo[N][n][0], muh[0], comp);
 #pragma unroll
-        for (int k = 0; k <= N; ++k) {
-            const float ah = A.hi[N][n][k], al = A.lo[N][n][k];
+        for (int k = 1; k <= N; ++k) {
+            const float ah = kA.hi[N][n][k], al = kA.lo[N][n][k];
             float p, pe, t, te;
             two_prod(ah, muh[k], p, pe);
             two_sum(s, p, t, te);
             s = t;
-            comp += pe + te + fmaf(ah, mul[k], al * muh[k]);
+            float e = fmaf(ah, mul[k], pe + te);
+            if (al != 0.0f) e = fmaf(al, muh[k], e);
+            comp += e;
         }
         c[n] = s + comp;
     }

@@ -14,8 +14,9 @@
 //     owns tile column c; it keeps running window sums of f^k (k = 1..N,
 //     Eq. (17) with omega == 1, rows clipped to the image) in registers
 //     across chunks (add the entering row, subtract the leaving row), and
-//     takes the vertical min / max of the 8 windows of a chunk from their
-//     common core plus at most 7 extra rows each (Eq. (8)).
+//     takes the vertical min / max of the 8 windows of a chunk as suffix
+//     extrema of the chunk's own 8 rows combined with prefix extrema of the
+//     rows below, 2w + 8 row visits per chunk (Eq. (8)).
 //  3. Horizontal phase: warp r owns chunk row r.  It turns each vertical
 //     sum row into a prefix sum (window sums are differences of two
 //     prefixes and fit in int64), and each min / max row into one
@@ -313,30 +314,54 @@ __device__ __forceinline__ bool fabf_tile(const CUtensorMap* tmap, const ImageJo
         if (threadIdx.x == 0) *redo_n = 0u;
         if (c < Cb) {
             if (col_in) {
-                // common core of the 8 windows [r, r + 2w], r = r0..r0+7
-                uint8_t cmin = 255, cmax = 0;
-                {
-                    const int a = max(r0 + kChunk - 1, rowlo), b = min(r0 + 2 * w, rowhi);
+                // Window of chunk row rr: tile rows [r0 + rr, r0 + rr + 2w]
+                // = [r0 + rr, r0 + 7] u [r0 + 8, r0 + rr + 2w] (2w + 1 >= 8,
+                // i.e. w >= 4): suffix extrema of the chunk's own rows, then
+                // prefix extrema from r0 + 8 that grow by one row per rr --
+                // 2w + 8 row visits per chunk.  For w < 4 every window is
+                // visited directly (2w + 1 < 8 rows).
+                // (the suffix extrema wait in this thread's own entries of the
+                // shared min / max rows)
+                uint8_t qmn = 255, qmx = 0;
+                const bool split = 2 * w + 1 >= kChunk;
+                if (split) {
+                    uint8_t mn = 255, mx = 0;
+#pragma unroll
+                    for (int rr = kChunk - 1; rr >= 0; --rr) {
+                        const int t = r0 + rr;
+                        if (t >= rowlo && t <= rowhi) {
+                            const uint8_t v = tile[t * Cb + c];
+                            mn = v < mn ? v : mn;
+                            mx = v > mx ? v : mx;
+                        }
+                        vmin[rr * Cb + c] = mn;
+                        vmax[rr * Cb + c] = mx;
+                    }
+                    const int a = max(r0 + kChunk, rowlo), b = min(r0 + 2 * w, rowhi);
                     for (int t = a; t <= b; ++t) {
                         const uint8_t v = tile[t * Cb + c];
-                        cmin = v < cmin ? v : cmin;
-                        cmax = v > cmax ? v : cmax;
+                        qmn = v < qmn ? v : qmn;
+                        qmx = v > qmx ? v : qmx;
                     }
                 }
 #pragma unroll
                 for (int rr = 0; rr < kChunk; ++rr) {
                     const int r = r0 + rr;
-                    uint8_t mn = cmin, mx = cmax;
-                    {
-                        const int a = max(r, rowlo), b = min(min(r0 + kChunk - 2, r + 2 * w), rowhi);
-                        for (int t = a; t <= b; ++t) {
+                    uint8_t mn, mx;
+                    if (split) {
+                        const int t = r + 2 * w;            // the row entering the prefix part
+                        if (rr > 0 && t >= rowlo && t <= rowhi) {
                             const uint8_t v = tile[t * Cb + c];
-                            mn = v < mn ? v : mn;
-                            mx = v > mx ? v : mx;
+                            qmn = v < qmn ? v : qmn;
+                            qmx = v > qmx ? v : qmx;
                         }
-                    }
-                    {
-                        const int a = max(max(r0 + 2 * w + 1, r), rowlo), b = min(r + 2 * w, rowhi);
+                        const uint8_t sn = vmin[rr * Cb + c], sx = vmax[rr * Cb + c];
+                        mn = sn < qmn ? sn : qmn;
+                        mx = sx > qmx ? sx : qmx;
+                    } else {
+                        mn = 255;
+                        mx = 0;
+                        const int a = max(r, rowlo), b = min(r + 2 * w, rowhi);
                         for (int t = a; t <= b; ++t) {
                             const uint8_t v = tile[t * Cb + c];
                             mn = v < mn ? v : mn;

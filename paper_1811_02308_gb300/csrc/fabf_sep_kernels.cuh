@@ -9,7 +9,7 @@
 //     item forms V_k = sum_t g[t] f(row + t - r, column)^k for k = 1..K by a
 //     direct (2r+1)-tap FIR in 32/64-bit integers (exact: V_k < 65535 255^6
 //     < 2^64), and each column takes the vertical min / max of the chunk's 8
-//     windows from their common core (Eq. (8)).
+//     windows from suffix and prefix extrema (Eq. (8)), as the box kernel.
 //  2. Horizontal pass, warp rr on chunk row rr: min / max by one sparse-table
 //     level, then for each of the lane's two pixels m_k = sum_t g[t]
 //     V_k(column + t - r), exact in 64 bits for k <= 4 and in 128 bits (two
@@ -249,30 +249,53 @@ __device__ __forceinline__ void sep_tile(const CUtensorMap* tmap, const SepParam
             const int X = xs + c;
             if (c < Cb) {
                 if (X >= 0 && X < J.W) {
-                    uint8_t cmin = 255, cmax = 0;
-                    {
-                        const int a = max(r0 + kChunk - 1, rowlo), b = min(r0 + 2 * r, rowhi);
+                    // suffix extrema of the chunk's rows and prefix extrema
+                    // from r0 + 8 (2r + 1 >= 8), as in the box kernel
+                    uint8_t qmn = 255, qmx = 0;
+                    const bool split = 2 * r + 1 >= kChunk;
+                    if (split) {
+                        uint8_t mn = 255, mx = 0;
+#pragma unroll
+                        for (int rr = kChunk - 1; rr >= 0; --rr) {
+                            const int t = r0 + rr;
+                            if (t >= rowlo && t <= rowhi) {
+                                const uint8_t v = tile[t * Cb + c];
+                                mn = v < mn ? v : mn;
+                                mx = v > mx ? v : mx;
+                            }
+                            vmin[rr * Cb + c] = mn;      // suffix extrema, completed below
+                            vmax[rr * Cb + c] = mx;
+                        }
+                        const int a = max(r0 + kChunk, rowlo), b = min(r0 + 2 * r, rowhi);
                         for (int t = a; t <= b; ++t) {
                             const uint8_t v = tile[t * Cb + c];
-                            cmin = v < cmin ? v : cmin;
-                            cmax = v > cmax ? v : cmax;
+                            qmn = v < qmn ? v : qmn;
+                            qmx = v > qmx ? v : qmx;
                         }
                     }
 #pragma unroll
                     for (int rr = 0; rr < kChunk; ++rr) {
                         const int row = r0 + rr;
-                        uint8_t mn = cmin, mx = cmax;
-                        const int a1 = max(row, rowlo), b1 = min(min(r0 + kChunk - 2, row + 2 * r), rowhi);
-                        for (int t = a1; t <= b1; ++t) {
-                            const uint8_t v = tile[t * Cb + c];
-                            mn = v < mn ? v : mn;
-                            mx = v > mx ? v : mx;
-                        }
-                        const int a2 = max(max(r0 + 2 * r + 1, row), rowlo), b2 = min(row + 2 * r, rowhi);
-                        for (int t = a2; t <= b2; ++t) {
-                            const uint8_t v = tile[t * Cb + c];
-                            mn = v < mn ? v : mn;
-                            mx = v > mx ? v : mx;
+                        uint8_t mn, mx;
+                        if (split) {
+                            const int t = row + 2 * r;
+                            if (rr > 0 && t >= rowlo && t <= rowhi) {
+                                const uint8_t v = tile[t * Cb + c];
+                                qmn = v < qmn ? v : qmn;
+                                qmx = v > qmx ? v : qmx;
+                            }
+                            const uint8_t sn = vmin[rr * Cb + c], sx = vmax[rr * Cb + c];
+                            mn = sn < qmn ? sn : qmn;
+                            mx = sx > qmx ? sx : qmx;
+                        } else {
+                            mn = 255;
+                            mx = 0;
+                            const int a = max(row, rowlo), b = min(row + 2 * r, rowhi);
+                            for (int t = a; t <= b; ++t) {
+                                const uint8_t v = tile[t * Cb + c];
+                                mn = v < mn ? v : mn;
+                                mx = v > mx ? v : mx;
+                            }
                         }
                         vmin[rr * Cb + c] = mn;
                         vmax[rr * Cb + c] = mx;
