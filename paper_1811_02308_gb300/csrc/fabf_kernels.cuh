@@ -19,9 +19,10 @@
 //     rows below, 2w + 8 row visits per chunk (Eq. (8)).
 //  3. Horizontal phase: warp r owns chunk row r.  It turns each vertical
 //     sum row into a prefix sum (window sums are differences of two
-//     prefixes and fit in int64), and each min / max row into one
-//     sparse-table level of width 2^floor(log2(2w+1)), so a window's min /
-//     max is the min / max of two entries.  Each lane then finishes two
+//     prefixes and fit in int64), and each min / max row into lane blocks
+//     of 5 entries (in-lane suffix and prefix extrema plus a table over 2^k
+//     consecutive lanes), so a window's min / max takes four lookups; for
+//     w <= 2 a sparse-table level of width 2^floor(log2(2w+1)) instead.  Each lane then finishes two
 //     pixels (fabf_device.cuh): m_0 from the clipped window geometry, the
 //     exact shifted moments, the fit, the integrals and the ratio.
 //
@@ -47,6 +48,9 @@ constexpr unsigned kTmaWaitLimit = 1u << 22;   // bounded mbarrier wait (polls)
 // Per-chunk list of pixels the binary32 forms hand to the FP64 path: a count
 // and one 16-bit (row, column) entry per pixel of the chunk.
 constexpr size_t kRedoBytes = 16 + 2 * kChunk * kTileW;
+
+// Lane-block extrema table of one row: levels k = 0..4 x 32 lanes (bytes).
+constexpr int kLaneTable = 5 * 32;
 
 constexpr int kPrecFP64 = 0;          // FABF_FP64
 constexpr int kPrecFP64Fit = 1;       // FABF_FP64FIT_FP32REC
@@ -108,7 +112,7 @@ __host__ __device__ inline size_t fused_smem_bytes(int N, int w, int Cb, int TH)
     const int K = N < 1 ? 1 : N;               // k = 1 is kept even for N = 0
     const int n32 = K < 2 ? K : 2;
     const int n64 = K > 2 ? K - 2 : 0;
-    size_t v = (size_t)kChunk * Cb * (2 + 4 * n32) + (size_t)kChunk * Cb * 8 * n64;
+    size_t v = (size_t)kChunk * Cb * (4 + 4 * n32) + (size_t)2 * kChunk * kLaneTable + (size_t)kChunk * Cb * 8 * n64;
     return 128 + tile + ((v + 15) & ~(size_t)15) + kRedoBytes;
 }
 
@@ -228,6 +232,70 @@ __device__ __forceinline__ void warp_sparse_row(uint8_t* row, int Cb, int levels
     }
 }
 
+// Window extrema of a row by lane blocks (Eq. (8), horizontal part).  Lane l
+// owns entries 5l .. 5l+4 (Cb <= 160).  The row is overwritten with in-lane
+// suffix extrema, `pre` receives in-lane prefix extrema and `lt` the extrema
+// of 2^k consecutive lanes' blocks (k = 0..4).  A window [a, e] of at least
+// 6 entries spans two or more lanes: the rest of a's lane, whole lanes
+// strictly between (two overlapping table entries) and the start of e's lane.
+template <bool IsMin>
+__device__ __forceinline__ void warp_lane_blocks(uint8_t* row, uint8_t* pre, uint8_t* lt, int Cb, int lane)
+{
+    const uint8_t id = IsMin ? 255 : 0;
+    uint8_t v[5], sfx[5], pfx[5];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        const int c = 5 * lane + q;
+        v[q] = c < Cb ? row[c] : id;
+    }
+    uint8_t acc = id;
+#pragma unroll
+    for (int q = 4; q >= 0; --q) {
+        acc = IsMin ? (v[q] < acc ? v[q] : acc) : (v[q] > acc ? v[q] : acc);
+        sfx[q] = acc;
+    }
+    acc = id;
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        acc = IsMin ? (v[q] < acc ? v[q] : acc) : (v[q] > acc ? v[q] : acc);
+        pfx[q] = acc;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        const int c = 5 * lane + q;
+        if (c < Cb) {
+            row[c] = sfx[q];
+            pre[c] = pfx[q];
+        }
+    }
+    uint32_t t = pfx[4];
+    lt[lane] = (uint8_t)t;
+#pragma unroll
+    for (int k = 1; k < 5; ++k) {
+        const int h = 1 << (k - 1);
+        const uint32_t u = __shfl_down_sync(0xffffffffu, t, h);
+        if (lane + h < 32) t = IsMin ? (u < t ? u : t) : (u > t ? u : t);
+        lt[k * 32 + lane] = (uint8_t)t;
+    }
+    __syncwarp();
+}
+
+// Extremum of row entries [a, e] (e - a >= 5) from the lane-block arrays.
+template <bool IsMin>
+__device__ __forceinline__ int lane_block_query(const uint8_t* row, const uint8_t* pre, const uint8_t* lt, int a, int e)
+{
+    const int la = (a * 205) >> 10, le = (e * 205) >> 10;     // a / 5, e / 5 for a, e < 1000
+    int r = IsMin ? min((int)row[a], (int)pre[e]) : max((int)row[a], (int)pre[e]);
+    const int n = le - la - 1;                                  // whole lanes strictly inside
+    if (n > 0) {
+        const int k = 31 - __clz(n);
+        const int u = lt[k * 32 + la + 1], v = lt[k * 32 + le - (1 << k)];
+        r = IsMin ? min(r, min(u, v)) : max(r, max(u, v));
+    }
+    return r;
+}
+
 // ---------------------------------------------------------------------------
 // One output tile (tx, ty) of image J.  smem must hold fused_smem_bytes();
 // its first 8 bytes are the CTA's mbarrier (initialised by the caller when
@@ -256,11 +324,16 @@ __device__ __forceinline__ bool fabf_tile(const CUtensorMap* tmap, const ImageJo
     const size_t tile_bytes = ((size_t)R * Cb + 127) & ~(size_t)127;
     uint8_t* vmin = tile + tile_bytes;
     uint8_t* vmax = vmin + kChunk * Cb;
-    uint32_t* v32 = reinterpret_cast<uint32_t*>(vmax + kChunk * Cb);    // [n32][kChunk][Cb]
+    uint8_t* pmin = vmax + kChunk * Cb;                                 // in-lane prefix extrema
+    uint8_t* pmax = pmin + kChunk * Cb;
+    uint8_t* ltmin = pmax + kChunk * Cb;                                // [kChunk][kLaneTable]
+    uint8_t* ltmax = ltmin + kChunk * kLaneTable;
+    uint32_t* v32 = reinterpret_cast<uint32_t*>(ltmax + kChunk * kLaneTable);   // [n32][kChunk][Cb]
     const size_t v32_bytes = (size_t)n32 * kChunk * Cb * 4;
     uint64_t* v64 = reinterpret_cast<uint64_t*>(reinterpret_cast<uint8_t*>(v32) +
                                                 ((v32_bytes + 7) & ~(size_t)7));   // [n64][kChunk][Cb]
-    const size_t v_bytes = (size_t)kChunk * Cb * (2 + 4 * n32) + (size_t)kChunk * Cb * 8 * n64;
+    const size_t v_bytes = (size_t)kChunk * Cb * (4 + 4 * n32) + (size_t)2 * kChunk * kLaneTable +
+                           (size_t)kChunk * Cb * 8 * n64;
     unsigned* redo_n = reinterpret_cast<unsigned*>(vmin + ((v_bytes + 15) & ~(size_t)15));
     uint16_t* redo_list = reinterpret_cast<uint16_t*>(reinterpret_cast<uint8_t*>(redo_n) + 16);
 
@@ -307,6 +380,7 @@ __device__ __forceinline__ bool fabf_tile(const CUtensorMap* tmap, const ImageJo
     int levels = 0;
     while ((2 << levels) <= 2 * w + 1) ++levels;                   // floor(log2(2w+1))
     const int span = 1 << levels;
+    const bool lane_blocks = 2 * w + 1 >= 6;                       // else sparse-table levels
 
     for (int r0 = 0; r0 < TH; r0 += kChunk) {
         if (y0 + r0 >= J.H) break;                                 // uniform per CTA
@@ -418,8 +492,13 @@ __device__ __forceinline__ bool fabf_tile(const CUtensorMap* tmap, const ImageJo
             const int a = x + off, b = a + 2 * w;          // tile columns of the window
             const uint8_t* rmin = vmin + rr * Cb;
             const uint8_t* rmax = vmax + rr * Cb;
-            alpha = min(rmin[a], rmin[b - span + 1]);
-            beta = max(rmax[a], rmax[b - span + 1]);
+            if (lane_blocks) {
+                alpha = lane_block_query<true>(rmin, pmin + rr * Cb, ltmin + rr * kLaneTable, a, b);
+                beta = lane_block_query<false>(rmax, pmax + rr * Cb, ltmax + rr * kLaneTable, a, b);
+            } else {
+                alpha = min(rmin[a], rmin[b - span + 1]);
+                beta = max(rmax[a], rmax[b - span + 1]);
+            }
             const int ry0 = max(Y - w, 0), ry1 = min(Y + w, J.H - 1);
             const int rx0 = max(Xo - w, 0), rx1 = min(Xo + w, J.W - 1);
             m[0] = (int64_t)(ry1 - ry0 + 1) * (rx1 - rx0 + 1);
@@ -446,8 +525,13 @@ __device__ __forceinline__ bool fabf_tile(const CUtensorMap* tmap, const ImageJo
             for (int k = 0; k < n32; ++k) warp_prefix_row<uint32_t>(v32 + (k * kChunk + rr) * Cb, Cb, lane);
 #pragma unroll
             for (int k = 0; k < n64; ++k) warp_prefix_row<uint64_t>(v64 + (k * kChunk + rr) * Cb, Cb, lane);
-            warp_sparse_row<true>(vmin + rr * Cb, Cb, levels, lane);
-            warp_sparse_row<false>(vmax + rr * Cb, Cb, levels, lane);
+            if (lane_blocks) {
+                warp_lane_blocks<true>(vmin + rr * Cb, pmin + rr * Cb, ltmin + rr * kLaneTable, Cb, lane);
+                warp_lane_blocks<false>(vmax + rr * Cb, pmax + rr * Cb, ltmax + rr * kLaneTable, Cb, lane);
+            } else {
+                warp_sparse_row<true>(vmin + rr * Cb, Cb, levels, lane);
+                warp_sparse_row<false>(vmax + rr * Cb, Cb, levels, lane);
+            }
             if (Y < J.H) {
                 // one copy of the per-pixel code for both pixels of the lane
                 // (keeps the hot loop small in the instruction cache)

@@ -10,8 +10,8 @@
 //     direct (2r+1)-tap FIR in 32/64-bit integers (exact: V_k < 65535 255^6
 //     < 2^64), and each column takes the vertical min / max of the chunk's 8
 //     windows from suffix and prefix extrema (Eq. (8)), as the box kernel.
-//  2. Horizontal pass, warp rr on chunk row rr: min / max by one sparse-table
-//     level, then for each of the lane's two pixels m_k = sum_t g[t]
+//  2. Horizontal pass, warp rr on chunk row rr: min / max by lane blocks
+//     (sparse-table levels for r <= 2), as the box kernel, then for each of the lane's two pixels m_k = sum_t g[t]
 //     V_k(column + t - r), exact in 64 bits for k <= 4 and in 128 bits (two
 //     64-bit partial sums of the 32-bit halves of V_k) for k = 5, 6; m_0
 //     from the tap prefix sums and the clipped window.  Out-of-image pixels
@@ -72,7 +72,7 @@ __host__ __device__ inline size_t sep_smem_bytes(int N, int r, int Cb, int TH)
 {
     const int K = N < 1 ? 1 : N;
     size_t tile = ((size_t)(TH + 2 * r) * Cb + 127) & ~(size_t)127;
-    size_t mm = ((size_t)2 * kChunk * Cb + 15) & ~(size_t)15;
+    size_t mm = ((size_t)4 * kChunk * Cb + (size_t)2 * kChunk * kLaneTable + 15) & ~(size_t)15;
     return 128 + tile + mm + (size_t)K * kChunk * Cb * 8 + kRedoBytes;
 }
 
@@ -215,7 +215,12 @@ __device__ __forceinline__ void sep_tile(const CUtensorMap* tmap, const SepParam
     const size_t tile_bytes = ((size_t)R * Cb + 127) & ~(size_t)127;
     uint8_t* vmin = tile + tile_bytes;
     uint8_t* vmax = vmin + kChunk * Cb;
-    uint64_t* V = reinterpret_cast<uint64_t*>(vmin + (((size_t)2 * kChunk * Cb + 15) & ~(size_t)15));   // [K][kChunk][Cb]
+    uint8_t* pmin = vmax + kChunk * Cb;                                 // in-lane prefix extrema
+    uint8_t* pmax = pmin + kChunk * Cb;
+    uint8_t* ltmin = pmax + kChunk * Cb;                                // [kChunk][kLaneTable]
+    uint8_t* ltmax = ltmin + kChunk * kLaneTable;
+    uint64_t* V = reinterpret_cast<uint64_t*>(
+        vmin + (((size_t)4 * kChunk * Cb + (size_t)2 * kChunk * kLaneTable + 15) & ~(size_t)15));   // [K][kChunk][Cb]
     unsigned* redo_n = reinterpret_cast<unsigned*>(V + (size_t)K * kChunk * Cb);
     uint16_t* redo_list = reinterpret_cast<uint16_t*>(reinterpret_cast<uint8_t*>(redo_n) + 16);
     unsigned long long* redo_count = P.n_fallback ? P.n_fallback + 1 : nullptr;
@@ -238,6 +243,7 @@ __device__ __forceinline__ void sep_tile(const CUtensorMap* tmap, const SepParam
     int levels = 0;
     while ((2 << levels) <= 2 * r + 1) ++levels;
     const int span = 1 << levels;
+    const bool lane_blocks = 2 * r + 1 >= 6;
     const int plane = kChunk * Cb;
 
     for (int r0 = 0; r0 < TH; r0 += kChunk) {
@@ -351,8 +357,13 @@ __device__ __forceinline__ void sep_tile(const CUtensorMap* tmap, const SepParam
         auto stats = [&](int rr, int x, int& alpha, int& beta, u128 (&m)[K + 1], int& fi) {
             const int Y = y0 + r0 + rr, Xo = x0 + x;
             const int a = x + off;                      // tile column of the window's left edge
-            alpha = min(vmin[rr * Cb + a], vmin[rr * Cb + a + 2 * r - span + 1]);
-            beta = max(vmax[rr * Cb + a], vmax[rr * Cb + a + 2 * r - span + 1]);
+            if (lane_blocks) {
+                alpha = lane_block_query<true>(vmin + rr * Cb, pmin + rr * Cb, ltmin + rr * kLaneTable, a, a + 2 * r);
+                beta = lane_block_query<false>(vmax + rr * Cb, pmax + rr * Cb, ltmax + rr * kLaneTable, a, a + 2 * r);
+            } else {
+                alpha = min(vmin[rr * Cb + a], vmin[rr * Cb + a + 2 * r - span + 1]);
+                beta = max(vmax[rr * Cb + a], vmax[rr * Cb + a + 2 * r - span + 1]);
+            }
             fi = tile[(r0 + rr + r) * Cb + a + r];
             const int ty0 = max(r - Y, 0), ty1 = min(2 * r, J.H - 1 - Y + r);
             const int tx0 = max(r - Xo, 0), tx1 = min(2 * r, J.W - 1 - Xo + r);
@@ -397,8 +408,13 @@ __device__ __forceinline__ void sep_tile(const CUtensorMap* tmap, const SepParam
         {
             const int rr = warp;
             const int Y = y0 + r0 + rr;
-            warp_sparse_row<true>(vmin + rr * Cb, Cb, levels, lane);
-            warp_sparse_row<false>(vmax + rr * Cb, Cb, levels, lane);
+            if (lane_blocks) {
+                warp_lane_blocks<true>(vmin + rr * Cb, pmin + rr * Cb, ltmin + rr * kLaneTable, Cb, lane);
+                warp_lane_blocks<false>(vmax + rr * Cb, pmax + rr * Cb, ltmax + rr * kLaneTable, Cb, lane);
+            } else {
+                warp_sparse_row<true>(vmin + rr * Cb, Cb, levels, lane);
+                warp_sparse_row<false>(vmax + rr * Cb, Cb, levels, lane);
+            }
             if (Y < J.H) {
 #pragma unroll 1
                 for (int h = 0; h < kTileW / 32; ++h) {
