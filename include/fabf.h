@@ -63,7 +63,7 @@ typedef enum {
  *     integrals, recursion and ratio in binary32.
  *   FABF_CFP32: fit with compensated binary32 dot products, the rest in
  *     binary32.
- * In both binary32 forms a pixel whose estimated error exceeds 0.02 gray
+ * In both binary32 forms a pixel whose estimated error exceeds 0.25 gray
  * levels (the ratio of Eq. (29) cancels badly, T2 <= 0, or the binary32
  * integrals are in a regime where they lose digits) is recomputed on the
  * FP64 path; fabf_get_status_ex counts those pixels. */

@@ -111,3 +111,13 @@ def test_binding_rejects_mismatched_buffers():
     for a, b, c, p in bad_in:
         with pytest.raises(ValueError):
             fabf._check_inputs(a, b, c, H, W, p)
+
+
+def test_precision_enum_bounds_without_gpu(lib):
+    # fabf_create checks the precision before touching the device
+    h = C.c_void_p()
+    cfg = fabf._Config(0, 0, 3, 0, None)
+    assert lib.fabf_create(C.byref(cfg), C.byref(h)) == fabf.FABF_EINVAL
+    cfg = fabf._Config(0, 0, -1, 0, None)
+    assert lib.fabf_create(C.byref(cfg), C.byref(h)) == fabf.FABF_EINVAL
+    assert lib.fabf_set_precision(None, fabf.FABF_CFP32) == fabf.FABF_EINVAL
