@@ -76,6 +76,14 @@ def load_library(path: str):
     lib.oracle_bruteforce_sep.argtypes = [u8p, f32p, f32p, I, I, L, u32p, I, f64p]
     lib.oracle_bruteforce_sep_pixels.argtypes = [u8p, f32p, f32p, I, I, L, u32p, I, i32p, i32p,
                                                  L, f64p]
+    lib.oracle_sharpen_theta.argtypes = [u8p, I, I, L, I, f32p]
+    lib.oracle_sharpen_log.argtypes = [u8p, I, I, L, u32p, I, i64p]
+    lib.oracle_sharpen_sigma.argtypes = [u8p, I, I, L, u32p, I, C.c_int64, C.c_double, C.c_double, f32p]
+    lib.oracle_texture_sigma.argtypes = [u8p, I, I, L, I, C.c_double, C.c_double, C.c_double, C.c_double,
+                                         f32p]
+    for fn in (lib.oracle_sharpen_theta, lib.oracle_sharpen_log, lib.oracle_sharpen_sigma,
+               lib.oracle_texture_sigma):
+        fn.restype = C.c_int
     for fn in (lib.oracle_hilbert_inverse, lib.oracle_integrals, lib.oracle_bounds,
                lib.oracle_moments, lib.oracle_shifted_moments, lib.oracle_fabf,
                lib.oracle_fabf_pixels, lib.oracle_fabf_trace, lib.oracle_bruteforce,
@@ -382,3 +390,76 @@ def bruteforce_sep_pixels(f, theta, sigma, taps, ys, xs):
                                                 _ptr(xs, C.c_int32), len(ys),
                                                 _ptr(out, C.c_double)), "bruteforce_sep_pixels")
     return out
+
+
+# ---------------------------------------------------------------------------
+# Applications (Sec. IV): centre and width maps, sharpening, texture filtering
+# ---------------------------------------------------------------------------
+def sharpen_theta(f, w):
+    """Sec. IV-A: theta = f + (f - mean of f over the clipped window), float32."""
+    f = np.ascontiguousarray(f, dtype=np.uint8)
+    H, W = f.shape
+    out = np.zeros((H, W), np.float32)
+    _check(_load().oracle_sharpen_theta(_ptr(f, C.c_uint8), H, W, W, w, _ptr(out, C.c_float)),
+           "sharpen_theta")
+    return out
+
+
+def sharpen_log(f, taps):
+    """Integer Laplacian of the integer-Gaussian-smoothed image (int64)."""
+    f = np.ascontiguousarray(f, dtype=np.uint8)
+    H, W = f.shape
+    t, r = _taps(taps)
+    out = np.zeros((H, W), np.int64)
+    _check(_load().oracle_sharpen_log(_ptr(f, C.c_uint8), H, W, W, _ptr(t, C.c_uint32), r,
+                                      _ptr(out, C.c_int64)), "sharpen_log")
+    return out
+
+
+def sharpen_sigma(f, taps, Lq, s_lo, s_hi):
+    """Sec. IV-A: sigma = s_hi - (s_hi - s_lo) min(|LoG|, Lq) / Lq, float32."""
+    f = np.ascontiguousarray(f, dtype=np.uint8)
+    H, W = f.shape
+    t, r = _taps(taps)
+    out = np.zeros((H, W), np.float32)
+    _check(_load().oracle_sharpen_sigma(_ptr(f, C.c_uint8), H, W, W, _ptr(t, C.c_uint32), r, int(Lq),
+                                        float(s_lo), float(s_hi), _ptr(out, C.c_float)), "sharpen_sigma")
+    return out
+
+
+def texture_sigma(f, k, eps, msat, s_lo, s_hi):
+    """Sec. IV-C: sigma from mRTV over the clipped window [-k, k]^2, float32."""
+    f = np.ascontiguousarray(f, dtype=np.uint8)
+    H, W = f.shape
+    out = np.zeros((H, W), np.float32)
+    _check(_load().oracle_texture_sigma(_ptr(f, C.c_uint8), H, W, W, int(k), float(eps), float(msat),
+                                        float(s_lo), float(s_hi), _ptr(out, C.c_float)), "texture_sigma")
+    return out
+
+
+def _next_input(g):
+    """Pass p+1 input: the output rounded half to even, clamped to [0, 255] (R9)."""
+    return np.clip(np.rint(g), 0, 255).astype(np.uint8)
+
+
+def sharpen(f, w, N, taps, Lq, s_lo, s_hi):
+    """One sharpening pass (Sec. IV-A): Algorithm 1 with the maps above."""
+    th = sharpen_theta(f, w)
+    sg = sharpen_sigma(f, taps, Lq, s_lo, s_hi)
+    g, _ = fabf(f, th, sg, w, N)
+    return g
+
+
+def texture_filter(f, w, N, k, eps, msat, t_lo, t_hi, taps, Lq, s_lo, s_hi, sigma_decay=0.8):
+    """Texture filtering (Sec. IV-C): two smoothing passes with theta = f and
+    the mRTV width map (scaled by sigma_decay on the second pass), then one
+    sharpening pass.  Returns (g_final, [intermediate outputs])."""
+    f = np.ascontiguousarray(f, dtype=np.uint8)
+    s1 = texture_sigma(f, k, eps, msat, t_lo, t_hi)
+    g1, _ = fabf(f, f.astype(np.float32), s1, w, N)
+    f2 = _next_input(g1)
+    s2 = (s1 * np.float32(sigma_decay)).astype(np.float32)
+    g2, _ = fabf(f2, f2.astype(np.float32), s2, w, N)
+    f3 = _next_input(g2)
+    g3 = sharpen(f3, w, N, taps, Lq, s_lo, s_hi)
+    return g3, [g1, g2]

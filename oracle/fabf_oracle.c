@@ -730,3 +730,109 @@ int oracle_bruteforce_sep(const uint8_t* f, const float* theta, const float* sig
     free(xs);
     return rc;
 }
+
+/* ------------------------------------------------------------------ */
+/* Applications (Sec. IV): the centre and width maps                   */
+/* ------------------------------------------------------------------ */
+/*
+ * Readings (the paper leaves the parameters of these rules open):
+ *   - sharpening centre (Sec. IV-A): theta = f + zeta with zeta = f - fbar,
+ *     fbar the plain mean of f over the filter window [-w, w]^2 clipped to
+ *     the image, i.e. theta = (2 f m_0 - m_1) / m_0, one binary64 division of
+ *     exact integers, rounded to binary32;
+ *   - sharpening width (Sec. IV-A): the Laplacian of a Gaussian of f, as the
+ *     integer Gaussian S = g x g * f (integer taps, coordinates clamped to the
+ *     image) followed by the 5-point Laplacian of S (clamped), so L is an
+ *     exact integer; with q = min(|L|, Lq) the width is sigma = s_hi - (s_hi -
+ *     s_lo) (q / Lq) in binary64 (division, product, difference), rounded to
+ *     binary32: low |LoG| gives a wide range kernel, high |LoG| a narrow one;
+ *   - texture width (Sec. IV-C): mRTV = Delta gmax / (gsum + eps) over the
+ *     window [-k, k]^2 clipped to the image, with Delta the range of f there
+ *     and g = |f(x+1, y) - f(x, y)| + |f(x, y+1) - f(x, y)| (forward
+ *     differences, clamped; the L1 norm keeps g an integer), then sigma =
+ *     s_hi - (s_hi - s_lo) min(mRTV / msat, 1) in binary64, rounded to
+ *     binary32.
+ */
+static inline int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+int oracle_sharpen_theta(const uint8_t* f, int H, int W, long pitch, int w, float* theta)
+{
+    if (check_args(H, W, pitch, w, 1)) return 1;
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            int64_t m[2];
+            pixel_moments(f, H, W, pitch, w, 1, y, x, m);
+            const int64_t num = 2 * (int64_t)f[(long)y * pitch + x] * m[0] - m[1];
+            theta[(long)y * W + x] = (float)((double)num / (double)m[0]);
+        }
+    return 0;
+}
+
+/* 5-point Laplacian of the integer Gaussian-smoothed image at (y, x). */
+static int64_t log_at(const uint8_t* f, int H, int W, long pitch, const uint32_t* taps, int r, int y, int x)
+{
+    int64_t S[5];
+    const int dy[5] = {0, -1, 1, 0, 0}, dx[5] = {0, 0, 0, -1, 1};
+    for (int q = 0; q < 5; ++q) {
+        const int yc = clampi(y + dy[q], 0, H - 1), xc = clampi(x + dx[q], 0, W - 1);
+        int64_t s = 0;
+        for (int ty = -r; ty <= r; ++ty)
+            for (int tx = -r; tx <= r; ++tx) {
+                const int yy = clampi(yc + ty, 0, H - 1), xx = clampi(xc + tx, 0, W - 1);
+                s += (int64_t)taps[ty + r] * taps[tx + r] * f[(long)yy * pitch + xx];
+            }
+        S[q] = s;
+    }
+    return S[1] + S[2] + S[3] + S[4] - 4 * S[0];
+}
+
+int oracle_sharpen_log(const uint8_t* f, int H, int W, long pitch, const uint32_t* taps, int r, int64_t* L)
+{
+    if (check_args(H, W, pitch, r, 0) || check_taps(taps, r)) return 1;
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) L[(long)y * W + x] = log_at(f, H, W, pitch, taps, r, y, x);
+    return 0;
+}
+
+int oracle_sharpen_sigma(const uint8_t* f, int H, int W, long pitch, const uint32_t* taps, int r, int64_t Lq,
+                         double s_lo, double s_hi, float* sigma)
+{
+    if (check_args(H, W, pitch, r, 0) || check_taps(taps, r) || Lq < 1) return 1;
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            int64_t L = log_at(f, H, W, pitch, taps, r, y, x);
+            if (L < 0) L = -L;
+            const int64_t q = L < Lq ? L : Lq;
+            const double u = (double)q / (double)Lq;
+            sigma[(long)y * W + x] = (float)(s_hi - (s_hi - s_lo) * u);
+        }
+    return 0;
+}
+
+int oracle_texture_sigma(const uint8_t* f, int H, int W, long pitch, int k, double eps, double msat, double s_lo,
+                         double s_hi, float* sigma)
+{
+    if (H < 1 || W < 1 || pitch < W || k < 1 || k > ORACLE_WMAX || !(eps > 0) || !(msat > 0)) return 1;
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            int y0, y1, x0, x1, fmin = 255, fmax = 0;
+            int64_t gmax = 0, gsum = 0;
+            window_bounds(H, W, y, x, k, &y0, &y1, &x0, &x1);
+            for (int yy = y0; yy <= y1; ++yy)
+                for (int xx = x0; xx <= x1; ++xx) {
+                    const int v = f[(long)yy * pitch + xx];
+                    const int vx = f[(long)yy * pitch + clampi(xx + 1, 0, W - 1)];
+                    const int vy = f[(long)clampi(yy + 1, 0, H - 1) * pitch + xx];
+                    const int64_t g = (vx > v ? vx - v : v - vx) + (vy > v ? vy - v : v - vy);
+                    if (v < fmin) fmin = v;
+                    if (v > fmax) fmax = v;
+                    if (g > gmax) gmax = g;
+                    gsum += g;
+                }
+            const double mrtv = (double)((int64_t)(fmax - fmin) * gmax) / ((double)gsum + eps);
+            double u = mrtv / msat;
+            if (u > 1.0) u = 1.0;
+            sigma[(long)y * W + x] = (float)(s_hi - (s_hi - s_lo) * u);
+        }
+    return 0;
+}

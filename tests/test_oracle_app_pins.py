@@ -1,0 +1,138 @@
+"""Pins of the oracle's application maps (Sec. IV; no GPU): the sharpening
+centre and width (Sec. IV-A) and the texture width from mRTV (Sec. IV-C),
+each against an independent numpy implementation of the same reading, bit
+for bit, plus the behaviour the paper describes (flat regions get wide range
+kernels, strong edges narrow ones; constant images pass unchanged)."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1811_02308_gb300 import synth
+
+
+def image(H, W, seed, n_blobs=4):
+    f, _, _ = synth.make_inputs(H, W, seed, n_blobs=n_blobs)
+    return f
+
+
+def lq_for(taps, lap_sat):
+    return int(math.floor(lap_sat * float(int(taps.sum())) ** 2 + 0.5))
+
+
+@pytest.mark.parametrize("H,W,w,seed", [(9, 11, 2, 1), (1, 7, 3, 2), (13, 5, 6, 3), (6, 6, 40, 4)])
+def test_sharpen_theta_is_twice_f_minus_window_mean(oracle_mod, H, W, w, seed):
+    f = image(H, W, seed)
+    th = oracle_mod.sharpen_theta(f, w)
+    for y in range(H):
+        for x in range(W):
+            win = f[max(0, y - w):y + w + 1, max(0, x - w):x + w + 1].astype(np.int64)
+            m0, m1 = win.size, int(win.sum())
+            ref = np.float32((2 * int(f[y, x]) * m0 - m1) / m0)   # int / int: correctly rounded
+            assert th[y, x] == ref, (y, x)
+
+
+def np_log(f, taps):
+    """Integer Gaussian (clamped coordinates) then 5-point Laplacian (clamped)."""
+    r = len(taps) // 2
+    g = taps.astype(np.int64)
+    H, W = f.shape
+    p = np.pad(f.astype(np.int64), r, mode="edge")
+    S = np.zeros((H, W), np.int64)
+    for ty in range(2 * r + 1):
+        for tx in range(2 * r + 1):
+            S += g[ty] * g[tx] * p[ty:ty + H, tx:tx + W]
+    Sp = np.pad(S, 1, mode="edge")
+    return Sp[:-2, 1:-1] + Sp[2:, 1:-1] + Sp[1:-1, :-2] + Sp[1:-1, 2:] - 4 * S
+
+
+@pytest.mark.parametrize("rho", [0.7, 1.0, 2.0])
+def test_sharpen_log_and_sigma(oracle_mod, rho):
+    f = image(17, 19, 5)
+    taps = synth.gaussian_taps(rho)
+    L = oracle_mod.sharpen_log(f, taps)
+    assert np.array_equal(L, np_log(f, taps))
+    Lq = lq_for(taps, 12.0)
+    sg = oracle_mod.sharpen_sigma(f, taps, Lq, 10.0, 40.0)
+    q = np.minimum(np.abs(L), Lq)
+    ref = np.array([[np.float32(40.0 - (40.0 - 10.0) * (int(v) / Lq)) for v in row] for row in q])
+    assert np.array_equal(sg, ref)
+    assert sg.min() >= 10.0 and sg.max() <= 40.0
+
+
+def np_texture_sigma(f, k, eps, msat, lo, hi):
+    H, W = f.shape
+    fi = f.astype(np.int64)
+    gx = np.abs(np.concatenate([fi[:, 1:], fi[:, -1:]], axis=1) - fi)
+    gy = np.abs(np.concatenate([fi[1:, :], fi[-1:, :]], axis=0) - fi)
+    g = gx + gy
+    out = np.zeros((H, W), np.float32)
+    for y in range(H):
+        for x in range(W):
+            sl = (slice(max(0, y - k), y + k + 1), slice(max(0, x - k), x + k + 1))
+            delta = int(fi[sl].max() - fi[sl].min())
+            mrtv = (delta * int(g[sl].max())) / (float(int(g[sl].sum())) + eps)
+            u = min(mrtv / msat, 1.0)
+            out[y, x] = np.float32(hi - (hi - lo) * u)
+    return out
+
+
+@pytest.mark.parametrize("k", [1, 2, 5])
+def test_texture_sigma_from_mrtv(oracle_mod, k):
+    f = image(15, 18, 7)
+    got = oracle_mod.texture_sigma(f, k, 1.0, 8.0, 5.0, 60.0)
+    assert np.array_equal(got, np_texture_sigma(f, k, 1.0, 8.0, 5.0, 60.0))
+
+
+def test_maps_on_constant_and_step_images(oracle_mod):
+    taps = synth.gaussian_taps(1.0)
+    Lq = lq_for(taps, 10.0)
+    c = np.full((12, 14), 90, np.uint8)
+    assert np.array_equal(oracle_mod.sharpen_theta(c, 3), c.astype(np.float32))
+    assert np.all(oracle_mod.sharpen_sigma(c, taps, Lq, 10.0, 40.0) == 40.0)      # flat: widest kernel
+    assert np.all(oracle_mod.texture_sigma(c, 2, 1.0, 8.0, 5.0, 60.0) == 60.0)
+    s = np.full((12, 14), 40, np.uint8)
+    s[:, 7:] = 200                                                                 # a strong vertical edge
+    sg = oracle_mod.sharpen_sigma(s, taps, Lq, 10.0, 40.0)
+    assert sg[6, 6] == 10.0 and sg[6, 7] == 10.0 and sg[6, 0] == 40.0
+    ts = oracle_mod.texture_sigma(s, 2, 1.0, 8.0, 5.0, 60.0)
+    assert ts[6, 6] == 5.0 and ts[6, 0] == 60.0
+    th = oracle_mod.sharpen_theta(s, 2)
+    assert th[6, 6] < 40.0 and th[6, 7] > 200.0                                    # pushed apart
+
+
+def test_texture_pipeline_keeps_constant_image(oracle_mod):
+    c = np.full((10, 12), 137, np.uint8)
+    taps = synth.gaussian_taps(1.0)
+    g, mids = oracle_mod.texture_filter(c, 3, 5, 2, 1.0, 8.0, 5.0, 60.0, taps, lq_for(taps, 10.0), 10.0, 40.0)
+    assert np.array_equal(g, c.astype(np.float64))
+    assert all(np.array_equal(m, c.astype(np.float64)) for m in mids)
+
+
+def test_texture_pipeline_is_the_composition(oracle_mod):
+    f = image(16, 20, 9, n_blobs=6)
+    taps = synth.gaussian_taps(1.0)
+    Lq = lq_for(taps, 10.0)
+    g, (g1, g2) = oracle_mod.texture_filter(f, 3, 4, 2, 1.0, 8.0, 5.0, 60.0, taps, Lq, 10.0, 40.0)
+    s1 = oracle_mod.texture_sigma(f, 2, 1.0, 8.0, 5.0, 60.0)
+    r1, _ = oracle_mod.fabf(f, f.astype(np.float32), s1, 3, 4)
+    assert np.array_equal(r1, g1)
+    f2 = np.clip(np.rint(r1), 0, 255).astype(np.uint8)
+    r2, _ = oracle_mod.fabf(f2, f2.astype(np.float32), (s1 * np.float32(0.8)).astype(np.float32), 3, 4)
+    assert np.array_equal(r2, g2)
+    f3 = np.clip(np.rint(r2), 0, 255).astype(np.uint8)
+    r3, _ = oracle_mod.fabf(f3, oracle_mod.sharpen_theta(f3, 3), oracle_mod.sharpen_sigma(f3, taps, Lq, 10.0, 40.0),
+                            3, 4)
+    assert np.array_equal(r3, g)
+
+
+def test_texture_smoothing_removes_fine_texture(oracle_mod):
+    # a flat region covered by fine texture (noise of std 10): mRTV is low
+    # there, so the width map is wide and the two smoothing passes remove most
+    # of the texture
+    rng = np.random.default_rng(3)
+    f = np.clip(np.rint(128 + rng.normal(0, 10, (24, 24))), 0, 255).astype(np.uint8)
+    taps = synth.gaussian_taps(1.0)
+    _, (g1, g2) = oracle_mod.texture_filter(f, 3, 5, 2, 1.0, 8.0, 5.0, 60.0, taps, lq_for(taps, 10.0), 10.0, 40.0)
+    inner = (slice(4, 20), slice(4, 20))
+    assert g2[inner].std() < 0.3 * f[inner].std()

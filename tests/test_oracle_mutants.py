@@ -66,6 +66,11 @@ MUTANTS = {
         "mu[k] = (double)(uint64_t)M[k] / (double)dk;"),
     "separable brute force unweighted denominator": ("den += om * phi;", "den += phi;"),
     "separable tap sum limit": ("s > ORACLE_TAP_SUM_MAX", "s > 2 * ORACLE_TAP_SUM_MAX"),
+    "sharpening centre sign": ("* m[0] - m[1];", "* m[0] + m[1];"),
+    "LoG centre weight": ("S[1] + S[2] + S[3] + S[4] - 4 * S[0]", "S[1] + S[2] + S[3] + S[4] - 5 * S[0]"),
+    "texture gradient direction": ("clampi(xx + 1, 0, W - 1)", "clampi(xx - 1, 0, W - 1)"),
+    "texture width map reversed": ("if (u > 1.0) u = 1.0;\n            sigma[(long)y * W + x] = (float)(s_hi - (s_hi - s_lo) * u);",
+                                   "if (u > 1.0) u = 1.0;\n            sigma[(long)y * W + x] = (float)(s_lo + (s_hi - s_lo) * u);"),
 }
 
 # ---------------------------------------------------------------------------
@@ -241,10 +246,34 @@ def battery():
         else:
             raise AssertionError("taps summing to 100000 were accepted")
 
+    def applications():
+        # the Sec. IV maps against direct numpy evaluations of the same readings
+        f, _, _ = R["tiny"]
+        fi = f.astype(np.int64)
+        H, W = f.shape
+        th = oracle.sharpen_theta(f, 2)
+        for y, x in ((0, 0), (5, 6), (10, 12)):
+            win = fi[max(0, y - 2):y + 3, max(0, x - 2):x + 3]
+            assert th[y, x] == np.float32((2 * int(fi[y, x]) * win.size - int(win.sum())) / win.size)
+        taps = np.array([1, 4, 1], np.uint32)
+        p = np.pad(fi, 1, mode="edge")
+        S = sum(int(taps[a]) * int(taps[b]) * p[a:a + H, b:b + W] for a in range(3) for b in range(3))
+        Sp = np.pad(S, 1, mode="edge")
+        L = Sp[:-2, 1:-1] + Sp[2:, 1:-1] + Sp[1:-1, :-2] + Sp[1:-1, 2:] - 4 * S
+        assert np.array_equal(oracle.sharpen_log(f, taps), L)
+        gx = np.abs(np.concatenate([fi[:, 1:], fi[:, -1:]], axis=1) - fi)
+        gy = np.abs(np.concatenate([fi[1:, :], fi[-1:, :]], axis=0) - fi)
+        g = gx + gy
+        ts = oracle.texture_sigma(f, 1, 1.0, 8.0, 5.0, 60.0)
+        for y, x in ((0, 0), (5, 6), (10, 12), (3, 9)):
+            sl = (slice(max(0, y - 1), y + 2), slice(max(0, x - 1), x + 2))
+            mr = int(fi[sl].max() - fi[sl].min()) * int(g[sl].max()) / (float(int(g[sl].sum())) + 1.0)
+            assert ts[y, x] == np.float32(60.0 - 55.0 * min(mr / 8.0, 1.0))
+
     for name, fn in [("hilbert", hilbert), ("window", window_stats), ("integrals", integrals),
                      ("fit", fit_moments), ("constant", constant_image), ("box mean", box_mean_limit),
                      ("truncated normal", truncated_normal), ("bruteforce", bruteforce),
-                     ("fallback", fallback_rule), ("separable", separable)]:
+                     ("fallback", fallback_rule), ("separable", separable), ("applications", applications)]:
         check(name, fn)
     return fails
 
