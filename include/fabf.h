@@ -235,6 +235,62 @@ int fabf_filter_sep(fabf_ctx* ctx, const uint8_t* img, const float* theta, const
  * pointers, capacity < 2r+1), FABF_EUNSUPPORTED (3 rho > 40). */
 int fabf_gaussian_taps(double rho, uint32_t* taps, int capacity, int* r);
 
+/* ---- applications (Sec. IV) ---------------------------------------------- */
+
+/* Sharpening and noise removal (Sec. IV-A).  The paper sets theta = f +
+ * zeta with zeta = f - fbar (fbar the mean of f over the window) and sigma
+ * by an affine map of |LoG f| that sends low values to wide kernels; its
+ * parameters are open, and are read here as:
+ *   theta = (2 f m_0 - m_1) / m_0 over the clipped window [-w, w]^2;
+ *   L = 5-point Laplacian of S = g x g * f with the integer Gaussian taps
+ *       g = fabf_gaussian_taps(rho_log) (coordinates clamped to the image);
+ *   sigma = sigma_hi - (sigma_hi - sigma_lo) min(|L|, Lq) / Lq with
+ *       Lq = floor(lap_sat (sum g)^2 + 1/2), i.e. lap_sat in gray levels. */
+typedef struct {
+    int w;               /* box radius of the filter and of the mean, 1..40 */
+    int N;               /* polynomial degree, 0..6 */
+    double rho_log;      /* width of the LoG's Gaussian (0 < rho_log <= 40/3) */
+    double lap_sat;      /* |LoG| (gray levels) from which sigma = sigma_lo */
+    double sigma_lo, sigma_hi;   /* 0 < sigma_lo <= sigma_hi */
+} fabf_sharpen_cfg;
+
+/* Texture filtering (Sec. IV-C): theta = f and sigma from mRTV = Delta
+ * max|grad f| / (sum |grad f| + eps) over [-k, k]^2 (clipped; Delta the
+ * range of f there; |grad f| read as |f(x+1,y) - f(x,y)| + |f(x,y+1) -
+ * f(x,y)| with clamped coordinates), sigma = sigma_hi - (sigma_hi -
+ * sigma_lo) min(mRTV / mrtv_sat, 1); two smoothing passes, the second with
+ * sigma scaled by sigma_decay and the rounded output of the first as input,
+ * then one sharpening pass (cfg.sharpen) on the rounded output. */
+typedef struct {
+    int w, N;            /* the two smoothing passes */
+    int k;               /* mRTV window radius, 1..40 */
+    double eps, mrtv_sat, sigma_lo, sigma_hi, sigma_decay;
+    fabf_sharpen_cfg sharpen;
+} fabf_texture_cfg;
+
+/* The sharpening maps of img into theta and sigma (float32 H x W, row
+ * stride W).  Device pointers only; stream-ordered; maps are identical to
+ * the reference definitions above to the last bit.  Errors: FABF_EINVAL
+ * (NULL or host pointers, bad sizes or parameters), FABF_EUNSUPPORTED (w >
+ * 40, N > 6, 3 rho_log > 40), FABF_ENOMEM, FABF_ECUDA. */
+int fabf_sharpen_maps(fabf_ctx* ctx, const uint8_t* img, int H, int W, size_t pitch,
+                      const fabf_sharpen_cfg* cfg, float* theta, float* sigma, void* cuda_stream);
+
+/* The texture width map of img (float32 H x W).  As fabf_sharpen_maps. */
+int fabf_texture_sigma(fabf_ctx* ctx, const uint8_t* img, int H, int W, size_t pitch,
+                       const fabf_texture_cfg* cfg, float* sigma, void* cuda_stream);
+
+/* One sharpening pass: the maps, then Algorithm 1 in the context's
+ * precision into out.  Device pointers; stream-ordered (intermediates are
+ * stream-ordered allocations); data errors through fabf_get_status. */
+int fabf_sharpen(fabf_ctx* ctx, const uint8_t* img, int H, int W, size_t pitch,
+                 const fabf_sharpen_cfg* cfg, void* out, int out_is_f64, void* cuda_stream);
+
+/* The texture-filtering pipeline (three passes of Algorithm 1).  As
+ * fabf_sharpen. */
+int fabf_texture_filter(fabf_ctx* ctx, const uint8_t* img, int H, int W, size_t pitch,
+                        const fabf_texture_cfg* cfg, void* out, int out_is_f64, void* cuda_stream);
+
 /* ---- host-side helpers (no GPU needed) ---------------------------------- */
 
 /* The exact inverse of the (N+1) x (N+1) Hilbert matrix of Eq. (18), by the

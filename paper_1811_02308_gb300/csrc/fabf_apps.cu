@@ -1,0 +1,371 @@
+// Applications of Sec. IV on the device: the sharpening centre and width maps
+// (Sec. IV-A), the texture width map from mRTV (Sec. IV-C), and the two
+// pipelines built on Algorithm 1 -- one sharpening pass, and texture
+// filtering (two smoothing passes, the second with the width scaled by
+// sigma_decay, then one sharpening pass).
+//
+// The maps follow the readings the CPU oracle states (integer-exact up to one
+// fixed sequence of binary64 operations, rounded to binary32), written with
+// explicitly rounded intrinsics so that no multiply-add is contracted: the
+// maps are bit-identical to the oracle's.
+//   theta_sharpen = (2 f m_0 - m_1) / m_0 over the clipped window [-w, w]^2;
+//   L = 5-point Laplacian of the integer Gaussian S = g x g * f (coordinates
+//       clamped), sigma_sharpen = s_hi - (s_hi - s_lo) (min(|L|, Lq) / Lq);
+//   g = |f(x+1, y) - f(x, y)| + |f(x, y+1) - f(x, y)| (clamped), mRTV =
+//       Delta gmax / (gsum + eps) over [-k, k]^2 (clipped), sigma_texture =
+//       s_hi - (s_hi - s_lo) min(mRTV / msat, 1).
+// These are cheap next to Algorithm 1 and are written as plain one-thread-
+// per-pixel kernels over global memory (separable passes where a window is
+// involved).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <initializer_list>
+
+#include "../../include/fabf.h"
+#include "fabf_internal.h"
+#include "fabf_sep_kernels.cuh"
+
+namespace fabf {
+namespace {
+
+constexpr int kAppThreads = 256;
+
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+// rs = sum of f over the clipped row segment [x - w, x + w]
+__global__ void box_rows_kernel(const uint8_t* f, long long pitch, int H, int W, int w, int32_t* rs)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)H * W) return;
+    const int y = (int)(i / W), x = (int)(i - (long long)y * W);
+    const uint8_t* row = f + (long long)y * pitch;
+    const int x0 = max(x - w, 0), x1 = min(x + w, W - 1);
+    int32_t s = 0;
+    for (int xx = x0; xx <= x1; ++xx) s += row[xx];
+    rs[i] = s;
+}
+
+__global__ void sharpen_theta_kernel(const uint8_t* f, long long pitch, const int32_t* rs, int H, int W, int w,
+                                     float* theta)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)H * W) return;
+    const int y = (int)(i / W), x = (int)(i - (long long)y * W);
+    const int y0 = max(y - w, 0), y1 = min(y + w, H - 1);
+    const int x0 = max(x - w, 0), x1 = min(x + w, W - 1);
+    int64_t m1 = 0;
+    for (int yy = y0; yy <= y1; ++yy) m1 += rs[(long long)yy * W + x];
+    const int64_t m0 = (int64_t)(y1 - y0 + 1) * (x1 - x0 + 1);
+    const int64_t num = 2 * (int64_t)f[(long long)y * pitch + x] * m0 - m1;
+    theta[i] = __double2float_rn(__ddiv_rn((double)num, (double)m0));
+}
+
+// gr = sum_t g[t] f(y, clamp(x + t - r))
+__global__ void gauss_rows_kernel(const uint8_t* f, long long pitch, int H, int W, const __grid_constant__ SepTaps T,
+                                  uint32_t* gr)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)H * W) return;
+    const int y = (int)(i / W), x = (int)(i - (long long)y * W);
+    const uint8_t* row = f + (long long)y * pitch;
+    uint32_t s = 0;
+    for (int t = 0; t <= 2 * T.r; ++t) s += T.g[t] * (uint32_t)row[clampi(x + t - T.r, 0, W - 1)];
+    gr[i] = s;
+}
+
+// S = sum_t g[t] gr(clamp(y + t - r), x)
+__global__ void gauss_cols_kernel(const uint32_t* gr, int H, int W, const __grid_constant__ SepTaps T, int64_t* S)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)H * W) return;
+    const int y = (int)(i / W), x = (int)(i - (long long)y * W);
+    int64_t s = 0;
+    for (int t = 0; t <= 2 * T.r; ++t) s += (int64_t)T.g[t] * gr[(long long)clampi(y + t - T.r, 0, H - 1) * W + x];
+    S[i] = s;
+}
+
+__global__ void sharpen_sigma_kernel(const int64_t* S, int H, int W, long long Lq, double s_lo, double s_hi,
+                                     float* sigma)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)H * W) return;
+    const int y = (int)(i / W), x = (int)(i - (long long)y * W);
+    const int64_t L = S[(long long)clampi(y - 1, 0, H - 1) * W + x] + S[(long long)clampi(y + 1, 0, H - 1) * W + x] +
+                      S[(long long)y * W + clampi(x - 1, 0, W - 1)] + S[(long long)y * W + clampi(x + 1, 0, W - 1)] -
+                      4 * S[i];
+    const int64_t a = L < 0 ? -L : L;
+    const int64_t q = a < Lq ? a : Lq;
+    const double u = __ddiv_rn((double)q, (double)Lq);
+    sigma[i] = __double2float_rn(__dsub_rn(s_hi, __dmul_rn(__dsub_rn(s_hi, s_lo), u)));
+}
+
+__global__ void texture_sigma_kernel(const uint8_t* f, long long pitch, int H, int W, int k, double eps, double msat,
+                                     double s_lo, double s_hi, float* sigma)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)H * W) return;
+    const int y = (int)(i / W), x = (int)(i - (long long)y * W);
+    const int y0 = max(y - k, 0), y1 = min(y + k, H - 1);
+    const int x0 = max(x - k, 0), x1 = min(x + k, W - 1);
+    int fmin = 255, fmax = 0, gmax = 0;
+    int64_t gsum = 0;
+    for (int yy = y0; yy <= y1; ++yy) {
+        const uint8_t* row = f + (long long)yy * pitch;
+        const uint8_t* below = f + (long long)min(yy + 1, H - 1) * pitch;
+        for (int xx = x0; xx <= x1; ++xx) {
+            const int v = row[xx];
+            const int vx = row[min(xx + 1, W - 1)];
+            const int vy = below[xx];
+            const int g = abs(vx - v) + abs(vy - v);
+            fmin = min(fmin, v);
+            fmax = max(fmax, v);
+            gmax = max(gmax, g);
+            gsum += g;
+        }
+    }
+    const double mrtv = __ddiv_rn((double)((int64_t)(fmax - fmin) * gmax), __dadd_rn((double)gsum, eps));
+    double u = __ddiv_rn(mrtv, msat);
+    if (u > 1.0) u = 1.0;
+    sigma[i] = __double2float_rn(__dsub_rn(s_hi, __dmul_rn(__dsub_rn(s_hi, s_lo), u)));
+}
+
+__global__ void u8_to_float_kernel(const uint8_t* f, long long pitch, int H, int W, float* out)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)H * W) return;
+    const int y = (int)(i / W), x = (int)(i - (long long)y * W);
+    out[i] = (float)f[(long long)y * pitch + x];
+}
+
+// The input of the next pass (reading R9): the output rounded half to even
+// and clamped to [0, 255]; theta_next = f_next (the smoothing passes keep
+// theta = f); the width scaled by decay (one binary32 product) when sig_out
+// is given.
+__global__ void next_input_kernel(const void* g, int g_f64, int H, int W, uint8_t* f_next, long long pitch_next,
+                                  float* theta_next, const float* sig_in, float* sig_out, float decay)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)H * W) return;
+    const int y = (int)(i / W), x = (int)(i - (long long)y * W);
+    const double v = g_f64 ? static_cast<const double*>(g)[i] : (double)static_cast<const float*>(g)[i];
+    double r = rint(v);
+    r = r < 0.0 ? 0.0 : (r > 255.0 ? 255.0 : r);
+    const uint8_t u = (uint8_t)r;
+    f_next[(long long)y * pitch_next + x] = u;
+    if (theta_next) theta_next[i] = (float)u;
+    if (sig_out) sig_out[i] = __fmul_rn(sig_in[i], decay);
+}
+
+unsigned blocks_for(long long n) { return (unsigned)((n + kAppThreads - 1) / kAppThreads); }
+
+int check_sharpen_cfg(const fabf_sharpen_cfg* c)
+{
+    if (!c) return FABF_EINVAL;
+    if (c->w < 1 || c->N < 0 || !(c->lap_sat > 0.0) || !std::isfinite(c->lap_sat)) return FABF_EINVAL;
+    if (!(c->sigma_lo > 0.0) || !(c->sigma_hi >= c->sigma_lo) || !std::isfinite(c->sigma_hi)) return FABF_EINVAL;
+    if (c->w > kWMax || c->N > kNMax) return FABF_EUNSUPPORTED;
+    return FABF_OK;
+}
+
+int check_texture_cfg(const fabf_texture_cfg* c)
+{
+    if (!c) return FABF_EINVAL;
+    if (c->w < 1 || c->N < 0 || c->k < 1 || !(c->eps > 0.0) || !(c->mrtv_sat > 0.0)) return FABF_EINVAL;
+    if (!(c->sigma_lo > 0.0) || !(c->sigma_hi >= c->sigma_lo) || !std::isfinite(c->sigma_hi)) return FABF_EINVAL;
+    if (!(c->sigma_decay > 0.0) || !std::isfinite(c->sigma_decay)) return FABF_EINVAL;
+    if (c->w > kWMax || c->N > kNMax || c->k > kWMax) return FABF_EUNSUPPORTED;
+    return check_sharpen_cfg(&c->sharpen);
+}
+
+// The LoG taps and the saturation level Lq = floor(lap_sat (sum g)^2 + 1/2).
+int sharpen_taps(const fabf_sharpen_cfg* c, SepTaps* T, long long* Lq)
+{
+    uint32_t g[2 * kWMax + 1];
+    int r = 0;
+    const int rc = fabf_gaussian_taps(c->rho_log, g, 2 * kWMax + 1, &r);
+    if (rc) return rc;
+    std::memset(T, 0, sizeof(*T));
+    T->r = r;
+    uint64_t sum = 0;
+    for (int t = 0; t <= 2 * r; ++t) {
+        T->g[t] = g[t];
+        sum += g[t];
+    }
+    const double q = std::floor(c->lap_sat * (double)sum * (double)sum + 0.5);
+    if (!(q >= 1.0 && q < 4.0e18)) return FABF_EINVAL;
+    *Lq = (long long)q;
+    return FABF_OK;
+}
+
+bool all_device(std::initializer_list<const void*> ps)
+{
+    for (const void* p : ps)
+        if (!is_device_ptr(p)) return false;
+    return true;
+}
+
+// Stream-ordered scratch for one pipeline call.
+struct Scratch {
+    void* base = nullptr;
+    cudaStream_t s = nullptr;
+    ~Scratch()
+    {
+        if (base) cudaFreeAsync(base, s);
+    }
+};
+
+// theta and sigma of the sharpening rules for f (device), into theta / sigma.
+int launch_sharpen_maps(const uint8_t* f, long long pitch, int H, int W, int w, const SepTaps& T, long long Lq,
+                        double s_lo, double s_hi, int32_t* rs, uint32_t* gr, int64_t* S, float* theta,
+                        float* sigma, cudaStream_t s)
+{
+    const long long n = (long long)H * W;
+    const unsigned b = blocks_for(n);
+    box_rows_kernel<<<b, kAppThreads, 0, s>>>(f, pitch, H, W, w, rs);
+    sharpen_theta_kernel<<<b, kAppThreads, 0, s>>>(f, pitch, rs, H, W, w, theta);
+    gauss_rows_kernel<<<b, kAppThreads, 0, s>>>(f, pitch, H, W, T, gr);
+    gauss_cols_kernel<<<b, kAppThreads, 0, s>>>(gr, H, W, T, S);
+    sharpen_sigma_kernel<<<b, kAppThreads, 0, s>>>(S, H, W, Lq, s_lo, s_hi, sigma);
+    return cuda_status(cudaGetLastError());
+}
+
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+}  // namespace
+}  // namespace fabf
+
+using namespace fabf;
+
+extern "C" {
+
+int fabf_sharpen_maps(fabf_ctx* ctx, const uint8_t* img, int H, int W, size_t pitch, const fabf_sharpen_cfg* cfg,
+                      float* theta, float* sigma, void* cuda_stream)
+{
+    if (!ctx || !img || !theta || !sigma || H < 1 || W < 1 || pitch < (size_t)W) return FABF_EINVAL;
+    int rc = check_sharpen_cfg(cfg);
+    if (rc) return rc;
+    if (!all_device({img, theta, sigma})) return FABF_EINVAL;
+    SepTaps T;
+    long long Lq = 0;
+    rc = sharpen_taps(cfg, &T, &Lq);
+    if (rc) return rc;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return FABF_ECUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    const size_t n = (size_t)H * W;
+    Scratch sc;
+    sc.s = s;
+    const size_t o_gr = align256(n * 4), o_S = o_gr + align256(n * 4);
+    cudaError_t e = cudaMallocAsync(&sc.base, o_S + n * 8, s);
+    if (e != cudaSuccess) return cuda_status(e);
+    uint8_t* b = static_cast<uint8_t*>(sc.base);
+    return launch_sharpen_maps(img, (long long)pitch, H, W, cfg->w, T, Lq, cfg->sigma_lo, cfg->sigma_hi,
+                               reinterpret_cast<int32_t*>(b), reinterpret_cast<uint32_t*>(b + o_gr),
+                               reinterpret_cast<int64_t*>(b + o_S), theta, sigma, s);
+}
+
+int fabf_texture_sigma(fabf_ctx* ctx, const uint8_t* img, int H, int W, size_t pitch, const fabf_texture_cfg* cfg,
+                       float* sigma, void* cuda_stream)
+{
+    if (!ctx || !img || !sigma || H < 1 || W < 1 || pitch < (size_t)W) return FABF_EINVAL;
+    int rc = check_texture_cfg(cfg);
+    if (rc) return rc;
+    if (!all_device({img, sigma})) return FABF_EINVAL;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return FABF_ECUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    texture_sigma_kernel<<<blocks_for((long long)H * W), kAppThreads, 0, s>>>(
+        img, (long long)pitch, H, W, cfg->k, cfg->eps, cfg->mrtv_sat, cfg->sigma_lo, cfg->sigma_hi, sigma);
+    return cuda_status(cudaGetLastError());
+}
+
+int fabf_sharpen(fabf_ctx* ctx, const uint8_t* img, int H, int W, size_t pitch, const fabf_sharpen_cfg* cfg, void* out,
+                 int out_is_f64, void* cuda_stream)
+{
+    if (!ctx || !img || !out || H < 1 || W < 1 || pitch < (size_t)W || H > 65535 || W > 65535) return FABF_EINVAL;
+    int rc = check_sharpen_cfg(cfg);
+    if (rc) return rc;
+    if (!all_device({img, out})) return FABF_EINVAL;
+    SepTaps T;
+    long long Lq = 0;
+    rc = sharpen_taps(cfg, &T, &Lq);
+    if (rc) return rc;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return FABF_ECUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    const size_t n = (size_t)H * W;
+    const size_t o_sg = align256(n * 4), o_rs = o_sg + align256(n * 4), o_gr = o_rs + align256(n * 4),
+                 o_S = o_gr + align256(n * 4);
+    Scratch sc;
+    sc.s = s;
+    cudaError_t e = cudaMallocAsync(&sc.base, o_S + n * 8, s);
+    if (e != cudaSuccess) return cuda_status(e);
+    uint8_t* b = static_cast<uint8_t*>(sc.base);
+    float* th = reinterpret_cast<float*>(b);
+    float* sg = reinterpret_cast<float*>(b + o_sg);
+    rc = launch_sharpen_maps(img, (long long)pitch, H, W, cfg->w, T, Lq, cfg->sigma_lo, cfg->sigma_hi,
+                             reinterpret_cast<int32_t*>(b + o_rs), reinterpret_cast<uint32_t*>(b + o_gr),
+                             reinterpret_cast<int64_t*>(b + o_S), th, sg, s);
+    if (rc) return rc;
+    return run_fused(ctx, img, pitch, th, sg, H, W, cfg->w, cfg->N, out, out_is_f64, nullptr, s);
+}
+
+int fabf_texture_filter(fabf_ctx* ctx, const uint8_t* img, int H, int W, size_t pitch, const fabf_texture_cfg* cfg,
+                        void* out, int out_is_f64, void* cuda_stream)
+{
+    if (!ctx || !img || !out || H < 1 || W < 1 || pitch < (size_t)W || H > 65535 || W > 65535) return FABF_EINVAL;
+    int rc = check_texture_cfg(cfg);
+    if (rc) return rc;
+    if (!all_device({img, out})) return FABF_EINVAL;
+    const fabf_sharpen_cfg& sc_cfg = cfg->sharpen;
+    SepTaps T;
+    long long Lq = 0;
+    rc = sharpen_taps(&sc_cfg, &T, &Lq);
+    if (rc) return rc;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return FABF_ECUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    const long long n = (long long)H * W;
+    const size_t pn = ((size_t)W + 15) & ~(size_t)15;          // 16-byte rows: the next passes use TMA
+    const int g_f64 = ctx->precision == kPrecFP64 ? 1 : 0;
+    const size_t gsz = (size_t)n * (g_f64 ? 8 : 4);
+    // scratch: sigma1, sigma2, theta, g, f_next (x2), rs, gr, S
+    const size_t o_s2 = align256(n * 4), o_th = o_s2 + align256(n * 4), o_g = o_th + align256(n * 4),
+                 o_f2 = o_g + align256(gsz), o_f3 = o_f2 + align256(pn * H), o_rs = o_f3 + align256(pn * H),
+                 o_gr = o_rs + align256(n * 4), o_S = o_gr + align256(n * 4), total = o_S + n * 8;
+    Scratch sc;
+    sc.s = s;
+    cudaError_t e = cudaMallocAsync(&sc.base, total, s);
+    if (e != cudaSuccess) return cuda_status(e);
+    uint8_t* b = static_cast<uint8_t*>(sc.base);
+    float* s1 = reinterpret_cast<float*>(b);
+    float* s2 = reinterpret_cast<float*>(b + o_s2);
+    float* th = reinterpret_cast<float*>(b + o_th);
+    void* g = b + o_g;
+    uint8_t* f2 = b + o_f2;
+    uint8_t* f3 = b + o_f3;
+    const unsigned nb = blocks_for(n);
+    // pass 1: theta = f, sigma from mRTV
+    texture_sigma_kernel<<<nb, kAppThreads, 0, s>>>(img, (long long)pitch, H, W, cfg->k, cfg->eps, cfg->mrtv_sat,
+                                                    cfg->sigma_lo, cfg->sigma_hi, s1);
+    u8_to_float_kernel<<<nb, kAppThreads, 0, s>>>(img, (long long)pitch, H, W, th);
+    rc = cuda_status(cudaGetLastError());
+    if (rc) return rc;
+    rc = run_fused(ctx, img, pitch, th, s1, H, W, cfg->w, cfg->N, g, g_f64, nullptr, s);
+    if (rc) return rc;
+    // pass 2: the rounded output, theta = f2, sigma scaled by sigma_decay
+    next_input_kernel<<<nb, kAppThreads, 0, s>>>(g, g_f64, H, W, f2, (long long)pn, th, s1, s2,
+                                                 (float)cfg->sigma_decay);
+    rc = cuda_status(cudaGetLastError());
+    if (rc) return rc;
+    rc = run_fused(ctx, f2, pn, th, s2, H, W, cfg->w, cfg->N, g, g_f64, nullptr, s);
+    if (rc) return rc;
+    // pass 3: sharpening of the rounded output
+    next_input_kernel<<<nb, kAppThreads, 0, s>>>(g, g_f64, H, W, f3, (long long)pn, nullptr, nullptr, nullptr, 1.0f);
+    rc = launch_sharpen_maps(f3, (long long)pn, H, W, sc_cfg.w, T, Lq, sc_cfg.sigma_lo, sc_cfg.sigma_hi,
+                             reinterpret_cast<int32_t*>(b + o_rs), reinterpret_cast<uint32_t*>(b + o_gr),
+                             reinterpret_cast<int64_t*>(b + o_S), th, s2, s);
+    if (rc) return rc;
+    return run_fused(ctx, f3, pn, th, s2, H, W, sc_cfg.w, sc_cfg.N, out, out_is_f64, nullptr, s);
+}
+
+}  // extern "C"

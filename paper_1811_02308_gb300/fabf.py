@@ -50,6 +50,19 @@ class Request(C.Structure):
                 ("out", C.c_void_p), ("out_is_f64", C.c_int)]
 
 
+class SharpenCfg(C.Structure):
+    """fabf_sharpen_cfg (Sec. IV-A sharpening maps)."""
+    _fields_ = [("w", C.c_int), ("N", C.c_int), ("rho_log", C.c_double), ("lap_sat", C.c_double),
+                ("sigma_lo", C.c_double), ("sigma_hi", C.c_double)]
+
+
+class TextureCfg(C.Structure):
+    """fabf_texture_cfg (Sec. IV-C texture filtering)."""
+    _fields_ = [("w", C.c_int), ("N", C.c_int), ("k", C.c_int), ("eps", C.c_double), ("mrtv_sat", C.c_double),
+                ("sigma_lo", C.c_double), ("sigma_hi", C.c_double), ("sigma_decay", C.c_double),
+                ("sharpen", SharpenCfg)]
+
+
 def library_path() -> str:
     return _build.LIB
 
@@ -89,6 +102,10 @@ def load(path: str | None = None):
         "fabf_gaussian_taps": ([C.c_double, vp, i, C.POINTER(i)], i),
         "fabf_debug_stages_sep": ([vp, vp, vp, vp, i, i, sz, vp, i, i] + [vp] * 11, i),
         "fabf_bruteforce_sep": ([vp, vp, vp, vp, i, i, sz, vp, i, vp, i, i, vp], i),
+        "fabf_sharpen_maps": ([vp, vp, i, i, sz, C.POINTER(SharpenCfg), vp, vp, vp], i),
+        "fabf_texture_sigma": ([vp, vp, i, i, sz, C.POINTER(TextureCfg), vp, vp], i),
+        "fabf_sharpen": ([vp, vp, i, i, sz, C.POINTER(SharpenCfg), vp, i, vp], i),
+        "fabf_texture_filter": ([vp, vp, i, i, sz, C.POINTER(TextureCfg), vp, i, vp], i),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -477,3 +494,64 @@ def fabf_tile_rows(ctx: Context, w: int, N: int, precision: int = FABF_FP64) -> 
     _check(load().fabf_tile_rows(ctx.handle, int(w), int(N), int(precision), C.byref(t)),
            "fabf_tile_rows")
     return t.value
+
+
+# ---------------------------------------------------------------------------
+# Applications (Sec. IV): device tensors only
+# ---------------------------------------------------------------------------
+def _img_dims(img, H=None, W=None, pitch=None):
+    H = int(img.shape[0]) if H is None else int(H)
+    p = int(img.shape[1]) if pitch is None else int(pitch)
+    W = p if W is None else int(W)
+    return H, W, p
+
+
+def fabf_sharpen_maps(ctx: Context, img, cfg: SharpenCfg, W=None, pitch=None, stream=None):
+    """(theta, sigma) float32 maps of the sharpening rules (device tensors)."""
+    import torch
+    H, W, p = _img_dims(img, None, W, pitch)
+    th = torch.empty((H, W), dtype=torch.float32, device=img.device)
+    sg = torch.empty((H, W), dtype=torch.float32, device=img.device)
+    s = _stream_of(img) if stream is None else stream
+    _check(load().fabf_sharpen_maps(ctx.handle, _ptr(img), H, W, p, C.byref(cfg), _ptr(th), _ptr(sg), s),
+           "fabf_sharpen_maps")
+    return th, sg
+
+
+def fabf_texture_sigma(ctx: Context, img, cfg: TextureCfg, W=None, pitch=None, stream=None):
+    """The mRTV width map of the texture filter (float32 device tensor)."""
+    import torch
+    H, W, p = _img_dims(img, None, W, pitch)
+    sg = torch.empty((H, W), dtype=torch.float32, device=img.device)
+    s = _stream_of(img) if stream is None else stream
+    _check(load().fabf_texture_sigma(ctx.handle, _ptr(img), H, W, p, C.byref(cfg), _ptr(sg), s),
+           "fabf_texture_sigma")
+    return sg
+
+
+def fabf_sharpen(ctx: Context, img, cfg: SharpenCfg, out=None, out_is_f64: bool = True, W=None, pitch=None,
+                 stream=None):
+    """One sharpening pass (Sec. IV-A) on a device image."""
+    H, W, p = _img_dims(img, None, W, pitch)
+    if out is None:
+        import torch
+        out = torch.empty((H, W), dtype=torch.float64 if out_is_f64 else torch.float32, device=img.device)
+    _check_out(out, H, W, out_is_f64)
+    s = _stream_of(img, out) if stream is None else stream
+    _check(load().fabf_sharpen(ctx.handle, _ptr(img), H, W, p, C.byref(cfg), _ptr(out), 1 if out_is_f64 else 0, s),
+           "fabf_sharpen")
+    return out
+
+
+def fabf_texture_filter(ctx: Context, img, cfg: TextureCfg, out=None, out_is_f64: bool = True, W=None,
+                        pitch=None, stream=None):
+    """The texture-filtering pipeline (Sec. IV-C) on a device image."""
+    H, W, p = _img_dims(img, None, W, pitch)
+    if out is None:
+        import torch
+        out = torch.empty((H, W), dtype=torch.float64 if out_is_f64 else torch.float32, device=img.device)
+    _check_out(out, H, W, out_is_f64)
+    s = _stream_of(img, out) if stream is None else stream
+    _check(load().fabf_texture_filter(ctx.handle, _ptr(img), H, W, p, C.byref(cfg), _ptr(out),
+                                      1 if out_is_f64 else 0, s), "fabf_texture_filter")
+    return out
