@@ -440,6 +440,35 @@ def run_gaussian(R, slots, steps, rhos=(3.0, 5.0), N=NDEG):
     return {"workload": "1920x1080 as above, Gaussian spatial kernel (integer taps, peak 1024), N=%d" % N, **out}
 
 
+def run_apps(R, slots, steps, w=5, N=5):
+    """Sec. IV applications on the 1920x1080 inputs: one sharpening pass
+    (maps + Algorithm 1) and the texture-filtering pipeline (mRTV map + two
+    smoothing passes + one sharpening pass), in the FP64 and compensated
+    binary32 forms; Mpix/s of whole pipelines (image pixels per second)."""
+    fabf = R.fabf
+    ctx = R.ctx
+    npix = H_ * W_
+    sh = fabf.SharpenCfg(w, N, 1.0, 10.0, 10.0, 40.0)
+    tx = fabf.TextureCfg(w, N, 2, 1.0, 8.0, 5.0, 60.0, 0.8, sh)
+    out = {"workload": "1920x1080 as above; sharpening: w=%d, N=%d, LoG rho 1, |LoG| saturation 10, "
+                       "sigma 10..40; texture: mRTV k=2, eps 1, saturation 8, sigma 5..60, decay 0.8, then "
+                       "the sharpening pass" % (w, N)}
+    for prec in (0, 2):
+        fabf.fabf_set_precision(ctx, prec)
+        o = slots[prec][0][3]
+        f64 = prec == 0
+        ms_s, _ = R.timed(lambda i: fabf.fabf_sharpen(ctx, slots[prec][i % len(slots[prec])][0], sh, out=o,
+                                                      out_is_f64=f64, stream=R.sh), steps, 3)
+        ms_t, _ = R.timed(lambda i: fabf.fabf_texture_filter(ctx, slots[prec][i % len(slots[prec])][0], tx, out=o,
+                                                             out_is_f64=f64, stream=R.sh), steps, 3)
+        st, _ = fabf.fabf_get_status(ctx, R.sh)
+        out[FORM_NAMES[prec]] = {"sharpen_mpix_per_s": npix * steps / (ms_s / 1e3) / 1e6,
+                                 "texture_mpix_per_s": npix * steps / (ms_t / 1e3) / 1e6,
+                                 "texture_ms_per_frame": ms_t / steps, "status": st}
+    fabf.fabf_set_precision(ctx, 0)
+    return out
+
+
 def sweep(args):
     """Config 1: 1920x1080 (200 blobs), theta = f + zeta, sigma in [5, 60];
     Mpix/s of every form for w in {5, 10, 20, 40} x N in {3, 4, 5, 6} (inputs
@@ -744,6 +773,7 @@ def main():
                                for k, v in bf_ms.items()}}
     if rank == 0 and not args.no_extra and ws == 1:
         line["gaussian"] = run_gaussian(R, slots, max(10, args.steps // 10))
+        line["applications"] = run_apps(R, slots, max(10, args.steps // 10))
         line["batch"] = {FORM_NAMES[p]: run_batch(R, p, max(5, args.steps // 20)) for p in (0, best)}
         line["serve"] = run_serve(R, best, args.serve_seconds)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
