@@ -37,6 +37,7 @@ struct fabf_ctx {
     unsigned long long* d_nfb = nullptr;     // fallback pixel count
     void* stage = nullptr;                   // grow-only staging buffer for host pointers
     size_t stage_bytes = 0;
+    std::mutex stage_lock;                   // one host-pointer call at a time uses the staging buffer
     std::mutex tune_lock;
     std::map<int, fabf::TuneEntry> tune;     // key: tune_key(w, N, precision)
     fabf::ServeState* serve = nullptr;
@@ -108,8 +109,9 @@ int ensure_stage(fabf_ctx* ctx, size_t bytes);
 // Run `launch(d_img, d_pitch, d_theta, d_sigma, d_out)` on device buffers.
 // All-device arguments are passed through (the call stays stream-ordered; the
 // status words are read by fabf_get_status).  Host buffers are staged through
-// the context's buffer (16-byte aligned image rows), the output copied back,
-// and the call synchronises and returns the kernels' status.
+// the context's buffer (16-byte aligned image rows; one such call at a time
+// per context), the output copied back, and the call synchronises and
+// returns the kernels' status.
 template <typename Launch>
 int with_device_buffers(fabf_ctx* ctx, const uint8_t* img, const float* theta, const float* sigma, int H, int W,
                         size_t pitch, void* out, int out_is_f64, cudaStream_t s, Launch&& launch)
@@ -117,6 +119,7 @@ int with_device_buffers(fabf_ctx* ctx, const uint8_t* img, const float* theta, c
     const bool di = is_device_ptr(img), dt = is_device_ptr(theta), ds = is_device_ptr(sigma),
                dout = is_device_ptr(out);
     if (di && dt && ds && dout) return launch(img, pitch, theta, sigma, out);
+    std::lock_guard<std::mutex> staged(ctx->stage_lock);   // held until the synchronous call returns
     const size_t npix = (size_t)H * W;
     const size_t osz = out_is_f64 ? 8 : 4;
     const size_t ipitch = ((size_t)W + 15) & ~(size_t)15;

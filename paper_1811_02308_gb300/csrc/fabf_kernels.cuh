@@ -33,6 +33,8 @@
 
 #include <cuda.h>
 #include <cuda_runtime.h>
+
+#include <atomic>
 #include <cstdint>
 
 #include "fabf_device.cuh"
@@ -114,6 +116,23 @@ __host__ __device__ inline size_t fused_smem_bytes(int N, int w, int Cb, int TH)
     const int n64 = K > 2 ? K - 2 : 0;
     size_t v = (size_t)kChunk * Cb * (4 + 4 * n32) + (size_t)2 * kChunk * kLaneTable + (size_t)kChunk * Cb * 8 * n64;
     return 128 + tile + ((v + 15) & ~(size_t)15) + kRedoBytes;
+}
+
+// Raise a kernel's dynamic shared-memory limit once per device and kernel
+// (the attribute is per device; the flags are set after a successful call,
+// and a race only repeats the call).
+template <auto Kernel>
+inline cudaError_t set_smem_limit_once(int bytes)
+{
+    constexpr int kMaxDevices = 64;
+    static std::atomic<bool> done[kMaxDevices];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < kMaxDevices && done[dev].load(std::memory_order_acquire)) return cudaSuccess;
+    e = cudaFuncSetAttribute(Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess && dev >= 0 && dev < kMaxDevices) done[dev].store(true, std::memory_order_release);
+    return e;
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p)

@@ -14,13 +14,8 @@ constexpr int kMaxDynSmem = 110 * 1024;   // >= fused_smem_bytes for every (w <=
 template <int N, int PREC>
 cudaError_t launch_fused_one(const CUtensorMap& tm, const FusedParams& p, dim3 grid, size_t smem, cudaStream_t s)
 {
-    static bool attr_set = false;
-    if (!attr_set) {
-        const cudaError_t e =
-            cudaFuncSetAttribute(fabf_fused_kernel<N, PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    const cudaError_t e = set_smem_limit_once<fabf_fused_kernel<N, PREC>>(kMaxDynSmem);
+    if (e != cudaSuccess) return e;
     fabf_fused_kernel<N, PREC><<<grid, kThreads, smem, s>>>(tm, p);
     return cudaGetLastError();
 }
@@ -44,13 +39,8 @@ cudaError_t launch_fused_impl(int N, const CUtensorMap& tm, const FusedParams& p
 template <int PREC>
 cudaError_t launch_batch_impl(const BatchParams& p, int grid, size_t smem, cudaStream_t s)
 {
-    static bool attr_set = false;
-    if (!attr_set) {
-        const cudaError_t e =
-            cudaFuncSetAttribute(fabf_batch_kernel<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    const cudaError_t e = set_smem_limit_once<fabf_batch_kernel<PREC>>(kMaxDynSmem);
+    if (e != cudaSuccess) return e;
     fabf_batch_kernel<PREC><<<grid, kThreads, smem, s>>>(p);
     return cudaGetLastError();
 }

@@ -547,13 +547,8 @@ constexpr int kSepMaxDynSmem = 110 * 1024;   // >= sep_smem_bytes for every r <=
 template <int N, int PREC>
 cudaError_t launch_sep_one(const CUtensorMap& tm, const SepParams& p, dim3 grid, size_t smem, cudaStream_t s)
 {
-    static bool attr_set = false;
-    if (!attr_set) {
-        const cudaError_t e = cudaFuncSetAttribute(fabf_sep_kernel<N, PREC>,
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, kSepMaxDynSmem);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    const cudaError_t e = set_smem_limit_once<fabf_sep_kernel<N, PREC>>(kSepMaxDynSmem);
+    if (e != cudaSuccess) return e;
     fabf_sep_kernel<N, PREC><<<grid, kThreads, smem, s>>>(tm, p);
     return cudaGetLastError();
 }

@@ -250,3 +250,30 @@ def test_bruteforce_matches_oracle(ctx, oracle_mod, w):
     ref = oracle_mod.bruteforce(f, th, s, w)
     assert g_close(g64, ref) <= 1e-12
     assert g_close(g32, ref) <= 2e-5
+
+
+def test_concurrent_host_pointer_calls_on_one_context(ctx, oracle_mod):
+    # host-pointer calls stage through the context's buffer one at a time;
+    # four threads calling at once each get their own image's result
+    import threading
+    imgs = [inputs(61 + 7 * i, 97 + 5 * i, 500 + i) for i in range(4)]
+    refs = [oracle_mod.fabf(f, th, s, 4, 5)[0] for f, th, s in imgs]
+    outs = [np.zeros(im[0].shape, np.float64) for im in imgs]
+    errs = []
+
+    def work(i):
+        try:
+            for _ in range(3):
+                f, th, s = imgs[i]
+                fabf.fabf_filter(ctx, f, th, s, 4, 5, out=outs[i])
+        except Exception as e:   # noqa: BLE001 - reported below
+            errs.append(e)
+
+    ts = [threading.Thread(target=work, args=(i,)) for i in range(4)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    assert not errs
+    for o, r in zip(outs, refs):
+        assert g_close(o, r) <= RTOL_G
