@@ -405,69 +405,17 @@ __device__ __forceinline__ bool fabf_tile(const CUtensorMap* tmap, const ImageJo
         if (y0 + r0 >= J.H) break;                                 // uniform per CTA
         // 2. Vertical phase for output rows r0 .. r0+7.
         if (threadIdx.x == 0) *redo_n = 0u;
+        // 2a. Window sums of column c (threads c < Cb): store, then slide the
+        //     window from [r, r+2w] to [r+1, r+2w+1].
         if (c < Cb) {
             if (col_in) {
-                // Window of chunk row rr: tile rows [r0 + rr, r0 + rr + 2w]
-                // = [r0 + rr, r0 + 7] u [r0 + 8, r0 + rr + 2w] (2w + 1 >= 8,
-                // i.e. w >= 4): suffix extrema of the chunk's own rows, then
-                // prefix extrema from r0 + 8 that grow by one row per rr --
-                // 2w + 8 row visits per chunk.  For w < 4 every window is
-                // visited directly (2w + 1 < 8 rows).
-                // (the suffix extrema wait in this thread's own entries of the
-                // shared min / max rows)
-                uint8_t qmn = 255, qmx = 0;
-                const bool split = 2 * w + 1 >= kChunk;
-                if (split) {
-                    uint8_t mn = 255, mx = 0;
-#pragma unroll
-                    for (int rr = kChunk - 1; rr >= 0; --rr) {
-                        const int t = r0 + rr;
-                        if (t >= rowlo && t <= rowhi) {
-                            const uint8_t v = tile[t * Cb + c];
-                            mn = v < mn ? v : mn;
-                            mx = v > mx ? v : mx;
-                        }
-                        vmin[rr * Cb + c] = mn;
-                        vmax[rr * Cb + c] = mx;
-                    }
-                    const int a = max(r0 + kChunk, rowlo), b = min(r0 + 2 * w, rowhi);
-                    for (int t = a; t <= b; ++t) {
-                        const uint8_t v = tile[t * Cb + c];
-                        qmn = v < qmn ? v : qmn;
-                        qmx = v > qmx ? v : qmx;
-                    }
-                }
 #pragma unroll
                 for (int rr = 0; rr < kChunk; ++rr) {
                     const int r = r0 + rr;
-                    uint8_t mn, mx;
-                    if (split) {
-                        const int t = r + 2 * w;            // the row entering the prefix part
-                        if (rr > 0 && t >= rowlo && t <= rowhi) {
-                            const uint8_t v = tile[t * Cb + c];
-                            qmn = v < qmn ? v : qmn;
-                            qmx = v > qmx ? v : qmx;
-                        }
-                        const uint8_t sn = vmin[rr * Cb + c], sx = vmax[rr * Cb + c];
-                        mn = sn < qmn ? sn : qmn;
-                        mx = sx > qmx ? sx : qmx;
-                    } else {
-                        mn = 255;
-                        mx = 0;
-                        const int a = max(r, rowlo), b = min(r + 2 * w, rowhi);
-                        for (int t = a; t <= b; ++t) {
-                            const uint8_t v = tile[t * Cb + c];
-                            mn = v < mn ? v : mn;
-                            mx = v > mx ? v : mx;
-                        }
-                    }
-                    vmin[rr * Cb + c] = mn;
-                    vmax[rr * Cb + c] = mx;
 #pragma unroll
                     for (int k = 0; k < n32; ++k) v32[(k * kChunk + rr) * Cb + c] = s32[k];
 #pragma unroll
                     for (int k = 0; k < n64; ++k) v64[(k * kChunk + rr) * Cb + c] = s64[k];
-                    // slide the window from [r, r+2w] to [r+1, r+2w+1]
                     if (r >= rowlo && r <= rowhi) {
                         const uint32_t v = tile[r * Cb + c];
                         uint32_t pw = v;
@@ -489,15 +437,87 @@ __device__ __forceinline__ bool fabf_tile(const CUtensorMap* tmap, const ImageJo
                     }
                 }
             } else {
-                // outside the image: identities of min, max and sum
+                // outside the image: the identity of the sums
 #pragma unroll
                 for (int rr = 0; rr < kChunk; ++rr) {
-                    vmin[rr * Cb + c] = 255;
-                    vmax[rr * Cb + c] = 0;
 #pragma unroll
                     for (int k = 0; k < n32; ++k) v32[(k * kChunk + rr) * Cb + c] = 0;
 #pragma unroll
                     for (int k = 0; k < n64; ++k) v64[(k * kChunk + rr) * Cb + c] = 0;
+                }
+            }
+        }
+        // 2b. Vertical extrema of column ce, on the threads the sums leave
+        //     idle (thread Cb + ce where it exists, else thread ce after its
+        //     sums), so the two run in different warps.
+        {
+            const int ce = threadIdx.x >= Cb ? threadIdx.x - Cb : (threadIdx.x + Cb >= kThreads ? threadIdx.x : -1);
+            if (ce >= 0 && ce < Cb) {
+                const int Xe = xs + ce;
+                if (Xe >= 0 && Xe < J.W) {
+                    // Window of chunk row rr: tile rows [r0 + rr, r0 + rr + 2w]
+                    // = [r0 + rr, r0 + 7] u [r0 + 8, r0 + rr + 2w] (2w + 1 >= 8,
+                    // i.e. w >= 4): suffix extrema of the chunk's own rows, then
+                    // prefix extrema from r0 + 8 that grow by one row per rr --
+                    // 2w + 8 row visits per chunk.  For w < 4 every window is
+                    // visited directly (2w + 1 < 8 rows).  The suffix extrema
+                    // wait in this thread's own entries of the shared rows.
+                    uint8_t qmn = 255, qmx = 0;
+                    const bool split = 2 * w + 1 >= kChunk;
+                    if (split) {
+                        uint8_t mn = 255, mx = 0;
+#pragma unroll
+                        for (int rr = kChunk - 1; rr >= 0; --rr) {
+                            const int t = r0 + rr;
+                            if (t >= rowlo && t <= rowhi) {
+                                const uint8_t v = tile[t * Cb + ce];
+                                mn = v < mn ? v : mn;
+                                mx = v > mx ? v : mx;
+                            }
+                            vmin[rr * Cb + ce] = mn;
+                            vmax[rr * Cb + ce] = mx;
+                        }
+                        const int a = max(r0 + kChunk, rowlo), b = min(r0 + 2 * w, rowhi);
+                        for (int t = a; t <= b; ++t) {
+                            const uint8_t v = tile[t * Cb + ce];
+                            qmn = v < qmn ? v : qmn;
+                            qmx = v > qmx ? v : qmx;
+                        }
+                    }
+#pragma unroll
+                    for (int rr = 0; rr < kChunk; ++rr) {
+                        const int r = r0 + rr;
+                        uint8_t mn, mx;
+                        if (split) {
+                            const int t = r + 2 * w;        // the row entering the prefix part
+                            if (rr > 0 && t >= rowlo && t <= rowhi) {
+                                const uint8_t v = tile[t * Cb + ce];
+                                qmn = v < qmn ? v : qmn;
+                                qmx = v > qmx ? v : qmx;
+                            }
+                            const uint8_t sn = vmin[rr * Cb + ce], sx = vmax[rr * Cb + ce];
+                            mn = sn < qmn ? sn : qmn;
+                            mx = sx > qmx ? sx : qmx;
+                        } else {
+                            mn = 255;
+                            mx = 0;
+                            const int a = max(r, rowlo), b = min(r + 2 * w, rowhi);
+                            for (int t = a; t <= b; ++t) {
+                                const uint8_t v = tile[t * Cb + ce];
+                                mn = v < mn ? v : mn;
+                                mx = v > mx ? v : mx;
+                            }
+                        }
+                        vmin[rr * Cb + ce] = mn;
+                        vmax[rr * Cb + ce] = mx;
+                    }
+                } else {
+                    // outside the image: the identities of min and max
+#pragma unroll
+                    for (int rr = 0; rr < kChunk; ++rr) {
+                        vmin[rr * Cb + ce] = 255;
+                        vmax[rr * Cb + ce] = 0;
+                    }
                 }
             }
         }
