@@ -173,10 +173,10 @@ int fabf_batch_stats(fabf_ctx* ctx, int* graph_captures, int* graph_launches);
  * the context uses for (w, N, precision): the autotuner's measured choice
  * among 8, 16, 24, 32 and 40 when autotune is on (the first query of a key
  * times each candidate on a synthetic 2048x4096 image and caches the result,
- * in tune_cache_path too), else 8 (FABF_FP64), 16 (FABF_FP64FIT_FP32REC) or
- * 32 (FABF_CFP32).  A single-image call uses the tallest candidate no taller
- * than this that still fills the SMs with several waves of CTAs (20 for the
- * FP64 fit form, 4 for the compensated form).  Make the first query of a key
+ * in tune_cache_path too), else 8 (FABF_FP64, FABF_FP64FIT_FP32REC) or 40
+ * (FABF_CFP32).  A single-image call uses the tallest candidate no taller
+ * than this that still fills the SMs with at least 6 waves of resident CTAs
+ * (compensated form), else 8.  Make the first query of a key
  * before any stream capture. */
 int fabf_tile_rows(fabf_ctx* ctx, int w, int N, int precision, int* tile_rows);
 

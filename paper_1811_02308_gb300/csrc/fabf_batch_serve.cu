@@ -187,7 +187,7 @@ int tile_rows_for(fabf_ctx* ctx, int w, int N, int prec, int H, int W)
     for (int TH : kTileCandidates) {
         if (TH > steady) break;
         const size_t smem = fused_smem_bytes(N, w, Cb, TH) + 1024;      // + the per-CTA reservation
-        const int per_sm = std::max(1, std::min(pc == kPrecFP64 ? 2 : 3, (int)((size_t)228 * 1024 / smem)));
+        const int per_sm = std::max(1, std::min(kCtasPerSm[pc], (int)((size_t)228 * 1024 / smem)));
         const long long tiles = tiles_x * ((H + TH - 1) / TH);
         if (tiles >= (long long)kMinWaves[pc] * num_sms * per_sm) best = TH;
     }
@@ -271,7 +271,8 @@ static int batch_build(fabf_ctx* ctx, const fabf_request* reqs, int n)
     p.next_tile = b->d_counter;
     p.status = ctx->d_status;
     p.n_fallback = ctx->d_nfb;
-    const int per_sm = smem <= (size_t)(113 * 1024) ? 2 : 1;
+    const int per_sm = std::max(1, std::min(kCtasPerSm[prec < 0 || prec > 2 ? 0 : prec],
+                                            (int)((size_t)228 * 1024 / (smem + 1024))));
     long long grid = (long long)ctx->num_sms * per_sm;
     if (grid > tiles) grid = tiles;
 

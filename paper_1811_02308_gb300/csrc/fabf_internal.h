@@ -93,12 +93,15 @@ int launch_fused_scratch(const uint8_t* img, size_t pitch, const float* theta, c
 // = 0: batches).  For one H x W image the choice is the tallest candidate
 // no taller than the steady one that still leaves kMinWaves[prec] waves of
 // resident CTAs across the SMs, else the shortest candidate: a short image
-// with tall tiles leaves SMs idle in the last wave.  Measured at 720p, 1080p
-// and 4096^2 for w in {5, 10, 20, 40}.
+// with tall tiles leaves SMs idle in the last wave.  Measured at 720p, 1080p,
+// 2160x3840 and 4096^2 for w in {5, 20, 40}.
 int tile_rows_for(fabf_ctx* ctx, int w, int N, int prec, int H, int W);
 constexpr int kTileCandidates[] = {8, 16, 24, 32, 40};
-constexpr int kSteadyTileRows[3] = {8, 16, 32};   // FP64, FP64 fit + FP32, compensated FP32
-constexpr int kMinWaves[3] = {1, 20, 4};
+constexpr int kSteadyTileRows[3] = {8, 8, 40};    // FP64, FP64 fit + FP32, compensated FP32
+constexpr int kMinWaves[3] = {1, 1, 6};
+// Resident CTAs per SM the kernels are compiled for (MinBlocks in
+// fabf_kernels.cuh); shared memory may allow fewer.
+constexpr int kCtasPerSm[3] = {2, 4, 4};
 constexpr int kDefaultTileRows = 32;               // stage-export runs of the tests
 
 int read_and_clear_status(fabf_ctx* ctx, cudaStream_t s, int* status, uint64_t* nfb, uint64_t* nredo);

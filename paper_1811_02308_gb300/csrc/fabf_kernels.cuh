@@ -661,10 +661,11 @@ __device__ __forceinline__ bool fabf_tile(const CUtensorMap* tmap, const ImageJo
 // ---------------------------------------------------------------------------
 // Resident CTAs per SM the register budget is sized for: the FP64 form is
 // bound by the FP64 pipe (two CTAs saturate it); the binary32 forms are
-// latency bound and gain from a third CTA.
+// bound by instruction issue and latency and gain from a fourth CTA (64
+// registers per thread), measured faster at every image size.
 template <int PREC>
 struct MinBlocks {
-    static constexpr int value = PREC == kPrecFP64 ? 2 : 3;
+    static constexpr int value = PREC == kPrecFP64 ? 2 : 4;
 };
 
 template <int N, int PREC>

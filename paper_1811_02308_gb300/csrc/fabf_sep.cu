@@ -30,7 +30,8 @@ static int sep_tile_rows(fabf_ctx* ctx, int r, int N, int prec, int H, int W)
     for (int TH : kTileCandidates) {
         if (TH > steady) break;
         const size_t smem = sep_smem_bytes(N, r, Cb, TH) + 1024;
-        const int per_sm = std::max(1, std::min(prec == kPrecFP64 ? 2 : 3, (int)((size_t)228 * 1024 / smem)));
+        const int per_sm = std::max(1, std::min(kCtasPerSm[prec < 0 || prec > 2 ? 0 : prec],
+                                                (int)((size_t)228 * 1024 / smem)));
         const long long tiles = tiles_x * ((H + TH - 1) / TH);
         if (tiles >= (long long)kMinWaves[prec] * ctx->num_sms * per_sm) best = TH;
     }

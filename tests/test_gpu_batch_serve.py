@@ -139,8 +139,8 @@ def test_autotuned_tiles_give_identical_results():
             th_rows = fabf.fabf_tile_rows(tc, w, N)
             assert th_rows in (8, 16, 24, 32, 40)
             assert fabf.fabf_tile_rows(dc, w, N) == 8
-            assert fabf.fabf_tile_rows(dc, w, N, fabf.FABF_FP64FIT_FP32REC) == 16
-            assert fabf.fabf_tile_rows(dc, w, N, fabf.FABF_CFP32) == 32
+            assert fabf.fabf_tile_rows(dc, w, N, fabf.FABF_FP64FIT_FP32REC) == 8
+            assert fabf.fabf_tile_rows(dc, w, N, fabf.FABF_CFP32) == 40
             a = fabf.fabf_filter(tc, dev(f), dev(th), dev(s), w, N).cpu().numpy()
             b = fabf.fabf_filter(dc, dev(f), dev(th), dev(s), w, N).cpu().numpy()
             assert np.array_equal(a, b)
