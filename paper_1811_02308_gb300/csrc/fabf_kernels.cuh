@@ -315,6 +315,38 @@ __device__ __forceinline__ int lane_block_query(const uint8_t* row, const uint8_
     return r;
 }
 
+// Add (Sign = +1) or subtract (Sign = -1) the powers v^1..v^K of one pixel to
+// the running window sums: k = 1, 2 in 32 bits, k >= 3 in 64 bits.  v^2..v^4
+// are exact in 32 bits (255^4 < 2^32), v^5 takes one widening multiply.
+template <int K, int Sign>
+__device__ __forceinline__ void add_powers(uint32_t (&s32)[2], uint64_t (&s64)[4], uint32_t v)
+{
+    const uint32_t v2 = v * v;
+    const uint32_t v3 = v2 * v;
+    const uint32_t v4 = v3 * v;
+    if constexpr (Sign > 0) {
+        s32[0] += v;
+        if constexpr (K >= 2) s32[1] += v2;
+        if constexpr (K >= 3) s64[0] += v3;
+        if constexpr (K >= 4) s64[1] += v4;
+        if constexpr (K >= 5) {
+            const uint64_t v5 = (uint64_t)v4 * v;
+            s64[2] += v5;
+            if constexpr (K >= 6) s64[3] += v5 * v;
+        }
+    } else {
+        s32[0] -= v;
+        if constexpr (K >= 2) s32[1] -= v2;
+        if constexpr (K >= 3) s64[0] -= v3;
+        if constexpr (K >= 4) s64[1] -= v4;
+        if constexpr (K >= 5) {
+            const uint64_t v5 = (uint64_t)v4 * v;
+            s64[2] -= v5;
+            if constexpr (K >= 6) s64[3] -= v5 * v;
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // One output tile (tx, ty) of image J.  smem must hold fused_smem_bytes();
 // its first 8 bytes are the CTA's mbarrier (initialised by the caller when
@@ -376,23 +408,11 @@ __device__ __forceinline__ bool fabf_tile(const CUtensorMap* tmap, const ImageJo
     const bool col_in = (c < Cb) && X >= 0 && X < J.W;
 
     // Running vertical sums for column c, initialised for output row 0.
-    uint32_t s32[n32 > 0 ? n32 : 1];
-    uint64_t s64[n64 > 0 ? n64 : 1];
-#pragma unroll
-    for (int k = 0; k < n32; ++k) s32[k] = 0;
-#pragma unroll
-    for (int k = 0; k < n64; ++k) s64[k] = 0;
+    uint32_t s32[2] = {0u, 0u};
+    uint64_t s64[4] = {0ull, 0ull, 0ull, 0ull};
     if (col_in) {
         const int t1 = min(2 * w, rowhi);
-        for (int t = rowlo; t <= t1; ++t) {
-            const uint32_t v = tile[t * Cb + c];
-            uint32_t pw = v;
-#pragma unroll
-            for (int k = 0; k < n32; ++k) { s32[k] += pw; pw *= v; }
-            uint64_t pq = (uint64_t)pw;
-#pragma unroll
-            for (int k = 0; k < n64; ++k) { s64[k] += pq; pq *= v; }
-        }
+        for (int t = rowlo; t <= t1; ++t) add_powers<K, +1>(s32, s64, tile[t * Cb + c]);
     }
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -416,25 +436,9 @@ __device__ __forceinline__ bool fabf_tile(const CUtensorMap* tmap, const ImageJo
                     for (int k = 0; k < n32; ++k) v32[(k * kChunk + rr) * Cb + c] = s32[k];
 #pragma unroll
                     for (int k = 0; k < n64; ++k) v64[(k * kChunk + rr) * Cb + c] = s64[k];
-                    if (r >= rowlo && r <= rowhi) {
-                        const uint32_t v = tile[r * Cb + c];
-                        uint32_t pw = v;
-#pragma unroll
-                        for (int k = 0; k < n32; ++k) { s32[k] -= pw; pw *= v; }
-                        uint64_t pq = (uint64_t)pw;
-#pragma unroll
-                        for (int k = 0; k < n64; ++k) { s64[k] -= pq; pq *= v; }
-                    }
+                    if (r >= rowlo && r <= rowhi) add_powers<K, -1>(s32, s64, tile[r * Cb + c]);
                     const int te = r + 2 * w + 1;
-                    if (te >= rowlo && te <= rowhi) {
-                        const uint32_t v = tile[te * Cb + c];
-                        uint32_t pw = v;
-#pragma unroll
-                        for (int k = 0; k < n32; ++k) { s32[k] += pw; pw *= v; }
-                        uint64_t pq = (uint64_t)pw;
-#pragma unroll
-                        for (int k = 0; k < n64; ++k) { s64[k] += pq; pq *= v; }
-                    }
+                    if (te >= rowlo && te <= rowhi) add_powers<K, +1>(s32, s64, tile[te * Cb + c]);
                 }
             } else {
                 // outside the image: the identity of the sums
