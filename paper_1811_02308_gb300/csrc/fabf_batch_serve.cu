@@ -92,8 +92,6 @@ void free_tune_image(TuneImage& t)
     t = TuneImage{};
 }
 
-std::mutex g_tune_img_lock;
-std::map<int, TuneImage> g_tune_img;   // per device
 
 void load_tune_cache(fabf_ctx* ctx)
 {
@@ -120,14 +118,19 @@ static int steady_tile_rows(fabf_ctx* ctx, int w, int N, int prec)
     auto it = ctx->tune.find(tune_key(w, N, prec));
     if (it != ctx->tune.end()) return it->second.TH;
 
-    TuneImage* t;
-    {
-        std::lock_guard<std::mutex> gi(g_tune_img_lock);
-        t = &g_tune_img[ctx->device];
-        if (ensure_tune_image(*t) != FABF_OK) return dflt;
+    // the timing image lives only for this measurement (about 140 MB)
+    TuneImage timg;
+    TuneImage* t = &timg;
+    if (ensure_tune_image(timg) != FABF_OK) {
+        free_tune_image(timg);
+        (void)cudaGetLastError();
+        return dflt;
     }
     cudaStream_t s;
-    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return dflt;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+        free_tune_image(timg);
+        return dflt;
+    }
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -154,6 +157,7 @@ static int steady_tile_rows(fabf_ctx* ctx, int w, int N, int prec)
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaStreamDestroy(s);
+    free_tune_image(timg);
     (void)cudaGetLastError();
     ctx->tune[tune_key(w, N, prec)] = TuneEntry{best, best_ms};
     if (!ctx->tune_cache_path.empty()) {

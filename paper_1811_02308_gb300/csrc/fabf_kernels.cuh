@@ -455,7 +455,8 @@ __device__ __forceinline__ bool fabf_tile(const CUtensorMap* tmap, const ImageJo
         //     idle (thread Cb + ce where it exists, else thread ce after its
         //     sums), so the two run in different warps.
         {
-            const int ce = threadIdx.x >= Cb ? threadIdx.x - Cb : (threadIdx.x + Cb >= kThreads ? threadIdx.x : -1);
+            const int tid = (int)threadIdx.x;
+            const int ce = tid >= Cb ? tid - Cb : (tid + Cb >= kThreads ? tid : -1);
             if (ce >= 0 && ce < Cb) {
                 const int Xe = xs + ce;
                 if (Xe >= 0 && Xe < J.W) {
