@@ -45,8 +45,8 @@ WORKLOAD = ("1920x1080 uint8 synthetic (200 blobs, 4 step edges, noise 10), box 
 # the library picks; profiles/); set to None whenever the kernel changes
 # until it is re-captured.  The float output of a launch stays in the 126 MB
 # L2 when the kernel ends, so the figure is the 9 B/px of compulsory reads.
-NCU_TRAFFIC_BYTES = 18.87e6        # FP64 form kernel (8-row tiles)
-NCU_TRAFFIC_BYTES_CFP32 = 18.77e6  # compensated FP32 kernel (16-row tiles)
+NCU_TRAFFIC_BYTES = 18.76e6        # FP64 form kernel (8-row tiles)
+NCU_TRAFFIC_BYTES_CFP32 = 19.40e6  # compensated FP32 kernel (8-row tiles, 4 CTAs per SM)
 NCU_TRAFFIC_BYTES_SEP = 18.77e6    # separable (Gaussian) kernel, rho = 5, compensated FP32
 SM_COUNT, SM_MAX_MHZ = 152, 2070.0
 FP64_FLOP_PER_SM_CLK = 4.0        # 2 DFMA per clock per SM (nominal 1.25 TFLOP/s FP64)
