@@ -213,6 +213,118 @@ int launch_fused_scratch(const uint8_t* img, size_t pitch, const float* theta, c
 }  // namespace fabf
 
 // ---------------------------------------------------------------------------
+// Host buffers, pipelined: the image is cut into up to kBands bands of tile
+// rows.  Band b's inputs (its rows of theta and sigma, and the image rows up
+// to its last tile's halo not copied yet) go up on the copy-in stream; its
+// tiles run on their own stream as soon as they are there (bands are
+// independent, so their kernels may overlap); its output rows come back on
+// the copy-out stream.  Copies in, kernels and copies out of different bands
+// overlap; the call returns when the last band is back, with the kernels'
+// status, as the unpipelined host path does.
+// ---------------------------------------------------------------------------
+static int ensure_pipeline(fabf_ctx* ctx)
+{
+    if (ctx->pipe_ready) return FABF_OK;
+    cudaError_t e = cudaStreamCreateWithFlags(&ctx->s_in, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->s_out, cudaStreamNonBlocking);
+    for (int b = 0; b < fabf_ctx::kBands && e == cudaSuccess; ++b) {
+        e = cudaStreamCreateWithFlags(&ctx->s_band[b], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_in[b], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_k[b], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_start, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_done, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_status(e);
+    ctx->pipe_ready = true;
+    return FABF_OK;
+}
+
+static void destroy_pipeline(fabf_ctx* ctx)
+{
+    if (!ctx->pipe_ready) return;
+    cudaStreamDestroy(ctx->s_in);
+    cudaStreamDestroy(ctx->s_out);
+    for (int b = 0; b < fabf_ctx::kBands; ++b) {
+        cudaStreamDestroy(ctx->s_band[b]);
+        cudaEventDestroy(ctx->ev_in[b]);
+        cudaEventDestroy(ctx->ev_k[b]);
+    }
+    cudaEventDestroy(ctx->ev_start);
+    cudaEventDestroy(ctx->ev_done);
+    ctx->pipe_ready = false;
+}
+
+static int filter_host_pipelined(fabf_ctx* ctx, const uint8_t* img, const float* theta, const float* sigma, int H,
+                                 int W, size_t pitch, int w, int N, void* out, int out_f64, cudaStream_t s)
+{
+    std::lock_guard<std::mutex> staged(ctx->stage_lock);
+    int rc = ensure_pipeline(ctx);
+    if (rc) return rc;
+    const int prec = ctx->precision;
+    const int TH = tile_rows_for(ctx, w, N, prec, H, W);
+    const size_t npix = (size_t)H * W, osz = out_f64 ? 8 : 4;
+    const size_t ipitch = ((size_t)W + 15) & ~(size_t)15;
+    const size_t o_th = (ipitch * H + 255) & ~(size_t)255;
+    const size_t o_sg = o_th + ((npix * 4 + 255) & ~(size_t)255);
+    const size_t o_out = o_sg + ((npix * 4 + 255) & ~(size_t)255);
+    rc = ensure_stage(ctx, o_out + npix * osz);
+    if (rc) return rc;
+    uint8_t* base = static_cast<uint8_t*>(ctx->stage);
+    const float* d_th = reinterpret_cast<const float*>(base + o_th);
+    const float* d_sg = reinterpret_cast<const float*>(base + o_sg);
+    uint8_t* d_out = base + o_out;
+
+    FusedParams p;
+    std::memset(&p, 0, sizeof(p));
+    CUtensorMap tm;
+    const size_t smem = make_job(&p.job, &tm, base, ipitch, d_th, d_sg, H, W, w, N, d_out, out_f64, TH);
+    p.status = ctx->d_status;
+    p.n_fallback = ctx->d_nfb;
+    const int tiles_y = p.job.tiles_y;
+    const int nb = tiles_y < fabf_ctx::kBands ? tiles_y : fabf_ctx::kBands;
+    const int bt = (tiles_y + nb - 1) / nb;                      // tile rows per band
+
+    cudaError_t e = cudaEventRecord(ctx->ev_start, s);           // after the caller's earlier work
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->s_in, ctx->ev_start, 0);
+    int copied = 0;                                              // image rows already sent
+    for (int b = 0; b < nb && e == cudaSuccess; ++b) {
+        const int t0 = b * bt, t1 = t0 + bt < tiles_y ? t0 + bt : tiles_y;
+        if (t0 >= t1) break;
+        const int y0 = t0 * TH, y1 = t1 * TH < H ? t1 * TH : H;
+        const int need = y1 + w < H ? y1 + w : H;                // rows the band's halo reaches
+        if (need > copied)
+            e = cudaMemcpy2DAsync(base + (size_t)copied * ipitch, ipitch, img + (size_t)copied * pitch, pitch, W,
+                                  need - copied, cudaMemcpyHostToDevice, ctx->s_in);
+        copied = need > copied ? need : copied;
+        const size_t r0 = (size_t)y0 * W, rn = (size_t)(y1 - y0) * W;
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(base + o_th + r0 * 4, theta + r0, rn * 4, cudaMemcpyHostToDevice, ctx->s_in);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(base + o_sg + r0 * 4, sigma + r0, rn * 4, cudaMemcpyHostToDevice, ctx->s_in);
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_in[b], ctx->s_in);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->s_band[b], ctx->ev_in[b], 0);
+        if (e == cudaSuccess) {
+            p.job.tile_y0 = t0;
+            e = launch_fused(prec, N, tm, p, dim3(p.job.tiles_x, t1 - t0), smem, ctx->s_band[b]);
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_k[b], ctx->s_band[b]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->s_out, ctx->ev_k[b], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(static_cast<uint8_t*>(out) + r0 * osz, d_out + r0 * osz, rn * osz,
+                                cudaMemcpyDeviceToHost, ctx->s_out);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_done, ctx->s_out);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ctx->ev_done, 0);
+    if (e != cudaSuccess) {
+        cudaStreamSynchronize(ctx->s_out);
+        return cuda_status(e);
+    }
+    int st = FABF_OK;
+    rc = read_and_clear_status(ctx, s, &st, nullptr, nullptr);
+    return rc ? rc : st;
+}
+
+// ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
 extern "C" {
@@ -255,6 +367,7 @@ int fabf_destroy(fabf_ctx* ctx)
     fabf::serve_destroy(ctx->serve);
     fabf::batch_destroy(ctx->batch);
     cudaDeviceSynchronize();
+    destroy_pipeline(ctx);
     if (ctx->stage) cudaFree(ctx->stage);
     cudaFree(ctx->d_status);
     cudaFree(ctx->d_nfb);
@@ -277,6 +390,8 @@ int fabf_filter(fabf_ctx* ctx, const uint8_t* img, const float* theta, const flo
     if (rc) return rc;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return FABF_ECUDA;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    if (!is_device_ptr(img) && !is_device_ptr(theta) && !is_device_ptr(sigma) && !is_device_ptr(out))
+        return filter_host_pipelined(ctx, img, theta, sigma, H, W, pitch, w, N, out, out_is_f64, s);
     return with_device_buffers(
         ctx, img, theta, sigma, H, W, pitch, out, out_is_f64, s,
         [&](const uint8_t* d_img, size_t d_pitch, const float* d_th, const float* d_sg, void* d_out) {

@@ -42,6 +42,12 @@ struct fabf_ctx {
     std::map<int, fabf::TuneEntry> tune;     // key: tune_key(w, N, precision)
     fabf::ServeState* serve = nullptr;
     fabf::BatchState* batch = nullptr;
+    // host-pointer pipeline (created on first use, under stage_lock): a copy-in
+    // stream, one compute stream per band, a copy-out stream and their events
+    static constexpr int kBands = 4;
+    bool pipe_ready = false;
+    cudaStream_t s_in = nullptr, s_out = nullptr, s_band[kBands] = {};
+    cudaEvent_t ev_start = nullptr, ev_in[kBands] = {}, ev_k[kBands] = {}, ev_done = nullptr;
 };
 
 namespace fabf {

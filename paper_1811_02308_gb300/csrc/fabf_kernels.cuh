@@ -86,6 +86,7 @@ struct ImageJob {
     int TH;                // output rows per tile (multiple of 8, <= 64)
     int tiles_x, tiles_y;
     long long tile_begin;  // index of this image's first tile in the launch
+    int tile_y0;           // single-image launches: tile row of blockIdx.y == 0 (a band of rows)
 };
 
 struct FusedParams {
@@ -680,7 +681,8 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<PREC>::value)
     extern __shared__ __align__(128) uint8_t smem[];
     uint32_t phase = 0;
     if (p.job.use_tma) mbar_init(reinterpret_cast<uint64_t*>(smem));
-    fabf_tile<N, PREC>(&tmap, p.job, blockIdx.x, blockIdx.y, smem, phase, p.status, p.n_fallback, p.dbg);
+    fabf_tile<N, PREC>(&tmap, p.job, blockIdx.x, blockIdx.y + p.job.tile_y0, smem, phase, p.status, p.n_fallback,
+                       p.dbg);
 }
 
 // ---------------------------------------------------------------------------

@@ -277,3 +277,51 @@ def test_concurrent_host_pointer_calls_on_one_context(ctx, oracle_mod):
     assert not errs
     for o, r in zip(outs, refs):
         assert g_close(o, r) <= RTOL_G
+
+
+@pytest.mark.parametrize("H,W,w,N", [(65535, 3, 2, 5), (3, 65535, 2, 5), (65535, 70, 40, 6)])
+def test_maximum_dimensions(ctx, oracle_mod, H, W, w, N):
+    # the largest height / width the ABI accepts (65535), every pixel computed,
+    # sampled pixels (and the four corners) checked against the oracle
+    f, th, s = inputs(H, W, 900 + W, n_blobs=10)
+    out = fabf.fabf_filter(ctx, dev(f), dev(th), dev(s), w, N)
+    st, _ = fabf.fabf_get_status(ctx)
+    assert st == fabf.FABF_OK
+    g = out.cpu().numpy()
+    rng = np.random.default_rng(H + W)
+    ys = np.concatenate([rng.integers(0, H, 1500), [0, 0, H - 1, H - 1]])
+    xs = np.concatenate([rng.integers(0, W, 1500), [0, W - 1, 0, W - 1]])
+    ref, _ = oracle_mod.fabf_pixels(f, th, s, w, N, ys, xs)
+    assert g_close(g[ys, xs], ref) <= RTOL_G
+    assert np.isfinite(g).all()
+
+
+def test_oversize_dimensions_rejected(ctx):
+    f = torch.zeros((2, 65536), dtype=torch.uint8, device="cuda")
+    th = torch.zeros((2, 65536), dtype=torch.float32, device="cuda")
+    _, rc = fabf.fabf_filter(ctx, f, th, th, 2, 3, check=False)
+    assert rc == fabf.FABF_EINVAL
+
+
+@pytest.mark.parametrize("H,W,w,N,f64,pitch_extra", [(1080, 1920, 20, 5, False, 0), (96, 160, 5, 5, True, 0),
+                                                     (17, 250, 3, 4, True, 5), (8, 64, 1, 2, False, 0),
+                                                     (301, 77, 40, 6, True, 3)])
+def test_pipelined_host_path_equals_device_path(ctx, H, W, w, N, f64, pitch_extra):
+    # host buffers go through the banded copy / compute / copy-back pipeline;
+    # the result must equal the device-pointer call bit for bit, in every form
+    f, th, s = inputs(H, W, 700 + H)
+    pitch = W + pitch_extra
+    buf = np.zeros((H, pitch), np.uint8)
+    buf[:, :W] = f
+    for prec in (fabf.FABF_FP64, fabf.FABF_CFP32):
+        if prec != fabf.FABF_FP64 and f64:
+            continue
+        fabf.fabf_set_precision(ctx, prec)
+        try:
+            host_out = np.zeros((H, W), np.float64 if f64 else np.float32)
+            fabf.fabf_filter(ctx, buf, th, s, w, N, out=host_out, out_is_f64=f64, pitch=pitch)
+            d = fabf.fabf_filter(ctx, dev(buf), dev(th), dev(s), w, N, out_is_f64=f64, pitch=pitch).cpu().numpy()
+            torch.cuda.synchronize()
+        finally:
+            fabf.fabf_set_precision(ctx, fabf.FABF_FP64)
+        assert np.array_equal(host_out, d), (prec, np.abs(host_out - d).max())
