@@ -463,3 +463,59 @@ def texture_filter(f, w, N, k, eps, msat, t_lo, t_hi, taps, Lq, s_lo, s_hi, sigm
     f3 = _next_input(g2)
     g3 = sharpen(f3, w, N, taps, Lq, s_lo, s_hi)
     return g3, [g1, g2]
+
+
+# ---------------------------------------------------------------------------
+# Colour (Sec. IV-C): channel by channel, width maps on the gray version
+# ---------------------------------------------------------------------------
+def luma(rgb):
+    """Gray version of an interleaved 8-bit colour image (H, W, 3): the
+    BT.601 luma 0.299 R + 0.587 G + 0.114 B rounded half up, computed in
+    integers as floor((299 R + 587 G + 114 B + 500) / 1000)."""
+    x = np.asarray(rgb).astype(np.int64)
+    return ((299 * x[..., 0] + 587 * x[..., 1] + 114 * x[..., 2] + 500) // 1000).astype(np.uint8)
+
+
+def _channel(rgb, c):
+    return np.ascontiguousarray(np.asarray(rgb)[..., c], dtype=np.uint8)
+
+
+def filter_rgb(rgb, theta, sigma, w, N):
+    """Algorithm 1 on each channel of a colour image (Sec. IV-C).  theta is
+    float32 (H, W, 3), or None for theta_c = f_c; sigma is one float32 (H, W)
+    map shared by the channels.  Returns float64 (H, W, 3)."""
+    H, W, _ = np.asarray(rgb).shape
+    out = np.empty((H, W, 3), np.float64)
+    for c in range(3):
+        f = _channel(rgb, c)
+        th = f.astype(np.float32) if theta is None else np.ascontiguousarray(np.asarray(theta)[..., c], np.float32)
+        out[..., c], _ = fabf(f, th, sigma, w, N)
+    return out
+
+
+def texture_filter_rgb(rgb, w, N, k, eps, msat, t_lo, t_hi, taps, Lq, s_lo, s_hi, sigma_decay=0.8,
+                       sw=None, sN=None):
+    """Texture filtering of a colour image (Sec. IV-C): the mRTV width map
+    of the luma; per channel the two smoothing passes (theta = f_c); the
+    sharpening width map of the luma of the rounded second outputs, shared by
+    the channels, with each channel's own sharpening centre.  sw, sN: the
+    sharpening pass's radius and degree (default w, N).  Returns float64
+    (H, W, 3)."""
+    sw = w if sw is None else sw
+    sN = N if sN is None else sN
+    H, W, _ = np.asarray(rgb).shape
+    s1 = texture_sigma(luma(rgb), k, eps, msat, t_lo, t_hi)
+    s2 = (s1 * np.float32(sigma_decay)).astype(np.float32)
+    f3 = np.empty((H, W, 3), np.uint8)
+    for c in range(3):
+        f = _channel(rgb, c)
+        g1, _ = fabf(f, f.astype(np.float32), s1, w, N)
+        f2 = _next_input(g1)
+        g2, _ = fabf(f2, f2.astype(np.float32), s2, w, N)
+        f3[..., c] = _next_input(g2)
+    s3 = sharpen_sigma(luma(f3), taps, Lq, s_lo, s_hi)
+    out = np.empty((H, W, 3), np.float64)
+    for c in range(3):
+        f = _channel(f3, c)
+        out[..., c], _ = fabf(f, sharpen_theta(f, sw), s3, sw, sN)
+    return out

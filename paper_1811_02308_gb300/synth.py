@@ -25,6 +25,11 @@ Recipe (all draws from ``numpy.random.default_rng(seed)``, in this order):
 * smooth fields (theta offset zeta, sigma): an 8x8 grid of ``U[lo, hi]``
   values upsampled bilinearly (corner-aligned) to H x W, float32.
 
+Colour images (``make_rgb``, interleaved H x W x 3) follow the same recipe
+with one geometry for the three channels: each blob draws its centre and
+width once and an amplitude per channel, each edge its line once and a
+height per channel (one sign), and the noise is independent per channel.
+
 The spatial kernel is an input too: ``gaussian_taps(rho)`` gives the integer
 taps of a Gaussian of width rho on the paper's window [-3 rho, 3 rho]
 (Eq. (4)), and ``random_taps`` draws arbitrary (asymmetric) taps for tests.
@@ -33,7 +38,7 @@ from __future__ import annotations
 
 import numpy as np
 
-__all__ = ["make_image", "smooth_field", "make_inputs", "config_seed", "gaussian_taps",
+__all__ = ["make_image", "make_rgb", "smooth_field", "make_inputs", "config_seed", "gaussian_taps",
            "random_taps"]
 
 
@@ -71,6 +76,38 @@ def make_image(H: int, W: int, n_blobs: int, rng: np.random.Generator,
         img += h * side
     img += rng.normal(0.0, noise_sigma, size=(H, W))
     return np.rint(np.clip(img, 0.0, 255.0)).astype(np.uint8)
+
+
+def make_rgb(H: int, W: int, seed: int, n_blobs: int = 20, noise_sigma: float = 10.0,
+             n_edges: int = 4) -> np.ndarray:
+    """Draw one H x W x 3 interleaved uint8 colour image, see module doc."""
+    rng = np.random.default_rng(seed)
+    img = np.full((H, W, 3), 64.0, dtype=np.float64)
+    scale = np.sqrt(H * W / max(n_blobs, 1))
+    for _ in range(n_blobs):
+        cy = rng.uniform(0.0, H)
+        cx = rng.uniform(0.0, W)
+        s = rng.uniform(0.1, 0.6) * scale
+        a = rng.uniform(0.0, 200.0, size=3)
+        r = int(np.ceil(6.0 * s))
+        y0, y1 = max(0, int(cy) - r), min(H, int(cy) + r + 1)
+        x0, x1 = max(0, int(cx) - r), min(W, int(cx) + r + 1)
+        if y0 >= y1 or x0 >= x1:
+            continue
+        dy = (np.arange(y0, y1, dtype=np.float64) - cy)[:, None]
+        dx = (np.arange(x0, x1, dtype=np.float64) - cx)[None, :]
+        img[y0:y1, x0:x1] += np.exp(-(dy * dy + dx * dx) / (2.0 * s * s))[:, :, None] * a
+    yy = np.arange(H, dtype=np.float64)[:, None]
+    xx = np.arange(W, dtype=np.float64)[None, :]
+    for _ in range(n_edges):
+        py = rng.uniform(0.0, H)
+        px = rng.uniform(0.0, W)
+        ang = rng.uniform(0.0, 2.0 * np.pi)
+        h = rng.uniform(60.0, 120.0, size=3) * (1.0 if rng.uniform() < 0.5 else -1.0)
+        side = ((xx - px) * np.cos(ang) + (yy - py) * np.sin(ang)) > 0.0
+        img += side[:, :, None] * h
+    img += rng.normal(0.0, noise_sigma, size=(H, W, 3))
+    return np.ascontiguousarray(np.rint(np.clip(img, 0.0, 255.0)).astype(np.uint8))
 
 
 def smooth_field(H: int, W: int, lo: float, hi: float,
