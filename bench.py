@@ -445,14 +445,19 @@ def run_apps(R, slots, steps, w=5, N=5):
     (maps + Algorithm 1) and the texture-filtering pipeline (mRTV map + two
     smoothing passes + one sharpening pass), in the FP64 and compensated
     binary32 forms; Mpix/s of whole pipelines (image pixels per second)."""
+    import torch
+
+    from paper_1811_02308_gb300 import synth
     fabf = R.fabf
     ctx = R.ctx
     npix = H_ * W_
+    rgb = torch.from_numpy(synth.make_rgb(H_, W_, 3000, N_BLOBS)).to(R.dev)
     sh = fabf.SharpenCfg(w, N, 1.0, 10.0, 10.0, 40.0)
     tx = fabf.TextureCfg(w, N, 2, 1.0, 8.0, 5.0, 60.0, 0.8, sh)
     out = {"workload": "1920x1080 as above; sharpening: w=%d, N=%d, LoG rho 1, |LoG| saturation 10, "
                        "sigma 10..40; texture: mRTV k=2, eps 1, saturation 8, sigma 5..60, decay 0.8, then "
-                       "the sharpening pass" % (w, N)}
+                       "the sharpening pass; colour texture: the same on an interleaved 1920x1080x3 "
+                       "image (maps from the luma, the passes per channel)" % (w, N)}
     for prec in (0, 2):
         fabf.fabf_set_precision(ctx, prec)
         o = slots[prec][0][3]
@@ -461,10 +466,16 @@ def run_apps(R, slots, steps, w=5, N=5):
                                                       out_is_f64=f64, stream=R.sh), steps, 3)
         ms_t, _ = R.timed(lambda i: fabf.fabf_texture_filter(ctx, slots[prec][i % len(slots[prec])][0], tx, out=o,
                                                              out_is_f64=f64, stream=R.sh), steps, 3)
+        o3 = torch.empty((H_, W_, 3), dtype=torch.float64 if f64 else torch.float32, device=R.dev)
+        ms_c, _ = R.timed(lambda i: fabf.fabf_texture_filter_rgb(ctx, rgb, tx, out=o3, out_is_f64=f64,
+                                                                 stream=R.sh), steps, 3)
         st, _ = fabf.fabf_get_status(ctx, R.sh)
         out[FORM_NAMES[prec]] = {"sharpen_mpix_per_s": npix * steps / (ms_s / 1e3) / 1e6,
                                  "texture_mpix_per_s": npix * steps / (ms_t / 1e3) / 1e6,
-                                 "texture_ms_per_frame": ms_t / steps, "status": st}
+                                 "texture_ms_per_frame": ms_t / steps,
+                                 "colour_texture_mpix_per_s": npix * steps / (ms_c / 1e3) / 1e6,
+                                 "colour_texture_ms_per_frame": ms_c / steps, "status": st}
+        del o3
     fabf.fabf_set_precision(ctx, 0)
     return out
 

@@ -291,6 +291,35 @@ int fabf_sharpen(fabf_ctx* ctx, const uint8_t* img, int H, int W, size_t pitch,
 int fabf_texture_filter(fabf_ctx* ctx, const uint8_t* img, int H, int W, size_t pitch,
                         const fabf_texture_cfg* cfg, void* out, int out_is_f64, void* cuda_stream);
 
+/* ---- colour images (Sec. IV-C: channel by channel) ----------------------- */
+/* rgb is an 8-bit interleaved H x W x 3 image (R, G, B) with a row pitch in
+ * bytes >= 3 W.  The paper computes the width maps of its colour examples on
+ * a gray version of the image; that version is read as the BT.601 luma
+ * rounded half up, in integers:  Y = floor((299 R + 587 G + 114 B + 500) /
+ * 1000).  Outputs are interleaved H x W x 3 (float32, or float64 when
+ * out_is_f64), row stride 3 W.  Device pointers only; stream-ordered
+ * (intermediates are stream-ordered allocations); data errors through
+ * fabf_get_status.  Errors: FABF_EINVAL (NULL or host pointers, H, W
+ * outside 1..65535, pitch < 3 W, bad parameters), FABF_EUNSUPPORTED,
+ * FABF_ENOMEM, FABF_ECUDA. */
+
+/* The luma Y of rgb (uint8 H x W, row pitch y_pitch >= W). */
+int fabf_luma(fabf_ctx* ctx, const uint8_t* rgb, int H, int W, size_t pitch, uint8_t* Y, size_t y_pitch,
+              void* cuda_stream);
+
+/* Algorithm 1 on each channel in the context's precision: theta is an
+ * interleaved float32 H x W x 3 map (NULL: theta_c = f_c, the classical
+ * filter), sigma one float32 H x W map shared by the channels. */
+int fabf_filter_rgb(fabf_ctx* ctx, const uint8_t* rgb, const float* theta, const float* sigma, int H, int W,
+                    size_t pitch, int w, int N, void* out, int out_is_f64, void* cuda_stream);
+
+/* The texture-filtering pipeline on a colour image: the mRTV width map of
+ * the luma; per channel the two smoothing passes (theta = f_c); then the
+ * sharpening width map of the luma of the rounded second outputs, shared by
+ * the channels, and each channel's own sharpening centre (cfg.sharpen). */
+int fabf_texture_filter_rgb(fabf_ctx* ctx, const uint8_t* rgb, int H, int W, size_t pitch,
+                            const fabf_texture_cfg* cfg, void* out, int out_is_f64, void* cuda_stream);
+
 /* ---- host-side helpers (no GPU needed) ---------------------------------- */
 
 /* The exact inverse of the (N+1) x (N+1) Hilbert matrix of Eq. (18), by the

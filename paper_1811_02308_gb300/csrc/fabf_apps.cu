@@ -2,7 +2,8 @@
 // (Sec. IV-A), the texture width map from mRTV (Sec. IV-C), and the two
 // pipelines built on Algorithm 1 -- one sharpening pass, and texture
 // filtering (two smoothing passes, the second with the width scaled by
-// sigma_decay, then one sharpening pass).
+// sigma_decay, then one sharpening pass); and colour images channel by
+// channel (Sec. IV-C), with the width maps taken from the luma.
 //
 // The maps follow the readings the CPU oracle states (integer-exact up to one
 // fixed sequence of binary64 operations, rounded to binary32), written with
@@ -159,6 +160,64 @@ __global__ void next_input_kernel(const void* g, int g_f64, int H, int W, uint8_
     if (sig_out) sig_out[i] = __fmul_rn(sig_in[i], decay);
 }
 
+// Colour images (Sec. IV-C) are filtered channel by channel; the width maps
+// come from the gray version, read as the BT.601 luma rounded half up in
+// integers: Y = floor((299 R + 587 G + 114 B + 500) / 1000).
+__device__ __forceinline__ uint8_t luma_of(unsigned r, unsigned g, unsigned b)
+{
+    return (uint8_t)((299u * r + 587u * g + 114u * b + 500u) / 1000u);
+}
+
+// Interleaved rgb (row pitch in bytes) into three planes (row pitch pn,
+// plane c at planes + c * plane_stride) and/or its luma Y (row pitch pn).
+__global__ void rgb_split_kernel(const uint8_t* rgb, long long pitch, int H, int W, uint8_t* planes, long long pn,
+                                 long long plane_stride, uint8_t* Y)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)H * W) return;
+    const int y = (int)(i / W), x = (int)(i - (long long)y * W);
+    const uint8_t* px = rgb + (long long)y * pitch + 3LL * x;
+    const unsigned r = px[0], g = px[1], b = px[2];
+    const long long o = (long long)y * pn + x;
+    if (planes) {
+        planes[o] = (uint8_t)r;
+        planes[o + plane_stride] = (uint8_t)g;
+        planes[o + 2 * plane_stride] = (uint8_t)b;
+    }
+    if (Y) Y[o] = luma_of(r, g, b);
+}
+
+// The luma of three planes (row pitch pn) into Y (row pitch pn).
+__global__ void planes_luma_kernel(const uint8_t* planes, long long pn, long long plane_stride, int H, int W,
+                                   uint8_t* Y)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)H * W) return;
+    const int y = (int)(i / W), x = (int)(i - (long long)y * W);
+    const long long o = (long long)y * pn + x;
+    Y[o] = luma_of(planes[o], planes[o + plane_stride], planes[o + 2 * plane_stride]);
+}
+
+// Channel c of an interleaved H x W x 3 float map into a plane.
+__global__ void channel_kernel(const float* x3, int H, int W, int c, float* out)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)H * W) return;
+    out[i] = x3[3 * i + c];
+}
+
+// Three output planes (H x W each, plane c at g + c * plane_elems elements)
+// into the interleaved H x W x 3 output.
+template <typename T>
+__global__ void interleave_kernel(const T* g, long long plane_elems, long long n, T* out)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    out[3 * i] = g[i];
+    out[3 * i + 1] = g[i + plane_elems];
+    out[3 * i + 2] = g[i + 2 * plane_elems];
+}
+
 unsigned blocks_for(long long n) { return (unsigned)((n + kAppThreads - 1) / kAppThreads); }
 
 int check_sharpen_cfg(const fabf_sharpen_cfg* c)
@@ -233,6 +292,25 @@ int launch_sharpen_maps(const uint8_t* f, long long pitch, int H, int W, int w, 
 }
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// Interleaves three planes of out_f64 ? double : float elements.
+int launch_interleave(const void* g, size_t plane_bytes, int out_f64, long long n, void* out, cudaStream_t s)
+{
+    if (out_f64)
+        interleave_kernel<double><<<blocks_for(n), kAppThreads, 0, s>>>(
+            static_cast<const double*>(g), (long long)(plane_bytes / 8), n, static_cast<double*>(out));
+    else
+        interleave_kernel<float><<<blocks_for(n), kAppThreads, 0, s>>>(
+            static_cast<const float*>(g), (long long)(plane_bytes / 4), n, static_cast<float*>(out));
+    return cuda_status(cudaGetLastError());
+}
+
+int check_rgb_args(const uint8_t* rgb, const void* out, int H, int W, size_t pitch)
+{
+    if (!rgb || !out || H < 1 || W < 1 || H > 65535 || W > 65535) return FABF_EINVAL;
+    if (pitch < 3 * (size_t)W) return FABF_EINVAL;
+    return FABF_OK;
+}
 
 }  // namespace
 }  // namespace fabf
@@ -366,6 +444,149 @@ int fabf_texture_filter(fabf_ctx* ctx, const uint8_t* img, int H, int W, size_t 
                              reinterpret_cast<int64_t*>(b + o_S), th, s2, s);
     if (rc) return rc;
     return run_fused(ctx, f3, pn, th, s2, H, W, sc_cfg.w, sc_cfg.N, out, out_is_f64, nullptr, s);
+}
+
+}  // extern "C"
+
+extern "C" {
+
+int fabf_luma(fabf_ctx* ctx, const uint8_t* rgb, int H, int W, size_t pitch, uint8_t* Y, size_t y_pitch,
+              void* cuda_stream)
+{
+    if (!ctx || !Y || y_pitch < (size_t)W) return FABF_EINVAL;
+    int rc = check_rgb_args(rgb, Y, H, W, pitch);
+    if (rc) return rc;
+    if (!all_device({rgb, Y})) return FABF_EINVAL;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return FABF_ECUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    rgb_split_kernel<<<blocks_for((long long)H * W), kAppThreads, 0, s>>>(rgb, (long long)pitch, H, W, nullptr,
+                                                                          (long long)y_pitch, 0, Y);
+    return cuda_status(cudaGetLastError());
+}
+
+int fabf_filter_rgb(fabf_ctx* ctx, const uint8_t* rgb, const float* theta, const float* sigma, int H, int W,
+                    size_t pitch, int w, int N, void* out, int out_is_f64, void* cuda_stream)
+{
+    if (!ctx || !sigma) return FABF_EINVAL;
+    int rc = check_rgb_args(rgb, out, H, W, pitch);
+    if (rc) return rc;
+    if (w < 1 || N < 0) return FABF_EINVAL;
+    if (w > kWMax || N > kNMax) return FABF_EUNSUPPORTED;
+    if (!all_device({rgb, sigma, out}) || (theta && !is_device_ptr(theta))) return FABF_EINVAL;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return FABF_ECUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    const long long n = (long long)H * W;
+    const size_t pn = ((size_t)W + 15) & ~(size_t)15;          // 16-byte rows for the TMA loads
+    const size_t plane = align256(pn * H), gplane = align256((size_t)n * (out_is_f64 ? 8 : 4));
+    // scratch: the three channel planes, one theta plane, three output planes
+    const size_t o_th = 3 * plane, o_g = o_th + align256((size_t)n * 4), total = o_g + 3 * gplane;
+    Scratch sc;
+    sc.s = s;
+    cudaError_t e = cudaMallocAsync(&sc.base, total, s);
+    if (e != cudaSuccess) return cuda_status(e);
+    uint8_t* b = static_cast<uint8_t*>(sc.base);
+    float* th = reinterpret_cast<float*>(b + o_th);
+    const unsigned nb = blocks_for(n);
+    rgb_split_kernel<<<nb, kAppThreads, 0, s>>>(rgb, (long long)pitch, H, W, b, (long long)pn, (long long)plane,
+                                                nullptr);
+    for (int c = 0; c < 3; ++c) {
+        const uint8_t* f = b + c * plane;
+        if (theta)
+            channel_kernel<<<nb, kAppThreads, 0, s>>>(theta, H, W, c, th);
+        else
+            u8_to_float_kernel<<<nb, kAppThreads, 0, s>>>(f, (long long)pn, H, W, th);
+        rc = cuda_status(cudaGetLastError());
+        if (rc) return rc;
+        rc = run_fused(ctx, f, pn, th, sigma, H, W, w, N, b + o_g + c * gplane, out_is_f64, nullptr, s);
+        if (rc) return rc;
+    }
+    return launch_interleave(b + o_g, gplane, out_is_f64, n, out, s);
+}
+
+int fabf_texture_filter_rgb(fabf_ctx* ctx, const uint8_t* rgb, int H, int W, size_t pitch,
+                            const fabf_texture_cfg* cfg, void* out, int out_is_f64, void* cuda_stream)
+{
+    if (!ctx) return FABF_EINVAL;
+    int rc = check_rgb_args(rgb, out, H, W, pitch);
+    if (rc) return rc;
+    rc = check_texture_cfg(cfg);
+    if (rc) return rc;
+    if (!all_device({rgb, out})) return FABF_EINVAL;
+    const fabf_sharpen_cfg& shc = cfg->sharpen;
+    SepTaps T;
+    long long Lq = 0;
+    rc = sharpen_taps(&shc, &T, &Lq);
+    if (rc) return rc;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return FABF_ECUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    const long long n = (long long)H * W;
+    const size_t pn = ((size_t)W + 15) & ~(size_t)15;
+    const size_t plane = align256(pn * H), f4 = align256((size_t)n * 4);
+    const int g_f64 = ctx->precision == kPrecFP64 ? 1 : 0;
+    const size_t gmid = align256((size_t)n * (g_f64 ? 8 : 4)), gplane = align256((size_t)n * (out_is_f64 ? 8 : 4));
+    // scratch: input planes (3), luma, pass-2 input, pass-3 inputs (3), sigma1, sigma2, theta, the
+    // intermediate output, the final output planes (3), and the sharpening maps' row sums and Gaussians
+    const size_t o_Y = 3 * plane, o_F2 = o_Y + plane, o_F3 = o_F2 + plane, o_s1 = o_F3 + 3 * plane,
+                 o_s2 = o_s1 + f4, o_th = o_s2 + f4, o_gm = o_th + f4, o_go = o_gm + gmid, o_rs = o_go + 3 * gplane,
+                 o_gr = o_rs + f4, o_S = o_gr + f4, total = o_S + (size_t)n * 8;
+    Scratch sc;
+    sc.s = s;
+    cudaError_t e = cudaMallocAsync(&sc.base, total, s);
+    if (e != cudaSuccess) return cuda_status(e);
+    uint8_t* b = static_cast<uint8_t*>(sc.base);
+    uint8_t* Y = b + o_Y;
+    uint8_t* F2 = b + o_F2;
+    uint8_t* F3 = b + o_F3;
+    float* s1 = reinterpret_cast<float*>(b + o_s1);
+    float* s2 = reinterpret_cast<float*>(b + o_s2);
+    float* th = reinterpret_cast<float*>(b + o_th);
+    void* gm = b + o_gm;
+    const unsigned nb = blocks_for(n);
+    const long long lpn = (long long)pn;
+    // the planes, and the texture width map of the luma
+    rgb_split_kernel<<<nb, kAppThreads, 0, s>>>(rgb, (long long)pitch, H, W, b, lpn, (long long)plane, Y);
+    texture_sigma_kernel<<<nb, kAppThreads, 0, s>>>(Y, lpn, H, W, cfg->k, cfg->eps, cfg->mrtv_sat, cfg->sigma_lo,
+                                                    cfg->sigma_hi, s1);
+    rc = cuda_status(cudaGetLastError());
+    if (rc) return rc;
+    // per channel: the two smoothing passes (theta = f), rounded into F3
+    for (int c = 0; c < 3; ++c) {
+        const uint8_t* f = b + c * plane;
+        u8_to_float_kernel<<<nb, kAppThreads, 0, s>>>(f, lpn, H, W, th);
+        rc = cuda_status(cudaGetLastError());
+        if (rc) return rc;
+        rc = run_fused(ctx, f, pn, th, s1, H, W, cfg->w, cfg->N, gm, g_f64, nullptr, s);
+        if (rc) return rc;
+        next_input_kernel<<<nb, kAppThreads, 0, s>>>(gm, g_f64, H, W, F2, lpn, th, c == 0 ? s1 : nullptr,
+                                                     c == 0 ? s2 : nullptr, (float)cfg->sigma_decay);
+        rc = cuda_status(cudaGetLastError());
+        if (rc) return rc;
+        rc = run_fused(ctx, F2, pn, th, s2, H, W, cfg->w, cfg->N, gm, g_f64, nullptr, s);
+        if (rc) return rc;
+        next_input_kernel<<<nb, kAppThreads, 0, s>>>(gm, g_f64, H, W, F3 + c * plane, lpn, nullptr, nullptr,
+                                                     nullptr, 1.0f);
+    }
+    // the sharpening width map of the luma of F3 (into s1), shared by the channels
+    int32_t* rs = reinterpret_cast<int32_t*>(b + o_rs);
+    planes_luma_kernel<<<nb, kAppThreads, 0, s>>>(F3, lpn, (long long)plane, H, W, Y);
+    gauss_rows_kernel<<<nb, kAppThreads, 0, s>>>(Y, lpn, H, W, T, reinterpret_cast<uint32_t*>(b + o_gr));
+    gauss_cols_kernel<<<nb, kAppThreads, 0, s>>>(reinterpret_cast<uint32_t*>(b + o_gr), H, W, T,
+                                                 reinterpret_cast<int64_t*>(b + o_S));
+    sharpen_sigma_kernel<<<nb, kAppThreads, 0, s>>>(reinterpret_cast<int64_t*>(b + o_S), H, W, Lq, shc.sigma_lo,
+                                                    shc.sigma_hi, s1);
+    rc = cuda_status(cudaGetLastError());
+    if (rc) return rc;
+    // per channel: its own sharpening centre, then the sharpening pass
+    for (int c = 0; c < 3; ++c) {
+        const uint8_t* f = F3 + c * plane;
+        box_rows_kernel<<<nb, kAppThreads, 0, s>>>(f, lpn, H, W, shc.w, rs);
+        sharpen_theta_kernel<<<nb, kAppThreads, 0, s>>>(f, lpn, rs, H, W, shc.w, th);
+        rc = cuda_status(cudaGetLastError());
+        if (rc) return rc;
+        rc = run_fused(ctx, f, pn, th, s1, H, W, shc.w, shc.N, b + o_go + c * gplane, out_is_f64, nullptr, s);
+        if (rc) return rc;
+    }
+    return launch_interleave(b + o_go, gplane, out_is_f64, n, out, s);
 }
 
 }  // extern "C"

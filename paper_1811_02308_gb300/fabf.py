@@ -106,6 +106,9 @@ def load(path: str | None = None):
         "fabf_texture_sigma": ([vp, vp, i, i, sz, C.POINTER(TextureCfg), vp, vp], i),
         "fabf_sharpen": ([vp, vp, i, i, sz, C.POINTER(SharpenCfg), vp, i, vp], i),
         "fabf_texture_filter": ([vp, vp, i, i, sz, C.POINTER(TextureCfg), vp, i, vp], i),
+        "fabf_luma": ([vp, vp, i, i, sz, vp, sz, vp], i),
+        "fabf_filter_rgb": ([vp, vp, vp, vp, i, i, sz, i, i, vp, i, vp], i),
+        "fabf_texture_filter_rgb": ([vp, vp, i, i, sz, C.POINTER(TextureCfg), vp, i, vp], i),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -554,4 +557,66 @@ def fabf_texture_filter(ctx: Context, img, cfg: TextureCfg, out=None, out_is_f64
     s = _stream_of(img, out) if stream is None else stream
     _check(load().fabf_texture_filter(ctx.handle, _ptr(img), H, W, p, C.byref(cfg), _ptr(out),
                                       1 if out_is_f64 else 0, s), "fabf_texture_filter")
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Colour images (Sec. IV-C): interleaved (H, W, 3) uint8 device tensors
+# ---------------------------------------------------------------------------
+def _rgb_dims(rgb):
+    import torch
+    if len(rgb.shape) != 3 or int(rgb.shape[2]) != 3 or rgb.dtype != torch.uint8:
+        raise ValueError("rgb must be a uint8 tensor of shape (H, W, 3)")
+    if not rgb.is_contiguous():
+        raise ValueError("rgb must be contiguous")
+    H, W = int(rgb.shape[0]), int(rgb.shape[1])
+    return H, W, 3 * W
+
+
+def _rgb_out(rgb, out, out_is_f64):
+    import torch
+    H, W, _ = _rgb_dims(rgb)
+    dt = torch.float64 if out_is_f64 else torch.float32
+    if out is None:
+        return torch.empty((H, W, 3), dtype=dt, device=rgb.device)
+    if tuple(out.shape) != (H, W, 3) or out.dtype != dt or not out.is_contiguous():
+        raise ValueError("out must be a contiguous (H, W, 3) %s tensor" % dt)
+    return out
+
+
+def fabf_luma(ctx: Context, rgb, stream=None):
+    """The integer BT.601 luma of an interleaved colour image (uint8 H x W)."""
+    import torch
+    H, W, p = _rgb_dims(rgb)
+    Y = torch.empty((H, W), dtype=torch.uint8, device=rgb.device)
+    s = _stream_of(rgb) if stream is None else stream
+    _check(load().fabf_luma(ctx.handle, _ptr(rgb), H, W, p, _ptr(Y), W, s), "fabf_luma")
+    return Y
+
+
+def fabf_filter_rgb(ctx: Context, rgb, theta, sigma, w: int, N: int, out=None, out_is_f64: bool = True,
+                    stream=None):
+    """Algorithm 1 on each channel of an interleaved colour image; theta is
+    (H, W, 3) float32 or None (theta_c = f_c), sigma one (H, W) float32 map."""
+    H, W, p = _rgb_dims(rgb)
+    import torch
+    if tuple(sigma.shape) != (H, W) or sigma.dtype != torch.float32 or not sigma.is_contiguous():
+        raise ValueError("sigma must be a contiguous (H, W) float32 tensor")
+    if theta is not None and (tuple(theta.shape) != (H, W, 3) or theta.dtype != torch.float32
+                              or not theta.is_contiguous()):
+        raise ValueError("theta must be a contiguous (H, W, 3) float32 tensor")
+    out = _rgb_out(rgb, out, out_is_f64)
+    s = _stream_of(rgb, out) if stream is None else stream
+    _check(load().fabf_filter_rgb(ctx.handle, _ptr(rgb), _ptr(theta), _ptr(sigma), H, W,
+                                  p, w, N, _ptr(out), 1 if out_is_f64 else 0, s), "fabf_filter_rgb")
+    return out
+
+
+def fabf_texture_filter_rgb(ctx: Context, rgb, cfg: TextureCfg, out=None, out_is_f64: bool = True, stream=None):
+    """The texture-filtering pipeline (Sec. IV-C) on an interleaved colour image."""
+    H, W, p = _rgb_dims(rgb)
+    out = _rgb_out(rgb, out, out_is_f64)
+    s = _stream_of(rgb, out) if stream is None else stream
+    _check(load().fabf_texture_filter_rgb(ctx.handle, _ptr(rgb), H, W, p, C.byref(cfg), _ptr(out),
+                                          1 if out_is_f64 else 0, s), "fabf_texture_filter_rgb")
     return out
