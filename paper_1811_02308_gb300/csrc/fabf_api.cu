@@ -159,14 +159,17 @@ int ensure_stage(fabf_ctx* ctx, size_t bytes)
 
 int read_and_clear_status(fabf_ctx* ctx, cudaStream_t s, int* status, uint64_t* nfb, uint64_t* nredo)
 {
-    unsigned st = 0;
-    unsigned long long n[2] = {0, 0};
-    cudaError_t e = cudaMemcpyAsync(&st, ctx->d_status, sizeof(st), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(n, ctx->d_nfb, sizeof(n), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_status, 0, sizeof(unsigned), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_nfb, 0, sizeof(n), s);
+    // one copy of the whole word block into pinned memory, one clear, one wait
+    std::lock_guard<std::mutex> lk(ctx->status_lock);
+    const uint8_t* hw = static_cast<const uint8_t*>(ctx->h_words);
+    cudaError_t e = cudaMemcpyAsync(ctx->h_words, ctx->d_status, fabf_ctx::kWordBytes, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_status, 0, fabf_ctx::kWordBytes, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_status(e);
+    unsigned st;
+    unsigned long long n[2];
+    std::memcpy(&st, hw, sizeof(st));
+    std::memcpy(n, hw + fabf_ctx::kNfbOffset, sizeof(n));
     if (status) *status = (st & kStatusTimeout) ? FABF_ETIMEOUT : (st & kStatusBadInput) ? FABF_EINVAL : FABF_OK;
     if (nfb) *nfb = n[0];
     if (nredo) *nredo = n[1];
@@ -345,17 +348,19 @@ int fabf_create(const fabf_config* cfg, fabf_ctx** out)
     if (c.tune_cache_path) ctx->tune_cache_path = c.tune_cache_path;
     cudaError_t e = cudaSetDevice(c.device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, c.device);
-    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_status, 256);
-    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_nfb, 256);
-    if (e == cudaSuccess) e = cudaMemset(ctx->d_status, 0, 256);
-    if (e == cudaSuccess) e = cudaMemset(ctx->d_nfb, 0, 256);
+    void* words = nullptr;
+    if (e == cudaSuccess) e = cudaMalloc(&words, fabf_ctx::kWordBytes);
+    if (e == cudaSuccess) e = cudaMemset(words, 0, fabf_ctx::kWordBytes);
+    if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_words, fabf_ctx::kWordBytes);
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
-        if (ctx->d_status) cudaFree(ctx->d_status);
-        if (ctx->d_nfb) cudaFree(ctx->d_nfb);
+        if (words) cudaFree(words);
+        if (ctx->h_words) cudaFreeHost(ctx->h_words);
         delete ctx;
         return cuda_status(e);
     }
+    ctx->d_status = static_cast<unsigned*>(words);
+    ctx->d_nfb = reinterpret_cast<unsigned long long*>(static_cast<uint8_t*>(words) + fabf_ctx::kNfbOffset);
     *out = ctx;
     return FABF_OK;
 }
@@ -369,8 +374,8 @@ int fabf_destroy(fabf_ctx* ctx)
     cudaDeviceSynchronize();
     destroy_pipeline(ctx);
     if (ctx->stage) cudaFree(ctx->stage);
-    cudaFree(ctx->d_status);
-    cudaFree(ctx->d_nfb);
+    cudaFree(ctx->d_status);                 // the block holding d_nfb too
+    cudaFreeHost(ctx->h_words);
     delete ctx;
     return FABF_OK;
 }

@@ -33,8 +33,14 @@ struct fabf_ctx {
     int autotune = 0;
     std::string tune_cache_path;
     int num_sms = 0;
-    unsigned* d_status = nullptr;            // status bits of stream-ordered calls
-    unsigned long long* d_nfb = nullptr;     // fallback pixel count
+    // status words of stream-ordered calls, one device block: the status bits
+    // at offset 0, the fallback and FP64 redo counts at kNfbOffset; read back
+    // through a pinned copy (h_words, under status_lock)
+    static constexpr size_t kNfbOffset = 256, kWordBytes = kNfbOffset + 16;
+    unsigned* d_status = nullptr;
+    unsigned long long* d_nfb = nullptr;
+    void* h_words = nullptr;
+    std::mutex status_lock;
     void* stage = nullptr;                   // grow-only staging buffer for host pointers
     size_t stage_bytes = 0;
     std::mutex stage_lock;                   // one host-pointer call at a time uses the staging buffer
