@@ -111,8 +111,12 @@ int fabf_set_precision(fabf_ctx* ctx, int precision);
  * (NULL = legacy default stream).  If img, theta, sigma and out are all
  * device pointers the work is only enqueued on the stream (stream-ordered,
  * the call returns at once; per-pixel data errors are read later with
- * fabf_get_status).  If any of them is a host pointer, the call stages the
- * host buffers through device memory and returns after out is written.
+ * fabf_get_status).  If any of them is a host pointer, the call returns
+ * after out is written.  When theta, sigma and out are pinned (page-locked)
+ * host memory, the kernel reads the maps and writes out in place over the
+ * chip-to-chip link and only a host image is copied to the device; other
+ * host buffers are staged through device memory (copies, kernels and copies
+ * back overlapping in bands of rows).
  * Errors: FABF_EINVAL, FABF_EUNSUPPORTED, FABF_ENOMEM, FABF_ECUDA,
  * FABF_ETIMEOUT (a tile copy into shared memory did not complete). */
 int fabf_filter(fabf_ctx* ctx, const uint8_t* img, const float* theta, const float* sigma,

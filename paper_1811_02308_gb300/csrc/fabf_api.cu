@@ -43,6 +43,22 @@ bool is_device_ptr(const void* p)
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// A pointer kernels can dereference: device or managed memory as is, pinned
+// host memory through its mapping (read and written in place over the
+// chip-to-chip link); nullptr for pageable host memory.
+const void* kernel_ptr(const void* p)
+{
+    if (!p) return nullptr;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return p;
+    if (a.type == cudaMemoryTypeHost && a.devicePointer) return a.devicePointer;
+    return nullptr;
+}
+
 int check_filter_args(const void* img, const void* theta, const void* sigma, const void* out,
                       int H, int W, size_t pitch, int w, int N)
 {
@@ -328,6 +344,38 @@ static int filter_host_pipelined(fabf_ctx* ctx, const uint8_t* img, const float*
 }
 
 // ---------------------------------------------------------------------------
+// Host-mapped theta, sigma and out (pinned host memory) with a host or device
+// image: the kernel reads the maps and writes the output in place in host
+// memory, so only the image is copied (its tiles are staged by TMA from
+// device memory).  Synchronous: returns the kernels' status.
+// ---------------------------------------------------------------------------
+static int filter_mapped(fabf_ctx* ctx, const uint8_t* img, const float* k_th, const float* k_sg, int H, int W,
+                         size_t pitch, int w, int N, void* k_out, int out_f64, cudaStream_t s)
+{
+    std::lock_guard<std::mutex> staged(ctx->stage_lock);
+    const uint8_t* d_img = img;
+    size_t d_pitch = pitch;
+    if (!is_device_ptr(img)) {
+        const size_t ipitch = ((size_t)W + 15) & ~(size_t)15;
+        int rc = ensure_stage(ctx, ipitch * H);
+        if (rc) return rc;
+        const cudaError_t e =
+            cudaMemcpy2DAsync(ctx->stage, ipitch, img, pitch, W, H, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return cuda_status(e);
+        d_img = static_cast<const uint8_t*>(ctx->stage);
+        d_pitch = ipitch;
+    }
+    int rc = run_fused(ctx, d_img, d_pitch, k_th, k_sg, H, W, w, N, k_out, out_f64, nullptr, s);
+    if (rc) {
+        cudaStreamSynchronize(s);
+        return rc;
+    }
+    int st = FABF_OK;
+    rc = read_and_clear_status(ctx, s, &st, nullptr, nullptr);
+    return rc ? rc : st;
+}
+
+// ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
 extern "C" {
@@ -395,7 +443,18 @@ int fabf_filter(fabf_ctx* ctx, const uint8_t* img, const float* theta, const flo
     if (rc) return rc;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return FABF_ECUDA;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-    if (!is_device_ptr(img) && !is_device_ptr(theta) && !is_device_ptr(sigma) && !is_device_ptr(out))
+    const bool di = is_device_ptr(img), dt = is_device_ptr(theta), ds = is_device_ptr(sigma),
+               dout = is_device_ptr(out);
+    if (!(dt && ds && dout)) {
+        // pinned host maps and output: read and written in place by the kernel
+        const void* kt = kernel_ptr(theta);
+        const void* ks = kernel_ptr(sigma);
+        void* ko = const_cast<void*>(kernel_ptr(out));
+        if (kt && ks && ko)
+            return filter_mapped(ctx, img, static_cast<const float*>(kt), static_cast<const float*>(ks), H, W,
+                                 pitch, w, N, ko, out_is_f64, s);
+    }
+    if (!di && !dt && !ds && !dout)
         return filter_host_pipelined(ctx, img, theta, sigma, H, W, pitch, w, N, out, out_is_f64, s);
     return with_device_buffers(
         ctx, img, theta, sigma, H, W, pitch, out, out_is_f64, s,

@@ -51,6 +51,9 @@ constexpr unsigned kTmaWaitLimit = 1u << 22;   // bounded mbarrier wait (polls)
 // and one 16-bit (row, column) entry per pixel of the chunk.
 constexpr size_t kRedoBytes = 16 + 2 * kChunk * kTileW;
 
+// The chunk's centres and widths (theta, sigma), prefetched into shared memory.
+constexpr size_t kMapBytes = 2 * kChunk * kTileW * sizeof(float);
+
 // Lane-block extrema table of one row: levels k = 0..4 x 32 lanes (bytes).
 constexpr int kLaneTable = 5 * 32;
 
@@ -116,7 +119,7 @@ __host__ __device__ inline size_t fused_smem_bytes(int N, int w, int Cb, int TH)
     const int n32 = K < 2 ? K : 2;
     const int n64 = K > 2 ? K - 2 : 0;
     size_t v = (size_t)kChunk * Cb * (4 + 4 * n32) + (size_t)2 * kChunk * kLaneTable + (size_t)kChunk * Cb * 8 * n64;
-    return 128 + tile + ((v + 15) & ~(size_t)15) + kRedoBytes;
+    return 128 + tile + ((v + 15) & ~(size_t)15) + kRedoBytes + kMapBytes;
 }
 
 // Raise a kernel's dynamic shared-memory limit once per device and kernel
@@ -144,6 +147,18 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p)
 // ---------------------------------------------------------------------------
 // Tile staging.
 // ---------------------------------------------------------------------------
+// Asynchronous 4-byte copy global -> shared (no register holds the value in
+// flight); commit closes the group, wait_all waits for this thread's groups.
+__device__ __forceinline__ void cp_async4(void* sdst, const void* gsrc)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 __device__ __forceinline__ void mbar_init(uint64_t* bar)
 {
     if (threadIdx.x == 0) {
@@ -388,6 +403,7 @@ __device__ __forceinline__ bool fabf_tile(const CUtensorMap* tmap, const ImageJo
                            (size_t)kChunk * Cb * 8 * n64;
     unsigned* redo_n = reinterpret_cast<unsigned*>(vmin + ((v_bytes + 15) & ~(size_t)15));
     uint16_t* redo_list = reinterpret_cast<uint16_t*>(reinterpret_cast<uint8_t*>(redo_n) + 16);
+    float* s_maps = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(redo_n) + kRedoBytes);   // [2][kChunk][kTileW]
 
     // 1. Stage tile + halo.
     if (J.use_tma) {
@@ -426,6 +442,17 @@ __device__ __forceinline__ bool fabf_tile(const CUtensorMap* tmap, const ImageJo
         if (y0 + r0 >= J.H) break;                                 // uniform per CTA
         // 2. Vertical phase for output rows r0 .. r0+7.
         if (threadIdx.x == 0) *redo_n = 0u;
+        // The chunk's theta and sigma start on their way into shared memory;
+        // the vertical phase covers their latency (HBM, or host memory over
+        // the chip-to-chip link when the caller's buffers are host-mapped).
+        for (int i = threadIdx.x; i < 2 * kChunk * kTileW; i += kThreads) {
+            const int which = i >= kChunk * kTileW ? 1 : 0;
+            const int e = i - which * kChunk * kTileW;
+            const int rr = e / kTileW, x = e - rr * kTileW;
+            const int Y = y0 + r0 + rr, Xo = x0 + x;
+            if (Y < J.H && Xo < J.W) cp_async4(s_maps + i, (which ? J.sigma : J.theta) + (long long)Y * J.W + Xo);
+        }
+        cp_async_commit();
         // 2a. Window sums of column c (threads c < Cb): store, then slide the
         //     window from [r, r+2w] to [r+1, r+2w+1].
         if (c < Cb) {
@@ -527,6 +554,7 @@ __device__ __forceinline__ bool fabf_tile(const CUtensorMap* tmap, const ImageJo
                 }
             }
         }
+        cp_async_wait_all();
         __syncthreads();
 
         // 3. Horizontal phase: warp `warp` owns chunk row `warp`.
@@ -589,7 +617,7 @@ __device__ __forceinline__ bool fabf_tile(const CUtensorMap* tmap, const ImageJo
                     int64_t m[K + 1];
                     stats(rr, x, alpha, beta, m, fi);
                     const long long pix = (long long)Y * J.W + Xo;
-                    const float th = J.theta[pix], sg = J.sigma[pix];
+                    const float th = s_maps[rr * kTileW + x], sg = s_maps[(kChunk + rr) * kTileW + x];
                     double g;
                     int fb = 0;
                     PixelTrace tr;
@@ -650,8 +678,8 @@ __device__ __forceinline__ bool fabf_tile(const CUtensorMap* tmap, const ImageJo
                 int64_t m[K + 1];
                 stats(rr, x, alpha, beta, m, fi);
                 const long long pix = (long long)(y0 + r0 + rr) * J.W + (x0 + x);
-                const double g = fabf_pixel_fp64<N>(c_ainv, alpha, beta, fi, m, J.theta[pix], J.sigma[pix], fb,
-                                                    nullptr);
+                const double g = fabf_pixel_fp64<N>(c_ainv, alpha, beta, fi, m, s_maps[rr * kTileW + x],
+                                                    s_maps[(kChunk + rr) * kTileW + x], fb, nullptr);
                 store(pix, g);
                 if (fb && n_fallback) atomicAdd(n_fallback, 1ull);
                 if (redo_count) atomicAdd(redo_count, 1ull);

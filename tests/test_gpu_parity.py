@@ -306,6 +306,33 @@ def test_oversize_dimensions_rejected(ctx):
 @pytest.mark.parametrize("H,W,w,N,f64,pitch_extra", [(1080, 1920, 20, 5, False, 0), (96, 160, 5, 5, True, 0),
                                                      (17, 250, 3, 4, True, 5), (8, 64, 1, 2, False, 0),
                                                      (301, 77, 40, 6, True, 3)])
+def test_pinned_host_buffers_equal_device_path(ctx, H, W, w, N, f64, pitch_extra):
+    # pinned theta, sigma and out are read and written in place by the kernel
+    # (only the image is copied); pinned or pageable image; the result must
+    # equal the device-pointer call bit for bit, in every form
+    f, th, s = inputs(H, W, 900 + H)
+    pitch = W + pitch_extra
+    buf = np.zeros((H, pitch), np.uint8)
+    buf[:, :W] = f
+    odt = torch.float64 if f64 else torch.float32
+    pth, psg = torch.from_numpy(th).pin_memory(), torch.from_numpy(s).pin_memory()
+    for prec in (fabf.FABF_FP64, fabf.FABF_CFP32):
+        if prec != fabf.FABF_FP64 and f64:
+            continue
+        fabf.fabf_set_precision(ctx, prec)
+        try:
+            d = fabf.fabf_filter(ctx, dev(buf), dev(th), dev(s), w, N, out_is_f64=f64, pitch=pitch).cpu().numpy()
+            for img in (buf, torch.from_numpy(buf).pin_memory()):
+                pout = torch.full((H, W), -1.0, dtype=odt).pin_memory()
+                fabf.fabf_filter(ctx, img, pth, psg, w, N, out=pout, out_is_f64=f64, pitch=pitch)
+                assert np.array_equal(pout.numpy(), d), (prec, np.abs(pout.numpy() - d).max())
+        finally:
+            fabf.fabf_set_precision(ctx, fabf.FABF_FP64)
+
+
+@pytest.mark.parametrize("H,W,w,N,f64,pitch_extra", [(1080, 1920, 20, 5, False, 0), (96, 160, 5, 5, True, 0),
+                                                     (17, 250, 3, 4, True, 5), (8, 64, 1, 2, False, 0),
+                                                     (301, 77, 40, 6, True, 3)])
 def test_pipelined_host_path_equals_device_path(ctx, H, W, w, N, f64, pitch_extra):
     # host buffers go through the banded copy / compute / copy-back pipeline;
     # the result must equal the device-pointer call bit for bit, in every form
