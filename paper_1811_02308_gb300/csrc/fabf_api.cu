@@ -43,20 +43,26 @@ bool is_device_ptr(const void* p)
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-// A pointer kernels can dereference: device or managed memory as is, pinned
-// host memory through its mapping (read and written in place over the
-// chip-to-chip link); nullptr for pageable host memory.
-const void* kernel_ptr(const void* p)
+// What a buffer is: device (or managed) memory, and the pointer kernels can
+// dereference -- the buffer itself, the mapping of pinned host memory (read
+// and written in place over the chip-to-chip link), or nullptr for pageable
+// host memory.
+PtrInfo ptr_info(const void* p)
 {
-    if (!p) return nullptr;
+    PtrInfo r;
+    if (!p) return r;
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         (void)cudaGetLastError();
-        return nullptr;
+        return r;
     }
-    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return p;
-    if (a.type == cudaMemoryTypeHost && a.devicePointer) return a.devicePointer;
-    return nullptr;
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) {
+        r.device = true;
+        r.kptr = p;
+    } else if (a.type == cudaMemoryTypeHost && a.devicePointer) {
+        r.kptr = a.devicePointer;
+    }
+    return r;
 }
 
 int check_filter_args(const void* img, const void* theta, const void* sigma, const void* out,
@@ -347,31 +353,43 @@ static int filter_host_pipelined(fabf_ctx* ctx, const uint8_t* img, const float*
 // Host-mapped theta, sigma and out (pinned host memory) with a host or device
 // image: the kernel reads the maps and writes the output in place in host
 // memory, so only the image is copied (its tiles are staged by TMA from
-// device memory).  Synchronous: returns the kernels' status.
+// device memory).  Synchronous: returns the kernels' status.  (Copying the
+// image in bands that start their tiles early measured no faster.)
 // ---------------------------------------------------------------------------
-static int filter_mapped(fabf_ctx* ctx, const uint8_t* img, const float* k_th, const float* k_sg, int H, int W,
-                         size_t pitch, int w, int N, void* k_out, int out_f64, cudaStream_t s)
+static int filter_mapped(fabf_ctx* ctx, const uint8_t* img, bool img_dev, const float* k_th, const float* k_sg,
+                         int H, int W, size_t pitch, int w, int N, void* k_out, int out_f64, cudaStream_t s)
 {
     std::lock_guard<std::mutex> staged(ctx->stage_lock);
     const uint8_t* d_img = img;
     size_t d_pitch = pitch;
-    if (!is_device_ptr(img)) {
+    cudaError_t e = cudaSuccess;
+    if (!img_dev) {
         const size_t ipitch = ((size_t)W + 15) & ~(size_t)15;
-        int rc = ensure_stage(ctx, ipitch * H);
+        const int rc = ensure_stage(ctx, ipitch * H);
         if (rc) return rc;
-        const cudaError_t e =
-            cudaMemcpy2DAsync(ctx->stage, ipitch, img, pitch, W, H, cudaMemcpyHostToDevice, s);
-        if (e != cudaSuccess) return cuda_status(e);
+        e = ipitch == pitch ? cudaMemcpyAsync(ctx->stage, img, pitch * H, cudaMemcpyHostToDevice, s)
+                            : cudaMemcpy2DAsync(ctx->stage, ipitch, img, pitch, W, H, cudaMemcpyHostToDevice, s);
         d_img = static_cast<const uint8_t*>(ctx->stage);
         d_pitch = ipitch;
     }
-    int rc = run_fused(ctx, d_img, d_pitch, k_th, k_sg, H, W, w, N, k_out, out_f64, nullptr, s);
-    if (rc) {
+    if (e == cudaSuccess) {
+        const int prec = ctx->precision;
+        FusedParams p;
+        std::memset(&p, 0, sizeof(p));
+        CUtensorMap tm;
+        const size_t smem = make_job(&p.job, &tm, d_img, d_pitch, k_th, k_sg, H, W, w, N, k_out, out_f64,
+                                     tile_rows_for(ctx, w, N, prec, H, W));
+        p.job.maps_host = 1;
+        p.status = ctx->d_status;
+        p.n_fallback = ctx->d_nfb;
+        e = launch_fused(prec, N, tm, p, dim3(p.job.tiles_x, p.job.tiles_y), smem, s);
+    }
+    if (e != cudaSuccess) {
         cudaStreamSynchronize(s);
-        return rc;
+        return cuda_status(e);
     }
     int st = FABF_OK;
-    rc = read_and_clear_status(ctx, s, &st, nullptr, nullptr);
+    const int rc = read_and_clear_status(ctx, s, &st, nullptr, nullptr);
     return rc ? rc : st;
 }
 
@@ -443,17 +461,14 @@ int fabf_filter(fabf_ctx* ctx, const uint8_t* img, const float* theta, const flo
     if (rc) return rc;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return FABF_ECUDA;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-    const bool di = is_device_ptr(img), dt = is_device_ptr(theta), ds = is_device_ptr(sigma),
-               dout = is_device_ptr(out);
-    if (!(dt && ds && dout)) {
+    // one attribute query per buffer: device (or managed), pinned host (with
+    // its kernel mapping) or pageable host
+    const PtrInfo pi = ptr_info(img), pt = ptr_info(theta), ps = ptr_info(sigma), po = ptr_info(out);
+    const bool di = pi.device, dt = pt.device, ds = ps.device, dout = po.device;
+    if (!(dt && ds && dout) && pt.kptr && ps.kptr && po.kptr)
         // pinned host maps and output: read and written in place by the kernel
-        const void* kt = kernel_ptr(theta);
-        const void* ks = kernel_ptr(sigma);
-        void* ko = const_cast<void*>(kernel_ptr(out));
-        if (kt && ks && ko)
-            return filter_mapped(ctx, img, static_cast<const float*>(kt), static_cast<const float*>(ks), H, W,
-                                 pitch, w, N, ko, out_is_f64, s);
-    }
+        return filter_mapped(ctx, img, di, static_cast<const float*>(pt.kptr), static_cast<const float*>(ps.kptr),
+                             H, W, pitch, w, N, const_cast<void*>(po.kptr), out_is_f64, s);
     if (!di && !dt && !ds && !dout)
         return filter_host_pipelined(ctx, img, theta, sigma, H, W, pitch, w, N, out, out_is_f64, s);
     return with_device_buffers(

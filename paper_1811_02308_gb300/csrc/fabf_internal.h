@@ -62,7 +62,11 @@ inline int tune_key(int w, int N, int prec) { return (w * 8 + N) * 4 + prec; }
 
 int cuda_status(cudaError_t e);
 bool is_device_ptr(const void* p);
-const void* kernel_ptr(const void* p);
+struct PtrInfo {
+    bool device = false;           // device or managed memory
+    const void* kptr = nullptr;    // what kernels dereference (nullptr: pageable host memory)
+};
+PtrInfo ptr_info(const void* p);
 int check_filter_args(const void* img, const void* theta, const void* sigma, const void* out, int H, int W,
                       size_t pitch, int w, int N);
 void fused_geometry(int w, int* off, int* Cb);

@@ -90,6 +90,7 @@ struct ImageJob {
     int tiles_x, tiles_y;
     long long tile_begin;  // index of this image's first tile in the launch
     int tile_y0;           // single-image launches: tile row of blockIdx.y == 0 (a band of rows)
+    int maps_host;         // theta / sigma are host memory read over the chip-to-chip link
 };
 
 struct FusedParams {
@@ -153,6 +154,12 @@ __device__ __forceinline__ void cp_async4(void* sdst, const void* gsrc)
 {
     const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
+
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc) : "memory");
 }
 
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
@@ -437,6 +444,13 @@ __device__ __forceinline__ bool fabf_tile(const CUtensorMap* tmap, const ImageJo
     while ((2 << levels) <= 2 * w + 1) ++levels;                   // floor(log2(2w+1))
     const int span = 1 << levels;
     const bool lane_blocks = 2 * w + 1 >= 6;                       // else sparse-table levels
+    // theta / sigma rows of device memory in 16-byte pieces when every piece
+    // is aligned (W a multiple of 4 and both bases 16-byte aligned; x0 is a
+    // multiple of 64; W a multiple of 4 also keeps every piece of an in-image
+    // start in the row).  Host memory is read in 4-byte pieces, measured
+    // faster over the chip-to-chip link.
+    const bool maps16 = !J.maps_host && (J.W & 3) == 0 &&
+                        ((reinterpret_cast<uintptr_t>(J.theta) | reinterpret_cast<uintptr_t>(J.sigma)) & 15) == 0;
 
     for (int r0 = 0; r0 < TH; r0 += kChunk) {
         if (y0 + r0 >= J.H) break;                                 // uniform per CTA
@@ -445,12 +459,26 @@ __device__ __forceinline__ bool fabf_tile(const CUtensorMap* tmap, const ImageJo
         // The chunk's theta and sigma start on their way into shared memory;
         // the vertical phase covers their latency (HBM, or host memory over
         // the chip-to-chip link when the caller's buffers are host-mapped).
-        for (int i = threadIdx.x; i < 2 * kChunk * kTileW; i += kThreads) {
-            const int which = i >= kChunk * kTileW ? 1 : 0;
-            const int e = i - which * kChunk * kTileW;
-            const int rr = e / kTileW, x = e - rr * kTileW;
-            const int Y = y0 + r0 + rr, Xo = x0 + x;
-            if (Y < J.H && Xo < J.W) cp_async4(s_maps + i, (which ? J.sigma : J.theta) + (long long)Y * J.W + Xo);
+        if (maps16) {
+            // 16-byte pieces: 2 maps x kChunk rows x kTileW / 4 pieces
+            for (int i = threadIdx.x; i < 2 * kChunk * (kTileW / 4); i += kThreads) {
+                const int which = i >= kChunk * (kTileW / 4) ? 1 : 0;
+                const int e = i - which * kChunk * (kTileW / 4);
+                const int rr = e / (kTileW / 4), x = 4 * (e - rr * (kTileW / 4));
+                const int Y = y0 + r0 + rr, Xo = x0 + x;
+                if (Y < J.H && Xo < J.W)
+                    cp_async16(s_maps + (which * kChunk + rr) * kTileW + x,
+                               (which ? J.sigma : J.theta) + (long long)Y * J.W + Xo);
+            }
+        } else {
+            for (int i = threadIdx.x; i < 2 * kChunk * kTileW; i += kThreads) {
+                const int which = i >= kChunk * kTileW ? 1 : 0;
+                const int e = i - which * kChunk * kTileW;
+                const int rr = e / kTileW, x = e - rr * kTileW;
+                const int Y = y0 + r0 + rr, Xo = x0 + x;
+                if (Y < J.H && Xo < J.W)
+                    cp_async4(s_maps + i, (which ? J.sigma : J.theta) + (long long)Y * J.W + Xo);
+            }
         }
         cp_async_commit();
         // 2a. Window sums of column c (threads c < Cb): store, then slide the
