@@ -672,7 +672,7 @@ __device__ __forceinline__ bool fabf_tile(const CUtensorMap* tmap, const ImageJo
                         if (fb && n_fallback) atomicAdd(n_fallback, 1ull);
                     }
                     store(pix, g);
-                    if (dbg.alpha) {
+                    if (PREC == kPrecFP64 && dbg.alpha) {   // the stage planes come from the FP64 form only
                         const long long plane = (long long)J.H * J.W;
                         dbg.alpha[pix] = (uint8_t)alpha;
                         dbg.beta[pix] = (uint8_t)beta;

@@ -450,7 +450,7 @@ __device__ __forceinline__ void sep_tile(const CUtensorMap* tmap, const SepParam
                         if (fb && P.n_fallback) atomicAdd(P.n_fallback, 1ull);
                     }
                     store(pix, g);
-                    if (P.dbg.alpha) {
+                    if (PREC == kPrecFP64 && P.dbg.alpha) {   // the stage planes come from the FP64 form only
                         const SepDebug& D = P.dbg;
                         const long long pl = (long long)J.H * J.W;
                         D.alpha[pix] = (uint8_t)alpha;
