@@ -738,20 +738,23 @@ int oracle_bruteforce_sep(const uint8_t* f, const float* theta, const float* sig
  * Readings (the paper leaves the parameters of these rules open):
  *   - sharpening centre (Sec. IV-A): theta = f + zeta with zeta = f - fbar,
  *     fbar the plain mean of f over the filter window [-w, w]^2 clipped to
- *     the image, i.e. theta = (2 f m_0 - m_1) / m_0, one binary64 division of
- *     exact integers, rounded to binary32;
+ *     the image, i.e. theta = (2 f m_0 - m_1) / m_0, the correctly rounded
+ *     binary32 quotient of two integers that binary32 holds exactly;
  *   - sharpening width (Sec. IV-A): the Laplacian of a Gaussian of f, as the
  *     integer Gaussian S = g x g * f (integer taps, coordinates clamped to the
  *     image) followed by the 5-point Laplacian of S (clamped), so L is an
  *     exact integer; with q = min(|L|, Lq) the width is sigma = s_hi - (s_hi -
- *     s_lo) (q / Lq) in binary64 (division, product, difference), rounded to
- *     binary32: low |LoG| gives a wide range kernel, high |LoG| a narrow one;
+ *     s_lo) (q / Lq) in binary32 (q and Lq rounded to binary32, then the
+ *     division, the difference s_hi - s_lo, the product and the difference,
+ *     each rounded): low |LoG| gives a wide range kernel, high |LoG| a narrow
+ *     one;
  *   - texture width (Sec. IV-C): mRTV = Delta gmax / (gsum + eps) over the
  *     window [-k, k]^2 clipped to the image, with Delta the range of f there
  *     and g = |f(x+1, y) - f(x, y)| + |f(x, y+1) - f(x, y)| (forward
  *     differences, clamped; the L1 norm keeps g an integer), then sigma =
- *     s_hi - (s_hi - s_lo) min(mRTV / msat, 1) in binary64, rounded to
- *     binary32.
+ *     s_hi - (s_hi - s_lo) min(mRTV / msat, 1), all in binary32 operations
+ *     in that order (Delta gmax and gsum are exact in binary32).
+ * The maps are binary32 maps, so they are evaluated in binary32.
  */
 static inline int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
@@ -763,7 +766,9 @@ int oracle_sharpen_theta(const uint8_t* f, int H, int W, long pitch, int w, floa
             int64_t m[2];
             pixel_moments(f, H, W, pitch, w, 1, y, x, m);
             const int64_t num = 2 * (int64_t)f[(long)y * pitch + x] * m[0] - m[1];
-            theta[(long)y * W + x] = (float)((double)num / (double)m[0]);
+            /* |num| <= 2 * 255 * 6561 < 2^24 and m_0 <= 6561: both exact in
+               binary32, so this is the correctly rounded binary32 quotient */
+            theta[(long)y * W + x] = (float)num / (float)m[0];
         }
     return 0;
 }
@@ -803,8 +808,10 @@ int oracle_sharpen_sigma(const uint8_t* f, int H, int W, long pitch, const uint3
             int64_t L = log_at(f, H, W, pitch, taps, r, y, x);
             if (L < 0) L = -L;
             const int64_t q = L < Lq ? L : Lq;
-            const double u = (double)q / (double)Lq;
-            sigma[(long)y * W + x] = (float)(s_hi - (s_hi - s_lo) * u);
+            /* binary32 throughout (the map is a binary32 map) */
+            const float u = (float)q / (float)Lq;
+            const float hi = (float)s_hi, lo = (float)s_lo;
+            sigma[(long)y * W + x] = hi - (hi - lo) * u;
         }
     return 0;
 }
@@ -829,10 +836,13 @@ int oracle_texture_sigma(const uint8_t* f, int H, int W, long pitch, int k, doub
                     if (g > gmax) gmax = g;
                     gsum += g;
                 }
-            const double mrtv = (double)((int64_t)(fmax - fmin) * gmax) / ((double)gsum + eps);
-            double u = mrtv / msat;
-            if (u > 1.0) u = 1.0;
-            sigma[(long)y * W + x] = (float)(s_hi - (s_hi - s_lo) * u);
+            /* binary32 throughout: Delta gmax <= 255 * 510 and gsum <=
+               81^2 * 510 are exact in binary32 */
+            const float mrtv = (float)((int64_t)(fmax - fmin) * gmax) / ((float)gsum + (float)eps);
+            float u = mrtv / (float)msat;
+            if (u > 1.0f) u = 1.0f;
+            const float hi = (float)s_hi, lo = (float)s_lo;
+            sigma[(long)y * W + x] = hi - (hi - lo) * u;
         }
     return 0;
 }

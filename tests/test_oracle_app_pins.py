@@ -4,6 +4,7 @@ each against an independent numpy implementation of the same reading, bit
 for bit, plus the behaviour the paper describes (flat regions get wide range
 kernels, strong edges narrow ones; constant images pass unchanged)."""
 import math
+from fractions import Fraction
 
 import numpy as np
 import pytest
@@ -20,6 +21,15 @@ def lq_for(taps, lap_sat):
     return int(math.floor(lap_sat * float(int(taps.sum())) ** 2 + 0.5))
 
 
+def rn32(q: Fraction) -> np.float32:
+    """The binary32 value nearest to the rational q (ties to even), found by
+    exact comparison among the neighbours of a first guess."""
+    c = np.float32(float(q))
+    cands = [np.nextafter(c, np.float32(-np.inf)), c, np.nextafter(c, np.float32(np.inf))]
+    best = min(cands, key=lambda v: (abs(Fraction(float(v)) - q), int(np.frombuffer(v.tobytes(), np.uint32)[0]) & 1))
+    return np.float32(best)
+
+
 @pytest.mark.parametrize("H,W,w,seed", [(9, 11, 2, 1), (1, 7, 3, 2), (13, 5, 6, 3), (6, 6, 40, 4)])
 def test_sharpen_theta_is_twice_f_minus_window_mean(oracle_mod, H, W, w, seed):
     f = image(H, W, seed)
@@ -28,7 +38,7 @@ def test_sharpen_theta_is_twice_f_minus_window_mean(oracle_mod, H, W, w, seed):
         for x in range(W):
             win = f[max(0, y - w):y + w + 1, max(0, x - w):x + w + 1].astype(np.int64)
             m0, m1 = win.size, int(win.sum())
-            ref = np.float32((2 * int(f[y, x]) * m0 - m1) / m0)   # int / int: correctly rounded
+            ref = rn32(Fraction(2 * int(f[y, x]) * m0 - m1, m0))   # the exact quotient, rounded once
             assert th[y, x] == ref, (y, x)
 
 
@@ -55,7 +65,9 @@ def test_sharpen_log_and_sigma(oracle_mod, rho):
     Lq = lq_for(taps, 12.0)
     sg = oracle_mod.sharpen_sigma(f, taps, Lq, 10.0, 40.0)
     q = np.minimum(np.abs(L), Lq)
-    ref = np.array([[np.float32(40.0 - (40.0 - 10.0) * (int(v) / Lq)) for v in row] for row in q])
+    f32 = np.float32
+    u = q.astype(f32) / f32(Lq)                                  # binary32 operations, in order
+    ref = f32(40.0) - (f32(40.0) - f32(10.0)) * u
     assert np.array_equal(sg, ref)
     assert sg.min() >= 10.0 and sg.max() <= 40.0
 
@@ -71,9 +83,10 @@ def np_texture_sigma(f, k, eps, msat, lo, hi):
         for x in range(W):
             sl = (slice(max(0, y - k), y + k + 1), slice(max(0, x - k), x + k + 1))
             delta = int(fi[sl].max() - fi[sl].min())
-            mrtv = (delta * int(g[sl].max())) / (float(int(g[sl].sum())) + eps)
-            u = min(mrtv / msat, 1.0)
-            out[y, x] = np.float32(hi - (hi - lo) * u)
+            f32 = np.float32
+            mrtv = f32(delta * int(g[sl].max())) / (f32(int(g[sl].sum())) + f32(eps))
+            u = min(mrtv / f32(msat), f32(1.0))
+            out[y, x] = f32(hi) - (f32(hi) - f32(lo)) * u
     return out
 
 

@@ -69,8 +69,10 @@ MUTANTS = {
     "sharpening centre sign": ("* m[0] - m[1];", "* m[0] + m[1];"),
     "LoG centre weight": ("S[1] + S[2] + S[3] + S[4] - 4 * S[0]", "S[1] + S[2] + S[3] + S[4] - 5 * S[0]"),
     "texture gradient direction": ("clampi(xx + 1, 0, W - 1)", "clampi(xx - 1, 0, W - 1)"),
-    "texture width map reversed": ("if (u > 1.0) u = 1.0;\n            sigma[(long)y * W + x] = (float)(s_hi - (s_hi - s_lo) * u);",
-                                   "if (u > 1.0) u = 1.0;\n            sigma[(long)y * W + x] = (float)(s_lo + (s_hi - s_lo) * u);"),
+    "texture width map reversed": ("u = 1.0f;\n            const float hi = (float)s_hi, lo = (float)s_lo;\n"
+                                   "            sigma[(long)y * W + x] = hi - (hi - lo) * u;",
+                                   "u = 1.0f;\n            const float hi = (float)s_hi, lo = (float)s_lo;\n"
+                                   "            sigma[(long)y * W + x] = lo + (hi - lo) * u;"),
 }
 
 # ---------------------------------------------------------------------------
@@ -254,7 +256,9 @@ def battery():
         th = oracle.sharpen_theta(f, 2)
         for y, x in ((0, 0), (5, 6), (10, 12)):
             win = fi[max(0, y - 2):y + 3, max(0, x - 2):x + 3]
-            assert th[y, x] == np.float32((2 * int(fi[y, x]) * win.size - int(win.sum())) / win.size)
+            # binary32 holds both integers exactly; IEEE division rounds the quotient once
+            num = 2 * int(fi[y, x]) * win.size - int(win.sum())
+            assert th[y, x] == np.float32(num) / np.float32(win.size)
         taps = np.array([1, 4, 1], np.uint32)
         p = np.pad(fi, 1, mode="edge")
         S = sum(int(taps[a]) * int(taps[b]) * p[a:a + H, b:b + W] for a in range(3) for b in range(3))
@@ -267,8 +271,9 @@ def battery():
         ts = oracle.texture_sigma(f, 1, 1.0, 8.0, 5.0, 60.0)
         for y, x in ((0, 0), (5, 6), (10, 12), (3, 9)):
             sl = (slice(max(0, y - 1), y + 2), slice(max(0, x - 1), x + 2))
-            mr = int(fi[sl].max() - fi[sl].min()) * int(g[sl].max()) / (float(int(g[sl].sum())) + 1.0)
-            assert ts[y, x] == np.float32(60.0 - 55.0 * min(mr / 8.0, 1.0))
+            f32 = np.float32
+            mr = f32(int(fi[sl].max() - fi[sl].min()) * int(g[sl].max())) / (f32(int(g[sl].sum())) + f32(1.0))
+            assert ts[y, x] == f32(60.0) - (f32(60.0) - f32(5.0)) * min(mr / f32(8.0), f32(1.0))
 
     for name, fn in [("hilbert", hilbert), ("window", window_stats), ("integrals", integrals),
                      ("fit", fit_moments), ("constant", constant_image), ("box mean", box_mean_limit),
