@@ -6,9 +6,10 @@
 // channel (Sec. IV-C), with the width maps taken from the luma.
 //
 // The maps follow the readings the CPU oracle states (integer-exact up to one
-// fixed sequence of binary64 operations, rounded to binary32), written with
-// explicitly rounded intrinsics so that no multiply-add is contracted: the
-// maps are bit-identical to the oracle's.
+// fixed sequence of binary32 operations: the maps are binary32 maps, and
+// binary64 runs at 1/64 of the binary32 rate on GB300),
+// written with explicitly rounded intrinsics so that no multiply-add is
+// contracted: the maps are bit-identical to the oracle's.
 //   theta_sharpen = (2 f m_0 - m_1) / m_0 over the clipped window [-w, w]^2;
 //   L = 5-point Laplacian of the integer Gaussian S = g x g * f (coordinates
 //       clamped), sigma_sharpen = s_hi - (s_hi - s_lo) (min(|L|, Lq) / Lq);
@@ -39,9 +40,9 @@ __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? l
 // rs = sum of f over the clipped row segment [x - w, x + w]
 __global__ void box_rows_kernel(const uint8_t* f, long long pitch, int H, int W, int w, int32_t* rs)
 {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (long long)H * W) return;
-    const int y = (int)(i / W), x = (int)(i - (long long)y * W);
+    const int x = (int)(blockIdx.x * blockDim.x + threadIdx.x), y = (int)blockIdx.y;
+    if (x >= W) return;
+    const long long i = (long long)y * W + x;
     const uint8_t* row = f + (long long)y * pitch;
     const int x0 = max(x - w, 0), x1 = min(x + w, W - 1);
     int32_t s = 0;
@@ -52,25 +53,27 @@ __global__ void box_rows_kernel(const uint8_t* f, long long pitch, int H, int W,
 __global__ void sharpen_theta_kernel(const uint8_t* f, long long pitch, const int32_t* rs, int H, int W, int w,
                                      float* theta)
 {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (long long)H * W) return;
-    const int y = (int)(i / W), x = (int)(i - (long long)y * W);
+    const int x = (int)(blockIdx.x * blockDim.x + threadIdx.x), y = (int)blockIdx.y;
+    if (x >= W) return;
+    const long long i = (long long)y * W + x;
     const int y0 = max(y - w, 0), y1 = min(y + w, H - 1);
     const int x0 = max(x - w, 0), x1 = min(x + w, W - 1);
     int64_t m1 = 0;
     for (int yy = y0; yy <= y1; ++yy) m1 += rs[(long long)yy * W + x];
     const int64_t m0 = (int64_t)(y1 - y0 + 1) * (x1 - x0 + 1);
-    const int64_t num = 2 * (int64_t)f[(long long)y * pitch + x] * m0 - m1;
-    theta[i] = __double2float_rn(__ddiv_rn((double)num, (double)m0));
+    // |num| <= 2 * 255 * 6561 < 2^24 and m0 <= 6561 are exact in binary32:
+    // the correctly rounded binary32 quotient
+    const int num = (int)(2 * (int64_t)f[(long long)y * pitch + x] * m0 - m1);
+    theta[i] = __fdiv_rn(__int2float_rn(num), __int2float_rn((int)m0));
 }
 
 // gr = sum_t g[t] f(y, clamp(x + t - r))
 __global__ void gauss_rows_kernel(const uint8_t* f, long long pitch, int H, int W, const __grid_constant__ SepTaps T,
                                   uint32_t* gr)
 {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (long long)H * W) return;
-    const int y = (int)(i / W), x = (int)(i - (long long)y * W);
+    const int x = (int)(blockIdx.x * blockDim.x + threadIdx.x), y = (int)blockIdx.y;
+    if (x >= W) return;
+    const long long i = (long long)y * W + x;
     const uint8_t* row = f + (long long)y * pitch;
     uint32_t s = 0;
     for (int t = 0; t <= 2 * T.r; ++t) s += T.g[t] * (uint32_t)row[clampi(x + t - T.r, 0, W - 1)];
@@ -80,45 +83,58 @@ __global__ void gauss_rows_kernel(const uint8_t* f, long long pitch, int H, int 
 // S = sum_t g[t] gr(clamp(y + t - r), x)
 __global__ void gauss_cols_kernel(const uint32_t* gr, int H, int W, const __grid_constant__ SepTaps T, int64_t* S)
 {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (long long)H * W) return;
-    const int y = (int)(i / W), x = (int)(i - (long long)y * W);
+    const int x = (int)(blockIdx.x * blockDim.x + threadIdx.x), y = (int)blockIdx.y;
+    if (x >= W) return;
+    const long long i = (long long)y * W + x;
     int64_t s = 0;
     for (int t = 0; t <= 2 * T.r; ++t) s += (int64_t)T.g[t] * gr[(long long)clampi(y + t - T.r, 0, H - 1) * W + x];
     S[i] = s;
 }
 
-__global__ void sharpen_sigma_kernel(const int64_t* S, int H, int W, long long Lq, double s_lo, double s_hi,
+__global__ void sharpen_sigma_kernel(const int64_t* S, int H, int W, long long Lq, float lo, float hi,
                                      float* sigma)
 {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (long long)H * W) return;
-    const int y = (int)(i / W), x = (int)(i - (long long)y * W);
+    const int x = (int)(blockIdx.x * blockDim.x + threadIdx.x), y = (int)blockIdx.y;
+    if (x >= W) return;
+    const long long i = (long long)y * W + x;
     const int64_t L = S[(long long)clampi(y - 1, 0, H - 1) * W + x] + S[(long long)clampi(y + 1, 0, H - 1) * W + x] +
                       S[(long long)y * W + clampi(x - 1, 0, W - 1)] + S[(long long)y * W + clampi(x + 1, 0, W - 1)] -
                       4 * S[i];
     const int64_t a = L < 0 ? -L : L;
     const int64_t q = a < Lq ? a : Lq;
-    const double u = __ddiv_rn((double)q, (double)Lq);
-    sigma[i] = __double2float_rn(__dsub_rn(s_hi, __dmul_rn(__dsub_rn(s_hi, s_lo), u)));
+    const float u = __fdiv_rn(__ll2float_rn(q), __ll2float_rn(Lq));
+    sigma[i] = __fsub_rn(hi, __fmul_rn(__fsub_rn(hi, lo), u));
 }
 
-__global__ void texture_sigma_kernel(const uint8_t* f, long long pitch, int H, int W, int k, double eps, double msat,
-                                     double s_lo, double s_hi, float* sigma)
+// One block per 256-pixel row segment.  The block stages the rows y - k ..
+// y + k + 1 and columns x - k .. x + 255 + k + 1 of f in shared memory,
+// with coordinates clamped to the image: an in-image row or column is
+// itself, and the clamped neighbour of the last row or column is the
+// clamped copy, as the definition wants.  Each thread then scans its window
+// there.
+__global__ void texture_sigma_kernel(const uint8_t* f, long long pitch, int H, int W, int k, float eps, float msat,
+                                     float lo, float hi, float* sigma)
 {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (long long)H * W) return;
-    const int y = (int)(i / W), x = (int)(i - (long long)y * W);
+    extern __shared__ uint8_t tile[];                // [2k + 2][kAppThreads + 2k + 1]
+    const int y = (int)blockIdx.y, xs = (int)(blockIdx.x * blockDim.x);
+    const int R = 2 * k + 2, C = (int)blockDim.x + 2 * k + 1;
+    for (int e = (int)threadIdx.x; e < R * C; e += (int)blockDim.x) {
+        const int r = e / C, c = e - r * C;
+        tile[e] = f[(long long)clampi(y - k + r, 0, H - 1) * pitch + clampi(xs - k + c, 0, W - 1)];
+    }
+    __syncthreads();
+    const int x = xs + (int)threadIdx.x;
+    if (x >= W) return;
+    const long long i = (long long)y * W + x;
     const int y0 = max(y - k, 0), y1 = min(y + k, H - 1);
     const int x0 = max(x - k, 0), x1 = min(x + k, W - 1);
-    int fmin = 255, fmax = 0, gmax = 0;
-    int64_t gsum = 0;
+    int fmin = 255, fmax = 0, gmax = 0, gsum = 0;
     for (int yy = y0; yy <= y1; ++yy) {
-        const uint8_t* row = f + (long long)yy * pitch;
-        const uint8_t* below = f + (long long)min(yy + 1, H - 1) * pitch;
+        const uint8_t* row = tile + (yy - (y - k)) * C - (xs - k);    // row[xx] = f(yy, xx)
+        const uint8_t* below = row + C;                                // the clamped next row
         for (int xx = x0; xx <= x1; ++xx) {
             const int v = row[xx];
-            const int vx = row[min(xx + 1, W - 1)];
+            const int vx = row[xx + 1];
             const int vy = below[xx];
             const int g = abs(vx - v) + abs(vy - v);
             fmin = min(fmin, v);
@@ -127,17 +143,19 @@ __global__ void texture_sigma_kernel(const uint8_t* f, long long pitch, int H, i
             gsum += g;
         }
     }
-    const double mrtv = __ddiv_rn((double)((int64_t)(fmax - fmin) * gmax), __dadd_rn((double)gsum, eps));
-    double u = __ddiv_rn(mrtv, msat);
-    if (u > 1.0) u = 1.0;
-    sigma[i] = __double2float_rn(__dsub_rn(s_hi, __dmul_rn(__dsub_rn(s_hi, s_lo), u)));
+    // Delta gmax <= 255 * 510 and gsum <= 81^2 * 510 are exact in binary32
+    const float mrtv = __fdiv_rn(__int2float_rn((fmax - fmin) * gmax),
+                                 __fadd_rn(__int2float_rn(gsum), eps));
+    float u = __fdiv_rn(mrtv, msat);
+    if (u > 1.0f) u = 1.0f;
+    sigma[i] = __fsub_rn(hi, __fmul_rn(__fsub_rn(hi, lo), u));
 }
 
 __global__ void u8_to_float_kernel(const uint8_t* f, long long pitch, int H, int W, float* out)
 {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (long long)H * W) return;
-    const int y = (int)(i / W), x = (int)(i - (long long)y * W);
+    const int x = (int)(blockIdx.x * blockDim.x + threadIdx.x), y = (int)blockIdx.y;
+    if (x >= W) return;
+    const long long i = (long long)y * W + x;
     out[i] = (float)f[(long long)y * pitch + x];
 }
 
@@ -148,13 +166,17 @@ __global__ void u8_to_float_kernel(const uint8_t* f, long long pitch, int H, int
 __global__ void next_input_kernel(const void* g, int g_f64, int H, int W, uint8_t* f_next, long long pitch_next,
                                   float* theta_next, const float* sig_in, float* sig_out, float decay)
 {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (long long)H * W) return;
-    const int y = (int)(i / W), x = (int)(i - (long long)y * W);
-    const double v = g_f64 ? static_cast<const double*>(g)[i] : (double)static_cast<const float*>(g)[i];
-    double r = rint(v);
-    r = r < 0.0 ? 0.0 : (r > 255.0 ? 255.0 : r);
-    const uint8_t u = (uint8_t)r;
+    const int x = (int)(blockIdx.x * blockDim.x + threadIdx.x), y = (int)blockIdx.y;
+    if (x >= W) return;
+    const long long i = (long long)y * W + x;
+    uint8_t u;
+    if (g_f64) {
+        double r = rint(static_cast<const double*>(g)[i]);
+        u = (uint8_t)(r < 0.0 ? 0.0 : (r > 255.0 ? 255.0 : r));
+    } else {   // the same rounding in binary32 (rintf(v) == rint((double)v) for every float v)
+        float r = rintf(static_cast<const float*>(g)[i]);
+        u = (uint8_t)(r < 0.0f ? 0.0f : (r > 255.0f ? 255.0f : r));
+    }
     f_next[(long long)y * pitch_next + x] = u;
     if (theta_next) theta_next[i] = (float)u;
     if (sig_out) sig_out[i] = __fmul_rn(sig_in[i], decay);
@@ -173,9 +195,8 @@ __device__ __forceinline__ uint8_t luma_of(unsigned r, unsigned g, unsigned b)
 __global__ void rgb_split_kernel(const uint8_t* rgb, long long pitch, int H, int W, uint8_t* planes, long long pn,
                                  long long plane_stride, uint8_t* Y)
 {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (long long)H * W) return;
-    const int y = (int)(i / W), x = (int)(i - (long long)y * W);
+    const int x = (int)(blockIdx.x * blockDim.x + threadIdx.x), y = (int)blockIdx.y;
+    if (x >= W) return;
     const uint8_t* px = rgb + (long long)y * pitch + 3LL * x;
     const unsigned r = px[0], g = px[1], b = px[2];
     const long long o = (long long)y * pn + x;
@@ -191,9 +212,8 @@ __global__ void rgb_split_kernel(const uint8_t* rgb, long long pitch, int H, int
 __global__ void planes_luma_kernel(const uint8_t* planes, long long pn, long long plane_stride, int H, int W,
                                    uint8_t* Y)
 {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (long long)H * W) return;
-    const int y = (int)(i / W), x = (int)(i - (long long)y * W);
+    const int x = (int)(blockIdx.x * blockDim.x + threadIdx.x), y = (int)blockIdx.y;
+    if (x >= W) return;
     const long long o = (long long)y * pn + x;
     Y[o] = luma_of(planes[o], planes[o + plane_stride], planes[o + 2 * plane_stride]);
 }
@@ -219,6 +239,12 @@ __global__ void interleave_kernel(const T* g, long long plane_elems, long long n
 }
 
 unsigned blocks_for(long long n) { return (unsigned)((n + kAppThreads - 1) / kAppThreads); }
+
+// One block row per image row (H <= 65535): no index division in the kernels.
+dim3 grid2d(int H, int W) { return dim3((unsigned)((W + kAppThreads - 1) / kAppThreads), (unsigned)H); }
+
+// Shared memory of one texture_sigma_kernel block (k <= 40: at most 27.6 KB).
+size_t texture_smem(int k) { return (size_t)(2 * k + 2) * (size_t)(kAppThreads + 2 * k + 1); }
 
 int check_sharpen_cfg(const fabf_sharpen_cfg* c)
 {
@@ -283,11 +309,11 @@ int launch_sharpen_maps(const uint8_t* f, long long pitch, int H, int W, int w, 
 {
     const long long n = (long long)H * W;
     const unsigned b = blocks_for(n);
-    box_rows_kernel<<<b, kAppThreads, 0, s>>>(f, pitch, H, W, w, rs);
-    sharpen_theta_kernel<<<b, kAppThreads, 0, s>>>(f, pitch, rs, H, W, w, theta);
-    gauss_rows_kernel<<<b, kAppThreads, 0, s>>>(f, pitch, H, W, T, gr);
-    gauss_cols_kernel<<<b, kAppThreads, 0, s>>>(gr, H, W, T, S);
-    sharpen_sigma_kernel<<<b, kAppThreads, 0, s>>>(S, H, W, Lq, s_lo, s_hi, sigma);
+    box_rows_kernel<<<grid2d(H, W), kAppThreads, 0, s>>>(f, pitch, H, W, w, rs);
+    sharpen_theta_kernel<<<grid2d(H, W), kAppThreads, 0, s>>>(f, pitch, rs, H, W, w, theta);
+    gauss_rows_kernel<<<grid2d(H, W), kAppThreads, 0, s>>>(f, pitch, H, W, T, gr);
+    gauss_cols_kernel<<<grid2d(H, W), kAppThreads, 0, s>>>(gr, H, W, T, S);
+    sharpen_sigma_kernel<<<grid2d(H, W), kAppThreads, 0, s>>>(S, H, W, Lq, (float)s_lo, (float)s_hi, sigma);
     return cuda_status(cudaGetLastError());
 }
 
@@ -353,8 +379,9 @@ int fabf_texture_sigma(fabf_ctx* ctx, const uint8_t* img, int H, int W, size_t p
     if (!all_device({img, sigma})) return FABF_EINVAL;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return FABF_ECUDA;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-    texture_sigma_kernel<<<blocks_for((long long)H * W), kAppThreads, 0, s>>>(
-        img, (long long)pitch, H, W, cfg->k, cfg->eps, cfg->mrtv_sat, cfg->sigma_lo, cfg->sigma_hi, sigma);
+    texture_sigma_kernel<<<grid2d(H, W), kAppThreads, texture_smem(cfg->k), s>>>(
+        img, (long long)pitch, H, W, cfg->k, (float)cfg->eps, (float)cfg->mrtv_sat, (float)cfg->sigma_lo,
+        (float)cfg->sigma_hi, sigma);
     return cuda_status(cudaGetLastError());
 }
 
@@ -423,22 +450,23 @@ int fabf_texture_filter(fabf_ctx* ctx, const uint8_t* img, int H, int W, size_t 
     uint8_t* f3 = b + o_f3;
     const unsigned nb = blocks_for(n);
     // pass 1: theta = f, sigma from mRTV
-    texture_sigma_kernel<<<nb, kAppThreads, 0, s>>>(img, (long long)pitch, H, W, cfg->k, cfg->eps, cfg->mrtv_sat,
-                                                    cfg->sigma_lo, cfg->sigma_hi, s1);
-    u8_to_float_kernel<<<nb, kAppThreads, 0, s>>>(img, (long long)pitch, H, W, th);
+    texture_sigma_kernel<<<grid2d(H, W), kAppThreads, texture_smem(cfg->k), s>>>(
+        img, (long long)pitch, H, W, cfg->k, (float)cfg->eps, (float)cfg->mrtv_sat, (float)cfg->sigma_lo,
+        (float)cfg->sigma_hi, s1);
+    u8_to_float_kernel<<<grid2d(H, W), kAppThreads, 0, s>>>(img, (long long)pitch, H, W, th);
     rc = cuda_status(cudaGetLastError());
     if (rc) return rc;
     rc = run_fused(ctx, img, pitch, th, s1, H, W, cfg->w, cfg->N, g, g_f64, nullptr, s);
     if (rc) return rc;
     // pass 2: the rounded output, theta = f2, sigma scaled by sigma_decay
-    next_input_kernel<<<nb, kAppThreads, 0, s>>>(g, g_f64, H, W, f2, (long long)pn, th, s1, s2,
+    next_input_kernel<<<grid2d(H, W), kAppThreads, 0, s>>>(g, g_f64, H, W, f2, (long long)pn, th, s1, s2,
                                                  (float)cfg->sigma_decay);
     rc = cuda_status(cudaGetLastError());
     if (rc) return rc;
     rc = run_fused(ctx, f2, pn, th, s2, H, W, cfg->w, cfg->N, g, g_f64, nullptr, s);
     if (rc) return rc;
     // pass 3: sharpening of the rounded output
-    next_input_kernel<<<nb, kAppThreads, 0, s>>>(g, g_f64, H, W, f3, (long long)pn, nullptr, nullptr, nullptr, 1.0f);
+    next_input_kernel<<<grid2d(H, W), kAppThreads, 0, s>>>(g, g_f64, H, W, f3, (long long)pn, nullptr, nullptr, nullptr, 1.0f);
     rc = launch_sharpen_maps(f3, (long long)pn, H, W, sc_cfg.w, T, Lq, sc_cfg.sigma_lo, sc_cfg.sigma_hi,
                              reinterpret_cast<int32_t*>(b + o_rs), reinterpret_cast<uint32_t*>(b + o_gr),
                              reinterpret_cast<int64_t*>(b + o_S), th, s2, s);
@@ -459,7 +487,7 @@ int fabf_luma(fabf_ctx* ctx, const uint8_t* rgb, int H, int W, size_t pitch, uin
     if (!all_device({rgb, Y})) return FABF_EINVAL;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return FABF_ECUDA;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-    rgb_split_kernel<<<blocks_for((long long)H * W), kAppThreads, 0, s>>>(rgb, (long long)pitch, H, W, nullptr,
+    rgb_split_kernel<<<grid2d(H, W), kAppThreads, 0, s>>>(rgb, (long long)pitch, H, W, nullptr,
                                                                           (long long)y_pitch, 0, Y);
     return cuda_status(cudaGetLastError());
 }
@@ -487,14 +515,14 @@ int fabf_filter_rgb(fabf_ctx* ctx, const uint8_t* rgb, const float* theta, const
     uint8_t* b = static_cast<uint8_t*>(sc.base);
     float* th = reinterpret_cast<float*>(b + o_th);
     const unsigned nb = blocks_for(n);
-    rgb_split_kernel<<<nb, kAppThreads, 0, s>>>(rgb, (long long)pitch, H, W, b, (long long)pn, (long long)plane,
+    rgb_split_kernel<<<grid2d(H, W), kAppThreads, 0, s>>>(rgb, (long long)pitch, H, W, b, (long long)pn, (long long)plane,
                                                 nullptr);
     for (int c = 0; c < 3; ++c) {
         const uint8_t* f = b + c * plane;
         if (theta)
             channel_kernel<<<nb, kAppThreads, 0, s>>>(theta, H, W, c, th);
         else
-            u8_to_float_kernel<<<nb, kAppThreads, 0, s>>>(f, (long long)pn, H, W, th);
+            u8_to_float_kernel<<<grid2d(H, W), kAppThreads, 0, s>>>(f, (long long)pn, H, W, th);
         rc = cuda_status(cudaGetLastError());
         if (rc) return rc;
         rc = run_fused(ctx, f, pn, th, sigma, H, W, w, N, b + o_g + c * gplane, out_is_f64, nullptr, s);
@@ -544,43 +572,43 @@ int fabf_texture_filter_rgb(fabf_ctx* ctx, const uint8_t* rgb, int H, int W, siz
     const unsigned nb = blocks_for(n);
     const long long lpn = (long long)pn;
     // the planes, and the texture width map of the luma
-    rgb_split_kernel<<<nb, kAppThreads, 0, s>>>(rgb, (long long)pitch, H, W, b, lpn, (long long)plane, Y);
-    texture_sigma_kernel<<<nb, kAppThreads, 0, s>>>(Y, lpn, H, W, cfg->k, cfg->eps, cfg->mrtv_sat, cfg->sigma_lo,
-                                                    cfg->sigma_hi, s1);
+    rgb_split_kernel<<<grid2d(H, W), kAppThreads, 0, s>>>(rgb, (long long)pitch, H, W, b, lpn, (long long)plane, Y);
+    texture_sigma_kernel<<<grid2d(H, W), kAppThreads, texture_smem(cfg->k), s>>>(
+        Y, lpn, H, W, cfg->k, (float)cfg->eps, (float)cfg->mrtv_sat, (float)cfg->sigma_lo, (float)cfg->sigma_hi, s1);
     rc = cuda_status(cudaGetLastError());
     if (rc) return rc;
     // per channel: the two smoothing passes (theta = f), rounded into F3
     for (int c = 0; c < 3; ++c) {
         const uint8_t* f = b + c * plane;
-        u8_to_float_kernel<<<nb, kAppThreads, 0, s>>>(f, lpn, H, W, th);
+        u8_to_float_kernel<<<grid2d(H, W), kAppThreads, 0, s>>>(f, lpn, H, W, th);
         rc = cuda_status(cudaGetLastError());
         if (rc) return rc;
         rc = run_fused(ctx, f, pn, th, s1, H, W, cfg->w, cfg->N, gm, g_f64, nullptr, s);
         if (rc) return rc;
-        next_input_kernel<<<nb, kAppThreads, 0, s>>>(gm, g_f64, H, W, F2, lpn, th, c == 0 ? s1 : nullptr,
+        next_input_kernel<<<grid2d(H, W), kAppThreads, 0, s>>>(gm, g_f64, H, W, F2, lpn, th, c == 0 ? s1 : nullptr,
                                                      c == 0 ? s2 : nullptr, (float)cfg->sigma_decay);
         rc = cuda_status(cudaGetLastError());
         if (rc) return rc;
         rc = run_fused(ctx, F2, pn, th, s2, H, W, cfg->w, cfg->N, gm, g_f64, nullptr, s);
         if (rc) return rc;
-        next_input_kernel<<<nb, kAppThreads, 0, s>>>(gm, g_f64, H, W, F3 + c * plane, lpn, nullptr, nullptr,
+        next_input_kernel<<<grid2d(H, W), kAppThreads, 0, s>>>(gm, g_f64, H, W, F3 + c * plane, lpn, nullptr, nullptr,
                                                      nullptr, 1.0f);
     }
     // the sharpening width map of the luma of F3 (into s1), shared by the channels
     int32_t* rs = reinterpret_cast<int32_t*>(b + o_rs);
-    planes_luma_kernel<<<nb, kAppThreads, 0, s>>>(F3, lpn, (long long)plane, H, W, Y);
-    gauss_rows_kernel<<<nb, kAppThreads, 0, s>>>(Y, lpn, H, W, T, reinterpret_cast<uint32_t*>(b + o_gr));
-    gauss_cols_kernel<<<nb, kAppThreads, 0, s>>>(reinterpret_cast<uint32_t*>(b + o_gr), H, W, T,
+    planes_luma_kernel<<<grid2d(H, W), kAppThreads, 0, s>>>(F3, lpn, (long long)plane, H, W, Y);
+    gauss_rows_kernel<<<grid2d(H, W), kAppThreads, 0, s>>>(Y, lpn, H, W, T, reinterpret_cast<uint32_t*>(b + o_gr));
+    gauss_cols_kernel<<<grid2d(H, W), kAppThreads, 0, s>>>(reinterpret_cast<uint32_t*>(b + o_gr), H, W, T,
                                                  reinterpret_cast<int64_t*>(b + o_S));
-    sharpen_sigma_kernel<<<nb, kAppThreads, 0, s>>>(reinterpret_cast<int64_t*>(b + o_S), H, W, Lq, shc.sigma_lo,
-                                                    shc.sigma_hi, s1);
+    sharpen_sigma_kernel<<<grid2d(H, W), kAppThreads, 0, s>>>(reinterpret_cast<int64_t*>(b + o_S), H, W, Lq,
+                                                              (float)shc.sigma_lo, (float)shc.sigma_hi, s1);
     rc = cuda_status(cudaGetLastError());
     if (rc) return rc;
     // per channel: its own sharpening centre, then the sharpening pass
     for (int c = 0; c < 3; ++c) {
         const uint8_t* f = F3 + c * plane;
-        box_rows_kernel<<<nb, kAppThreads, 0, s>>>(f, lpn, H, W, shc.w, rs);
-        sharpen_theta_kernel<<<nb, kAppThreads, 0, s>>>(f, lpn, rs, H, W, shc.w, th);
+        box_rows_kernel<<<grid2d(H, W), kAppThreads, 0, s>>>(f, lpn, H, W, shc.w, rs);
+        sharpen_theta_kernel<<<grid2d(H, W), kAppThreads, 0, s>>>(f, lpn, rs, H, W, shc.w, th);
         rc = cuda_status(cudaGetLastError());
         if (rc) return rc;
         rc = run_fused(ctx, f, pn, th, s1, H, W, shc.w, shc.N, b + o_go + c * gplane, out_is_f64, nullptr, s);
