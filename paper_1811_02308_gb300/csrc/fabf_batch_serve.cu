@@ -378,12 +378,21 @@ __global__ void next_pass_kernel(const void* prev_out, int out_f64, const float*
 {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const double g = out_f64 ? static_cast<const double*>(prev_out)[i]
-                             : (double)static_cast<const float*>(prev_out)[i];
-    double q = rint(g);                      // round half to even
-    q = q < 0.0 ? 0.0 : (q > 255.0 ? 255.0 : q);
-    if (!(g == g)) q = 0.0;                  // NaN (bad input) stays flagged by the status word
-    const uint8_t f = (uint8_t)q;
+    // round half to even and clamp; NaN (bad input, flagged by the status
+    // word) gives 0.  Float outputs round in binary32 (rintf(v) equals
+    // rint((double)v) for every float v; binary64 is the slow pipe here).
+    uint8_t f;
+    if (out_f64) {
+        const double g = static_cast<const double*>(prev_out)[i];
+        double q = rint(g);
+        q = q < 0.0 ? 0.0 : (q > 255.0 ? 255.0 : q);
+        f = (g == g) ? (uint8_t)q : (uint8_t)0;
+    } else {
+        const float g = static_cast<const float*>(prev_out)[i];
+        float q = rintf(g);
+        q = q < 0.0f ? 0.0f : (q > 255.0f ? 255.0f : q);
+        f = (g == g) ? (uint8_t)q : (uint8_t)0;
+    }
     img[i] = f;
     theta[i] = (float)f + zeta[i];
     sigma[i] = sigma[i] * decay;

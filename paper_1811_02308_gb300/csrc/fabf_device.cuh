@@ -191,6 +191,27 @@ struct PixelTrace {       // optional per-pixel export of every stage
 // Algorithm 1 from mu_k = M_k / (beta - alpha)^k on: the fit, the kernel
 // parameters, the integrals and the ratio, in binary64 (shared by the box and
 // the separable spatial kernels).
+// Eqs. (25), (28)-(29) from the fitted coefficients c (any common scale:
+// it cancels in F): t0, lambda, the integrals and the two sums, in the order
+// of Algorithm 1; returns F = T1 / T2.
+template <int N>
+__device__ __forceinline__ double fp64_ratio(const double (&c)[N + 1], int alpha, int d, float theta_f, float sigma_f,
+                                             double& t0, double& lam, double (&I)[N + 2], double& T1, double& T2)
+{
+    const double sg = (double)sigma_f;
+    t0 = ((double)theta_f - (double)alpha) / (double)d;
+    lam = (double)(d * d) / (2.0 * sg * sg);
+    integrals_fp64<N + 1>(lam, t0, I);
+    T1 = c[0] * I[1];
+    T2 = c[0] * I[0];
+#pragma unroll
+    for (int k = 2; k <= N + 1; ++k) {
+        T1 = fma(c[k - 1], I[k], T1);
+        T2 = fma(c[k - 1], I[k - 1], T2);
+    }
+    return T1 / T2;
+}
+
 template <int N>
 __device__ __forceinline__ double fabf_tail_fp64(const AinvTable& A, int alpha, int d,
                                                  const double (&mu)[(N < 1 ? 1 : N) + 1], float theta_f,
@@ -206,20 +227,8 @@ __device__ __forceinline__ double fabf_tail_fp64(const AinvTable& A, int alpha, 
         for (int k = 0; k <= N; ++k) acc = fma(A.v[N][n][k], mu[k], acc);
         c[n] = acc;
     }
-    // Eq. (25) and Algorithm 1.
-    const double sg = (double)sigma_f;
-    const double t0 = ((double)theta_f - (double)alpha) / (double)d;
-    const double lam = (double)(d * d) / (2.0 * sg * sg);
-    double I[N + 2];
-    integrals_fp64<N + 1>(lam, t0, I);
-    // Eq. (29), accumulated in the order of Algorithm 1.
-    double T1 = c[0] * I[1], T2 = c[0] * I[0];
-#pragma unroll
-    for (int k = 2; k <= N + 1; ++k) {
-        T1 = fma(c[k - 1], I[k], T1);
-        T2 = fma(c[k - 1], I[k - 1], T2);
-    }
-    double F = T1 / T2;
+    double t0, lam, I[N + 2], T1, T2;
+    double F = fp64_ratio<N>(c, alpha, d, theta_f, sigma_f, t0, lam, I, T1, T2);
     fallback = 0;
     if (!(T2 > 0.0) || !isfinite(F)) {   // fitted polynomial not positive enough
         F = mu[1] / mu[0];                // sigma -> infinity limit (spatial-kernel mean)
@@ -498,6 +507,33 @@ __device__ __forceinline__ void u63_to_ff(uint64_t v, float& hi, float& lo)
     lo = t - (hi - s2);
 }
 
+// Row n of the compensated fit c = A^{-1} mu from float-float (commonly
+// scaled) moments mu_k = muh[k] + mul[k]: the result as the unevaluated
+// pair s + comp.  The entries are compile-time constants after unrolling
+// (immediate operands); their low halves are zero for N <= 5 (entries <
+// 2^24), and those products are skipped.  The first product is exact as
+// s + comp.
+template <int N>
+__device__ __forceinline__ void compensated_fit_row(int n, const float (&muh)[(N < 1 ? 1 : N) + 1],
+                                                    const float (&mul)[(N < 1 ? 1 : N) + 1], float& s, float& comp)
+{
+    constexpr AinvSplitTable kA = make_ainv_split_table();
+    two_prod(kA.hi[N][n][0], muh[0], s, comp);
+    comp = fmaf(kA.hi[N][n][0], mul[0], comp);
+    if (kA.lo[N][n][0] != 0.0f) comp = fmaf(kA.lo[N][n][0], muh[0], comp);
+#pragma unroll
+    for (int k = 1; k <= N; ++k) {
+        const float ah = kA.hi[N][n][k], al = kA.lo[N][n][k];
+        float p, pe, t, te;
+        two_prod(ah, muh[k], p, pe);
+        two_sum(s, p, t, te);
+        s = t;
+        float e = fmaf(ah, mul[k], pe + te);
+        if (al != 0.0f) e = fmaf(al, muh[k], e);
+        comp += e;
+    }
+}
+
 // Compensated binary32 fit from float-float (commonly scaled) moments
 // mu_k = muh[k] + mul[k], then the binary32 tail.
 template <int N>
@@ -505,29 +541,12 @@ __device__ __forceinline__ float fabf_fit_tail_cfp32(const AinvSplitTable& A, co
                                                      const float (&mul)[(N < 1 ? 1 : N) + 1], int alpha, int d,
                                                      float theta_f, float sigma_f, int& fallback, bool& redo)
 {
-    // The entries are compile-time constants after unrolling (immediate
-    // operands); their low halves are zero for N <= 5 (entries < 2^24), and
-    // those products are skipped.  The first product is exact as s + comp.
     (void)A;
-    constexpr AinvSplitTable kA = make_ainv_split_table();
     float c[N + 1];
 #pragma unroll
     for (int n = 0; n <= N; ++n) {
         float s, comp;
-        two_prod(kA.hi[N][n][0], muh[0], s, comp);
-        comp = fmaf(kA.hi[N][n][0], mul[0], comp);
-        if (kA.lo[N][n][0] != 0.0f) comp = fmaf(kA.lo[N][n][0], muh[0], comp);
-#pragma unroll
-        for (int k = 1; k <= N; ++k) {
-            const float ah = kA.hi[N][n][k], al = kA.lo[N][n][k];
-            float p, pe, t, te;
-            two_prod(ah, muh[k], p, pe);
-            two_sum(s, p, t, te);
-            s = t;
-            float e = fmaf(ah, mul[k], pe + te);
-            if (al != 0.0f) e = fmaf(al, muh[k], e);
-            comp += e;
-        }
+        compensated_fit_row<N>(n, muh, mul, s, comp);
         c[n] = s + comp;
     }
     return fabf_tail_fp32<N>(c, [&] { return muh[1] / muh[0]; }, alpha, d, theta_f, sigma_f, fallback, redo);
@@ -564,6 +583,61 @@ __device__ __forceinline__ float fabf_pixel_cfp32(const AinvSplitTable& A, int a
         }
     }
     return fabf_fit_tail_cfp32<N>(A, muh, mul, alpha, d, theta_f, sigma_f, fallback, redo);
+}
+
+// The FP64 redo of FABF_CFP32 for the pixels its guard hands back, from
+// commonly scaled moments v_k < 2^63 (the scale cancels in Eq. (29)): the
+// same float-float moments and compensated fit as the binary32 tail, each
+// coefficient taken as its unevaluated pair s + comp in binary64 (the fit is
+// as accurate as if evaluated in twice the working precision), then the
+// binary64 integrals and ratio.  This skips the binary64 divisions and the
+// binary64 fit of fabf_pixel_fp64: about a third of the binary64
+// instructions, each of which occupies the narrow FP64 pipe for a whole warp.
+template <int N>
+__device__ __forceinline__ double fabf_redo_scaled(const uint64_t (&v)[(N < 1 ? 1 : N) + 1], int alpha, int d,
+                                                   float theta_f, float sigma_f, int& fallback)
+{
+    constexpr int K = N < 1 ? 1 : N;
+    float muh[K + 1], mul[K + 1];
+#pragma unroll
+    for (int k = 0; k <= K; ++k) u63_to_ff(v[k], muh[k], mul[k]);
+    double c[N + 1];
+#pragma unroll
+    for (int n = 0; n <= N; ++n) {
+        float sh, sc;
+        compensated_fit_row<N>(n, muh, mul, sh, sc);
+        c[n] = (double)sh + (double)sc;
+    }
+    double t0, lam, I[N + 2], T1, T2;
+    double F = fp64_ratio<N>(c, alpha, d, theta_f, sigma_f, t0, lam, I, T1, T2);
+    fallback = 0;
+    if (!(T2 > 0.0) || !isfinite(F)) {   // the sigma -> infinity limit, as fabf_tail_fp64
+        F = ((double)muh[1] + (double)mul[1]) / ((double)muh[0] + (double)mul[0]);
+        fallback = 1;
+    }
+    return (double)alpha + (double)d * F;
+}
+
+// The box path's redo: the exactly scaled moments mu'_k = M_k d^(K-k).
+template <int N>
+__device__ __forceinline__ double fabf_pixel_cfp32_redo(int alpha, int beta, int fi,
+                                                        const int64_t (&m)[(N < 1 ? 1 : N) + 1], float theta_f,
+                                                        float sigma_f, int& fallback)
+{
+    constexpr int K = N < 1 ? 1 : N;
+    fallback = 0;
+    if (alpha == beta) return (double)fi;
+    const int d = beta - alpha;
+    int64_t M[K + 1];
+    shifted_moments<K>(alpha, m, M);
+    uint64_t v[K + 1];
+    int64_t dp = 1;
+#pragma unroll
+    for (int k = K; k >= 0; --k) {
+        v[k] = (uint64_t)(M[k] * dp);
+        dp *= d;
+    }
+    return fabf_redo_scaled<N>(v, alpha, d, theta_f, sigma_f, fallback);
 }
 
 }  // namespace fabf

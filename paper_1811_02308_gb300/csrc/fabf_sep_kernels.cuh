@@ -198,6 +198,35 @@ __device__ __forceinline__ float sep_pixel_fp32(int alpha, int beta, int fi, con
     }
 }
 
+// The compensated form's FP64 redo (fabf_redo_scaled) from the separable
+// moments, scaled and shifted as in sep_pixel_fp32's compensated fit; with
+// all-ones taps this is the box path's redo bit for bit.
+template <int N>
+__device__ __forceinline__ double sep_pixel_cfp32_redo(int alpha, int beta, int fi,
+                                                       const u128 (&m)[(N < 1 ? 1 : N) + 1], float th, float sg,
+                                                       int& fallback)
+{
+    constexpr int K = N < 1 ? 1 : N;
+    fallback = 0;
+    if (alpha == beta) return (double)fi;
+    const int d = beta - alpha;
+    u128 M[K + 1];
+    sep_shifted_moments<K>(alpha, m, M);
+    u128 sc[K + 1];
+    uint64_t dp = 1;
+#pragma unroll
+    for (int k = K; k >= 0; --k) {
+        sc[k] = mul_u128_u64(M[k], dp);
+        dp *= (uint64_t)d;
+    }
+    const uint64_t top = (uint64_t)(sc[0] >> 64);
+    const int shift = top ? 65 - __clzll(top) : ((uint64_t)sc[0] >> 63 ? 1 : 0);   // sc[0] >> shift < 2^63
+    uint64_t v[K + 1];
+#pragma unroll
+    for (int k = 0; k <= K; ++k) v[k] = (uint64_t)(sc[k] >> shift);
+    return fabf_redo_scaled<N>(v, alpha, d, th, sg, fallback);
+}
+
 template <int N, int PREC>
 __device__ __forceinline__ void sep_tile(const CUtensorMap* tmap, const SepParams& P, int tx, int ty,
                                          uint8_t* smem, uint32_t& phase)
@@ -488,7 +517,9 @@ __device__ __forceinline__ void sep_tile(const CUtensorMap* tmap, const SepParam
                 u128 m[K + 1], M[K + 1];
                 stats(rr, x, alpha, beta, m, fi);
                 const long long pix = (long long)(y0 + r0 + rr) * J.W + (x0 + x);
-                const double g = sep_pixel_fp64<N>(alpha, beta, fi, m, J.theta[pix], J.sigma[pix], fb, nullptr, M);
+                const double g = PREC == kPrecCFP32
+                                     ? sep_pixel_cfp32_redo<N>(alpha, beta, fi, m, J.theta[pix], J.sigma[pix], fb)
+                                     : sep_pixel_fp64<N>(alpha, beta, fi, m, J.theta[pix], J.sigma[pix], fb, nullptr, M);
                 store(pix, g);
                 if (fb && P.n_fallback) atomicAdd(P.n_fallback, 1ull);
                 if (redo_count) atomicAdd(redo_count, 1ull);
