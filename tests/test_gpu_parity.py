@@ -322,10 +322,15 @@ def test_pinned_host_buffers_equal_device_path(ctx, H, W, w, N, f64, pitch_extra
         fabf.fabf_set_precision(ctx, prec)
         try:
             d = fabf.fabf_filter(ctx, dev(buf), dev(th), dev(s), w, N, out_is_f64=f64, pitch=pitch).cpu().numpy()
-            for img in (buf, torch.from_numpy(buf).pin_memory()):
+            for img in (buf, torch.from_numpy(buf).pin_memory(), dev(buf)):
                 pout = torch.full((H, W), -1.0, dtype=odt).pin_memory()
                 fabf.fabf_filter(ctx, img, pth, psg, w, N, out=pout, out_is_f64=f64, pitch=pitch)
+                torch.cuda.synchronize()
                 assert np.array_equal(pout.numpy(), d), (prec, np.abs(pout.numpy() - d).max())
+            # mixed: pinned maps with a pageable output take the staged paths
+            hout = np.full((H, W), -1.0, np.float64 if f64 else np.float32)
+            fabf.fabf_filter(ctx, buf, pth, psg, w, N, out=hout, out_is_f64=f64, pitch=pitch)
+            assert np.array_equal(hout, d)
         finally:
             fabf.fabf_set_precision(ctx, fabf.FABF_FP64)
 
