@@ -356,34 +356,42 @@ static int filter_host_pipelined(fabf_ctx* ctx, const uint8_t* img, const float*
 // device memory).  Synchronous: returns the kernels' status.  (Copying the
 // image in bands that start their tiles early measured no faster.)
 // ---------------------------------------------------------------------------
+int fabf::stage_image(fabf_ctx* ctx, const uint8_t* img, bool img_dev, int H, int W, size_t pitch, cudaStream_t s,
+                      const uint8_t** d_img, size_t* d_pitch)
+{
+    *d_img = img;
+    *d_pitch = pitch;
+    if (img_dev) return FABF_OK;
+    const size_t ipitch = ((size_t)W + 15) & ~(size_t)15;
+    const int rc = ensure_stage(ctx, ipitch * H);
+    if (rc) return rc;
+    const cudaError_t e = ipitch == pitch
+                              ? cudaMemcpyAsync(ctx->stage, img, pitch * H, cudaMemcpyHostToDevice, s)
+                              : cudaMemcpy2DAsync(ctx->stage, ipitch, img, pitch, W, H, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_status(e);
+    *d_img = static_cast<const uint8_t*>(ctx->stage);
+    *d_pitch = ipitch;
+    return FABF_OK;
+}
+
 static int filter_mapped(fabf_ctx* ctx, const uint8_t* img, bool img_dev, const float* k_th, const float* k_sg,
                          int H, int W, size_t pitch, int w, int N, void* k_out, int out_f64, cudaStream_t s)
 {
     std::lock_guard<std::mutex> staged(ctx->stage_lock);
-    const uint8_t* d_img = img;
-    size_t d_pitch = pitch;
-    cudaError_t e = cudaSuccess;
-    if (!img_dev) {
-        const size_t ipitch = ((size_t)W + 15) & ~(size_t)15;
-        const int rc = ensure_stage(ctx, ipitch * H);
-        if (rc) return rc;
-        e = ipitch == pitch ? cudaMemcpyAsync(ctx->stage, img, pitch * H, cudaMemcpyHostToDevice, s)
-                            : cudaMemcpy2DAsync(ctx->stage, ipitch, img, pitch, W, H, cudaMemcpyHostToDevice, s);
-        d_img = static_cast<const uint8_t*>(ctx->stage);
-        d_pitch = ipitch;
-    }
-    if (e == cudaSuccess) {
-        const int prec = ctx->precision;
-        FusedParams p;
-        std::memset(&p, 0, sizeof(p));
-        CUtensorMap tm;
-        const size_t smem = make_job(&p.job, &tm, d_img, d_pitch, k_th, k_sg, H, W, w, N, k_out, out_f64,
-                                     tile_rows_for(ctx, w, N, prec, H, W));
-        p.job.maps_host = 1;
-        p.status = ctx->d_status;
-        p.n_fallback = ctx->d_nfb;
-        e = launch_fused(prec, N, tm, p, dim3(p.job.tiles_x, p.job.tiles_y), smem, s);
-    }
+    const uint8_t* d_img = nullptr;
+    size_t d_pitch = 0;
+    const int src = stage_image(ctx, img, img_dev, H, W, pitch, s, &d_img, &d_pitch);
+    if (src) return src;
+    const int prec = ctx->precision;
+    FusedParams p;
+    std::memset(&p, 0, sizeof(p));
+    CUtensorMap tm;
+    const size_t smem = make_job(&p.job, &tm, d_img, d_pitch, k_th, k_sg, H, W, w, N, k_out, out_f64,
+                                 tile_rows_for(ctx, w, N, prec, H, W));
+    p.job.maps_host = 1;
+    p.status = ctx->d_status;
+    p.n_fallback = ctx->d_nfb;
+    const cudaError_t e = launch_fused(prec, N, tm, p, dim3(p.job.tiles_x, p.job.tiles_y), smem, s);
     if (e != cudaSuccess) {
         cudaStreamSynchronize(s);
         return cuda_status(e);

@@ -126,6 +126,11 @@ int read_and_clear_status(fabf_ctx* ctx, cudaStream_t s, int* status, uint64_t* 
 // Grow the context's staging buffer to at least `bytes`.
 int ensure_stage(fabf_ctx* ctx, size_t bytes);
 
+// A host image copied into the staging buffer (16-byte rows for TMA) on s,
+// a device image passed through; the caller holds stage_lock.
+int stage_image(fabf_ctx* ctx, const uint8_t* img, bool img_dev, int H, int W, size_t pitch, cudaStream_t s,
+                const uint8_t** d_img, size_t* d_pitch);
+
 // Run `launch(d_img, d_pitch, d_theta, d_sigma, d_out)` on device buffers.
 // All-device arguments are passed through (the call stays stream-ordered; the
 // status words are read by fabf_get_status).  Host buffers are staged through

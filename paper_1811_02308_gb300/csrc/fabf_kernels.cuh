@@ -166,6 +166,45 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+// theta / sigma rows of device memory go in 16-byte pieces when every piece
+// is aligned (W a multiple of 4 and both bases 16-byte aligned; tile columns
+// start at multiples of 64; W a multiple of 4 also keeps every piece of an
+// in-image start in the row).  Host memory is read in 4-byte pieces,
+// measured faster over the chip-to-chip link.
+__device__ __forceinline__ bool maps_in_16(const ImageJob& J)
+{
+    return !J.maps_host && (J.W & 3) == 0 &&
+           ((reinterpret_cast<uintptr_t>(J.theta) | reinterpret_cast<uintptr_t>(J.sigma)) & 15) == 0;
+}
+
+// theta and sigma of image rows Y0 .. Y0 + kChunk - 1, columns x0 .. x0 +
+// kTileW - 1, into s_maps[2][kChunk][kTileW] with cp.async (one committed
+// group; the caller waits with cp_async_wait_all before reading).
+__device__ __forceinline__ void prefetch_maps(const ImageJob& J, float* s_maps, int Y0, int x0, bool maps16)
+{
+    if (maps16) {
+        // 16-byte pieces: 2 maps x kChunk rows x kTileW / 4 pieces
+        for (int i = threadIdx.x; i < 2 * kChunk * (kTileW / 4); i += kThreads) {
+            const int which = i >= kChunk * (kTileW / 4) ? 1 : 0;
+            const int e = i - which * kChunk * (kTileW / 4);
+            const int rr = e / (kTileW / 4), x = 4 * (e - rr * (kTileW / 4));
+            const int Y = Y0 + rr, Xo = x0 + x;
+            if (Y < J.H && Xo < J.W)
+                cp_async16(s_maps + (which * kChunk + rr) * kTileW + x,
+                           (which ? J.sigma : J.theta) + (long long)Y * J.W + Xo);
+        }
+    } else {
+        for (int i = threadIdx.x; i < 2 * kChunk * kTileW; i += kThreads) {
+            const int which = i >= kChunk * kTileW ? 1 : 0;
+            const int e = i - which * kChunk * kTileW;
+            const int rr = e / kTileW, x = e - rr * kTileW;
+            const int Y = Y0 + rr, Xo = x0 + x;
+            if (Y < J.H && Xo < J.W) cp_async4(s_maps + i, (which ? J.sigma : J.theta) + (long long)Y * J.W + Xo);
+        }
+    }
+    cp_async_commit();
+}
+
 __device__ __forceinline__ void mbar_init(uint64_t* bar)
 {
     if (threadIdx.x == 0) {
@@ -444,13 +483,7 @@ __device__ __forceinline__ bool fabf_tile(const CUtensorMap* tmap, const ImageJo
     while ((2 << levels) <= 2 * w + 1) ++levels;                   // floor(log2(2w+1))
     const int span = 1 << levels;
     const bool lane_blocks = 2 * w + 1 >= 6;                       // else sparse-table levels
-    // theta / sigma rows of device memory in 16-byte pieces when every piece
-    // is aligned (W a multiple of 4 and both bases 16-byte aligned; x0 is a
-    // multiple of 64; W a multiple of 4 also keeps every piece of an in-image
-    // start in the row).  Host memory is read in 4-byte pieces, measured
-    // faster over the chip-to-chip link.
-    const bool maps16 = !J.maps_host && (J.W & 3) == 0 &&
-                        ((reinterpret_cast<uintptr_t>(J.theta) | reinterpret_cast<uintptr_t>(J.sigma)) & 15) == 0;
+    const bool maps16 = maps_in_16(J);
 
     for (int r0 = 0; r0 < TH; r0 += kChunk) {
         if (y0 + r0 >= J.H) break;                                 // uniform per CTA
@@ -459,28 +492,7 @@ __device__ __forceinline__ bool fabf_tile(const CUtensorMap* tmap, const ImageJo
         // The chunk's theta and sigma start on their way into shared memory;
         // the vertical phase covers their latency (HBM, or host memory over
         // the chip-to-chip link when the caller's buffers are host-mapped).
-        if (maps16) {
-            // 16-byte pieces: 2 maps x kChunk rows x kTileW / 4 pieces
-            for (int i = threadIdx.x; i < 2 * kChunk * (kTileW / 4); i += kThreads) {
-                const int which = i >= kChunk * (kTileW / 4) ? 1 : 0;
-                const int e = i - which * kChunk * (kTileW / 4);
-                const int rr = e / (kTileW / 4), x = 4 * (e - rr * (kTileW / 4));
-                const int Y = y0 + r0 + rr, Xo = x0 + x;
-                if (Y < J.H && Xo < J.W)
-                    cp_async16(s_maps + (which * kChunk + rr) * kTileW + x,
-                               (which ? J.sigma : J.theta) + (long long)Y * J.W + Xo);
-            }
-        } else {
-            for (int i = threadIdx.x; i < 2 * kChunk * kTileW; i += kThreads) {
-                const int which = i >= kChunk * kTileW ? 1 : 0;
-                const int e = i - which * kChunk * kTileW;
-                const int rr = e / kTileW, x = e - rr * kTileW;
-                const int Y = y0 + r0 + rr, Xo = x0 + x;
-                if (Y < J.H && Xo < J.W)
-                    cp_async4(s_maps + i, (which ? J.sigma : J.theta) + (long long)Y * J.W + Xo);
-            }
-        }
-        cp_async_commit();
+        prefetch_maps(J, s_maps, y0 + r0, x0, maps16);
         // 2a. Window sums of column c (threads c < Cb): store, then slide the
         //     window from [r, r+2w] to [r+1, r+2w+1].
         if (c < Cb) {

@@ -9,6 +9,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 
 #include "../../include/fabf.h"
 #include "fabf_internal.h"
@@ -70,12 +71,13 @@ static int make_taps(const uint32_t* taps, int r, SepTaps* T)
 
 static int run_sep(int prec, const SepTaps& T, const uint8_t* img, size_t pitch, const float* theta,
                    const float* sigma, int H, int W, int N, void* out, int out_f64, int TH, const SepDebug* dbg,
-                   unsigned* status, unsigned long long* nfb, cudaStream_t s)
+                   unsigned* status, unsigned long long* nfb, cudaStream_t s, int maps_host = 0)
 {
     SepParams p;
     std::memset(&p, 0, sizeof(p));
     CUtensorMap tm;
     (void)make_job(&p.job, &tm, img, pitch, theta, sigma, H, W, T.r, N, out, out_f64, TH);
+    p.job.maps_host = maps_host;
     p.taps = T;
     p.status = status;
     p.n_fallback = nfb;
@@ -116,11 +118,30 @@ int fabf_filter_sep(fabf_ctx* ctx, const uint8_t* img, const float* theta, const
     if (rc) return rc;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return FABF_ECUDA;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    const int prec = ctx->precision;
+    const int TH = sep_tile_rows(ctx, r, N, prec, H, W);
+    const PtrInfo pi = ptr_info(img), pt = ptr_info(theta), ps = ptr_info(sigma), po = ptr_info(out);
+    if (!(pt.device && ps.device && po.device) && pt.kptr && ps.kptr && po.kptr) {
+        // pinned host maps and output: read and written in place by the
+        // kernel over the chip-to-chip link; only a host image is copied
+        std::lock_guard<std::mutex> staged(ctx->stage_lock);
+        const uint8_t* d_img = nullptr;
+        size_t d_pitch = 0;
+        rc = stage_image(ctx, img, pi.device, H, W, pitch, s, &d_img, &d_pitch);
+        if (rc) return rc;
+        rc = run_sep(prec, T, d_img, d_pitch, static_cast<const float*>(pt.kptr), static_cast<const float*>(ps.kptr),
+                     H, W, N, const_cast<void*>(po.kptr), out_is_f64, TH, nullptr, ctx->d_status, ctx->d_nfb, s, 1);
+        if (rc) {
+            cudaStreamSynchronize(s);
+            return rc;
+        }
+        int st = FABF_OK;
+        rc = read_and_clear_status(ctx, s, &st, nullptr, nullptr);
+        return rc ? rc : st;
+    }
     return with_device_buffers(
         ctx, img, theta, sigma, H, W, pitch, out, out_is_f64, s,
         [&](const uint8_t* d_img, size_t d_pitch, const float* d_th, const float* d_sg, void* d_out) {
-            const int prec = ctx->precision;
-            const int TH = sep_tile_rows(ctx, r, N, prec, H, W);
             return run_sep(prec, T, d_img, d_pitch, d_th, d_sg, H, W, N, d_out, out_is_f64, TH, nullptr,
                            ctx->d_status, ctx->d_nfb, s);
         });

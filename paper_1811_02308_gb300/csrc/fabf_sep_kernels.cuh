@@ -73,7 +73,7 @@ __host__ __device__ inline size_t sep_smem_bytes(int N, int r, int Cb, int TH)
     const int K = N < 1 ? 1 : N;
     size_t tile = ((size_t)(TH + 2 * r) * Cb + 127) & ~(size_t)127;
     size_t mm = ((size_t)4 * kChunk * Cb + (size_t)2 * kChunk * kLaneTable + 15) & ~(size_t)15;
-    return 128 + tile + mm + (size_t)K * kChunk * Cb * 8 + kRedoBytes;
+    return 128 + tile + mm + (size_t)K * kChunk * Cb * 8 + kRedoBytes + kMapBytes;
 }
 
 // Correctly rounded (to nearest even) conversion of an unsigned 128-bit
@@ -252,6 +252,8 @@ __device__ __forceinline__ void sep_tile(const CUtensorMap* tmap, const SepParam
         vmin + (((size_t)4 * kChunk * Cb + (size_t)2 * kChunk * kLaneTable + 15) & ~(size_t)15));   // [K][kChunk][Cb]
     unsigned* redo_n = reinterpret_cast<unsigned*>(V + (size_t)K * kChunk * Cb);
     uint16_t* redo_list = reinterpret_cast<uint16_t*>(reinterpret_cast<uint8_t*>(redo_n) + 16);
+    float* s_maps = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(redo_n) + kRedoBytes);   // [2][kChunk][kTileW]
+    const bool maps16 = maps_in_16(J);
     unsigned long long* redo_count = P.n_fallback ? P.n_fallback + 1 : nullptr;
 
     if (J.use_tma) {
@@ -278,6 +280,9 @@ __device__ __forceinline__ void sep_tile(const CUtensorMap* tmap, const SepParam
     for (int r0 = 0; r0 < TH; r0 += kChunk) {
         if (y0 + r0 >= J.H) break;                                   // uniform per CTA
         if (threadIdx.x == 0) *redo_n = 0u;
+        // the chunk's theta and sigma into shared memory while the vertical
+        // phase runs (as in the box kernel)
+        prefetch_maps(J, s_maps, y0 + r0, x0, maps16);
         // 1a. Vertical min / max of the 8 windows [rr, rr + 2r] of column c.
         {
             const int c = threadIdx.x;
@@ -379,6 +384,7 @@ __device__ __forceinline__ void sep_tile(const CUtensorMap* tmap, const SepParam
             if constexpr (K >= 5) Vi[4 * plane] = a5;
             if constexpr (K >= 6) Vi[5 * plane] = a6;
         }
+        cp_async_wait_all();
         __syncthreads();
 
         // Window statistics of the pixel at chunk row rr, tile column x (the
@@ -454,7 +460,7 @@ __device__ __forceinline__ void sep_tile(const CUtensorMap* tmap, const SepParam
                     u128 m[K + 1];
                     stats(rr, x, alpha, beta, m, fi);
                     const long long pix = (long long)Y * J.W + Xo;
-                    const float th = J.theta[pix], sg = J.sigma[pix];
+                    const float th = s_maps[rr * kTileW + x], sg = s_maps[(kChunk + rr) * kTileW + x];
                     double g;
                     int fb = 0;
                     PixelTrace tr;
@@ -517,9 +523,9 @@ __device__ __forceinline__ void sep_tile(const CUtensorMap* tmap, const SepParam
                 u128 m[K + 1], M[K + 1];
                 stats(rr, x, alpha, beta, m, fi);
                 const long long pix = (long long)(y0 + r0 + rr) * J.W + (x0 + x);
-                const double g = PREC == kPrecCFP32
-                                     ? sep_pixel_cfp32_redo<N>(alpha, beta, fi, m, J.theta[pix], J.sigma[pix], fb)
-                                     : sep_pixel_fp64<N>(alpha, beta, fi, m, J.theta[pix], J.sigma[pix], fb, nullptr, M);
+                const float th = s_maps[rr * kTileW + x], sg = s_maps[(kChunk + rr) * kTileW + x];
+                const double g = PREC == kPrecCFP32 ? sep_pixel_cfp32_redo<N>(alpha, beta, fi, m, th, sg, fb)
+                                                    : sep_pixel_fp64<N>(alpha, beta, fi, m, th, sg, fb, nullptr, M);
                 store(pix, g);
                 if (fb && P.n_fallback) atomicAdd(P.n_fallback, 1ull);
                 if (redo_count) atomicAdd(redo_count, 1ull);

@@ -245,3 +245,24 @@ def test_sep_precision_forms_all_ones_equal_box(ctx, prec):
     finally:
         fabf.fabf_set_precision(ctx, fabf.FABF_FP64)
     assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("prec", [fabf.FABF_FP64, fabf.FABF_CFP32])
+def test_sep_pinned_host_buffers_equal_device_path(ctx, prec):
+    # pinned theta, sigma and out are read and written in place by the
+    # kernel (only a host image is copied); the result equals the device call
+    f, th, s = inputs(93, 171, 88)
+    taps = synth.gaussian_taps(2.0)
+    f64 = prec == fabf.FABF_FP64
+    odt = torch.float64 if f64 else torch.float32
+    fabf.fabf_set_precision(ctx, prec)
+    try:
+        d = fabf.fabf_filter_sep(ctx, dev(f), dev(th), dev(s), taps, 5, out_is_f64=f64).cpu().numpy()
+        pth, psg = torch.from_numpy(th).pin_memory(), torch.from_numpy(s).pin_memory()
+        for img in (f, torch.from_numpy(f).pin_memory(), dev(f)):
+            pout = torch.full((93, 171), -1.0, dtype=odt).pin_memory()
+            fabf.fabf_filter_sep(ctx, img, pth, psg, taps, 5, out=pout, out_is_f64=f64)
+            torch.cuda.synchronize()
+            assert np.array_equal(pout.numpy(), d)
+    finally:
+        fabf.fabf_set_precision(ctx, fabf.FABF_FP64)
