@@ -79,8 +79,9 @@ def test_sharpen_pass_matches_oracle(ctx, oracle_mod):
     assert rel(g, ref).max() <= RTOL_G
 
 
-def test_texture_pipeline_matches_oracle(ctx, oracle_mod):
-    f, _, _ = synth.make_inputs(80, 144, 31, n_blobs=20)
+@pytest.mark.parametrize("H,W", [(80, 144), (1, 57), (41, 1)])
+def test_texture_pipeline_matches_oracle(ctx, oracle_mod, H, W):
+    f, _, _ = synth.make_inputs(H, W, 31, n_blobs=20)
     g = fabf.fabf_texture_filter(ctx, dev(f), texture_cfg(w=4, N=5)).cpu().numpy()
     st, _ = fabf.fabf_get_status(ctx)
     assert st == fabf.FABF_OK

@@ -80,7 +80,7 @@ def test_filter_rgb_binary32_output(ctx, oracle_mod):
     assert np.abs(g.astype(np.float64) - ref).max() <= 255 * 2.0 ** -24 + 1e-9
 
 
-@pytest.mark.parametrize("H,W,sw,sN", [(80, 144, None, None), (37, 61, 2, 6)])
+@pytest.mark.parametrize("H,W,sw,sN", [(80, 144, None, None), (37, 61, 2, 6), (1, 45, None, None), (29, 1, 3, 4)])
 def test_texture_rgb_matches_oracle(ctx, oracle_mod, H, W, sw, sN):
     rgb = synth.make_rgb(H, W, 31 + W, n_blobs=15)
     g = fabf.fabf_texture_filter_rgb(ctx, dev(rgb), texture_cfg(sw=sw, sN=sN)).cpu().numpy()
