@@ -223,9 +223,11 @@ int fabf_filter_noalloc(const uint8_t* img, const float* theta, const float* sig
  *   taps  HOST array of 2r+1 integers read during the call: taps[t] >= 0,
  *         taps[r] >= 1, sum <= 65535 (so every moment is an exact integer
  *         below 2^81, summed in 64/128-bit arithmetic);
- *   r     1..40;  N 0..6;  the other arguments, the pointer kinds, the
+ *   r     1..40;  N 0..6;  the other arguments, the pointer kinds (pinned
+ *         theta, sigma and out are read and written in place), the
  *         synchronisation and the status reporting are those of fabf_filter.
- * Always computed in binary64 (the context's precision is not used).
+ * Computed in the context's precision (fabf_set_precision); the binary32
+ * forms shift the 128-bit scaled moments right by one common amount.
  * Errors: FABF_EINVAL (NULL pointers, taps[r] == 0, bad sizes),
  * FABF_EUNSUPPORTED (r > 40, N > 6, tap sum > 65535), FABF_ECUDA. */
 int fabf_filter_sep(fabf_ctx* ctx, const uint8_t* img, const float* theta, const float* sigma,
