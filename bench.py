@@ -791,7 +791,10 @@ def main():
     e2e_s = (time.perf_counter() - t0) / n_e2e
     fabf.fabf_set_precision(ctx, 0)
     e2e = {"value": ws * npix / e2e_s / 1e6, "unit": "Mpix/s",
-           "h2d_bytes_per_step": npix * (1 + 4 + 4), "d2h_bytes_per_step": npix * (8 if best == 0 else 4)}
+           "h2d_bytes_per_step": npix * (1 + 4 + 4), "d2h_bytes_per_step": npix * (8 if best == 0 else 4),
+           "path": "fabf_filter on pinned host buffers: the image is copied to the device, the kernel reads "
+                   "theta and sigma and writes the output in host memory over NVLink-C2C; synchronous call, "
+                   "wall clock"}
 
     line = {"metric": METRIC, "value": head["value"], "unit": "Mpix/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": forms[best]["total_ms"] / args.steps,
