@@ -121,3 +121,29 @@ def test_precision_enum_bounds_without_gpu(lib):
     cfg = fabf._Config(0, 0, -1, 0, None)
     assert lib.fabf_create(C.byref(cfg), C.byref(h)) == fabf.FABF_EINVAL
     assert lib.fabf_set_precision(None, fabf.FABF_CFP32) == fabf.FABF_EINVAL
+
+
+def test_colour_and_application_argument_checks_without_gpu(lib):
+    # argument checks that return before any CUDA call
+    null = C.c_void_p(0)
+    buf = np.zeros(64, np.uint8)
+    out = np.zeros(64, np.float64)
+    assert lib.fabf_luma(null, buf.ctypes.data, 4, 4, 12, buf.ctypes.data, 4, 0) == fabf.FABF_EINVAL
+    assert lib.fabf_filter_rgb(null, buf.ctypes.data, 0, out.ctypes.data, 4, 4, 12, 2, 3, out.ctypes.data, 1,
+                               0) == fabf.FABF_EINVAL
+    tx = fabf.TextureCfg(3, 5, 2, 1.0, 8.0, 5.0, 60.0, 0.8, fabf.SharpenCfg(3, 5, 1.0, 10.0, 10.0, 40.0))
+    assert lib.fabf_texture_filter_rgb(null, buf.ctypes.data, 4, 4, 12, C.byref(tx), out.ctypes.data, 1,
+                                       0) == fabf.FABF_EINVAL
+    sh = fabf.SharpenCfg(3, 5, 1.0, 10.0, 10.0, 40.0)
+    assert lib.fabf_sharpen(null, buf.ctypes.data, 4, 4, 4, C.byref(sh), out.ctypes.data, 1, 0) == fabf.FABF_EINVAL
+    assert lib.fabf_texture_filter(null, buf.ctypes.data, 4, 4, 4, C.byref(tx), out.ctypes.data, 1,
+                                   0) == fabf.FABF_EINVAL
+
+
+def test_colour_binding_rejects_bad_shapes():
+    torch = pytest.importorskip("torch")
+    with pytest.raises(ValueError):
+        fabf._rgb_dims(torch.zeros((4, 4, 2), dtype=torch.uint8))
+    with pytest.raises(ValueError):
+        fabf._rgb_dims(torch.zeros((4, 4, 3), dtype=torch.float32))
+    assert fabf._rgb_dims(torch.zeros((4, 5, 3), dtype=torch.uint8)) == (4, 5, 15)
