@@ -253,7 +253,7 @@ def reference_arm(args):
     pool = OraclePool()
     try:
         # each step a bounded sample: the whole run stays near a minute
-        per_step_s = max(0.05, min(4.0, 60.0 / max(1, args.steps + args.warmup)))
+        per_step_s = max(0.05, min(4.0, args.ref_seconds / max(1, args.steps + args.warmup)))
         n_core = pool.calibrate(per_step_s, 3)
         for i in range(args.warmup):
             pool.run(n_core, 10 + i)
@@ -672,6 +672,8 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="fabf", choices=["fabf", "reference"])
+    ap.add_argument("--ref-seconds", type=float, default=60.0,
+                    help="--impl reference: about how long warm-up plus timed steps take in all")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--traffic-bytes", type=float, default=None,
                     help="DRAM bytes per launch of the fused kernel from an ncu capture")
