@@ -46,10 +46,9 @@ WORKLOAD = ("1920x1080 uint8 synthetic (200 blobs, 4 step edges, noise 10), box 
 # until it is re-captured.  The float output of a launch stays in the 126 MB
 # L2 when the kernel ends, so the figure is the 9 B/px of compulsory reads.
 NCU_TRAFFIC_BYTES = 18.76e6        # FP64 form kernel (8-row tiles)
+NCU_TRAFFIC_BYTES_FP64FIT = None   # FP64-fit kernel (not captured)
 NCU_TRAFFIC_BYTES_CFP32 = 19.40e6  # compensated FP32 kernel (8-row tiles, 4 CTAs per SM)
 NCU_TRAFFIC_BYTES_SEP = 18.77e6    # separable (Gaussian) kernel, rho = 5, compensated FP32
-SM_COUNT, SM_MAX_MHZ = 152, 2070.0
-FP64_FLOP_PER_SM_CLK = 4.0        # 2 DFMA per clock per SM (nominal 1.25 TFLOP/s FP64)
 FORM_NAMES = {0: "fp64", 1: "fp64fit_fp32rec", 2: "cfp32"}
 FORMS_BY_NAME = {v: k for k, v in FORM_NAMES.items()}
 
@@ -67,17 +66,64 @@ def fp64_flops_per_pixel(N: int, form: int = 0) -> float:
     return (N + 1) + 2 * (N + 1) ** 2 + 5 + 95 + 4 * N + 4 * (N + 1) + 3
 
 
-def fp32_flops_per_pixel(N: int) -> float:
-    """Algorithmic binary32 work of one non-flat pixel of the compensated
-    form (FMA = 2 flops, erf/exp = 20): float-float moments 20 (N+1),
-    compensated fit 14 (N+1)^2 (TwoProduct 3, TwoSum 6, cross terms 3,
-    accumulation 2), t0 and lambda 6, I_0 and I_1 with 2 erf + 2 exp 90,
-    recursion 4N, T1/T2 and the guard's |c||I| sums 8(N+1), estimate and
-    ratio 12."""
+def method_flops_per_pixel(N: int) -> float:
+    """The method's own arithmetic per non-flat pixel, whatever the precision
+    it runs in (Algorithm 1: mu scaling, the fit, t0 and lambda, the four
+    transcendentals, the recursion, T1/T2 and the ratio) -- the FP64 form's
+    count above.  The binary32 forms' roofline divides this by the FP32
+    peak; their extra compensation work is reported beside it."""
+    return fp64_flops_per_pixel(N, 0)
+
+
+def cfp32_executed_flops_per_pixel(N: int) -> float:
+    """Binary32 work the compensated form executes per non-flat pixel (FMA =
+    2 flops, erf/exp = 20): float-float moments 20 (N+1), compensated fit
+    14 (N+1)^2 (TwoProduct 3, TwoSum 6, cross terms 3, accumulation 2), t0
+    and lambda 6, I_0 and I_1 with 2 erf + 2 exp 90, recursion 4N, T1/T2 and
+    the guard's |c||I| sums 8(N+1), estimate and ratio 12."""
     return 20 * (N + 1) + 14 * (N + 1) ** 2 + 6 + 90 + 4 * N + 8 * (N + 1) + 12
 
 
-FP32_FLOP_PER_SM_CLK = 256.0      # 128 FP32 lanes x FMA
+# Warp instructions the compensated kernel executes per pixel on this
+# workload (smsp__inst_executed.sum / pixels, one ncu capture of the launch
+# bench.py times; profiles/); None whenever the kernel changes until it is
+# re-captured.
+NCU_INST_PER_PIXEL_CFP32 = None
+
+# This GPU's arithmetic pipe peaks, measured at start-up by fabf_pipe_peaks
+# (CUDA events around FP64 / FP32 FMA, INT32 IMAD and MUFU loops).
+PEAKS = {}
+PEAK_SOURCE = ("measured on this GPU in this run (fabf_pipe_peaks: best of 3 event-timed launches of 8 "
+               "independent FMA chains per thread, 4 x 256-thread CTAs per SM)")
+
+
+def alu_roofline(prec: int, N: int, npix: int, kern_ms: float, traffic=None) -> dict:
+    """Roofline of one launch of the form `prec`: the method's algorithmic
+    flops per pixel times the pixels, over the launch's CUDA-event time,
+    against the measured peak of the pipe the form runs its arithmetic on
+    (FP64 for the FP64 and FP64-fit forms, FP32 FMA for the compensated
+    form, whose compensation work is reported beside it, not counted)."""
+    if prec == 2:
+        fl, pipe, peak = method_flops_per_pixel(N), "fp32", PEAKS["fp32_tflops"]
+    else:
+        fl, pipe, peak = fp64_flops_per_pixel(N, prec), "fp64", PEAKS["fp64_tflops"]
+    a = fl * npix / (kern_ms / 1e3) / 1e12
+    r = {"bound": "alu", "pipe": pipe, "achieved": a, "peak": peak, "unit": "TFLOP/s", "frac": a / peak,
+         "traffic": traffic, "peak_source": PEAK_SOURCE, "flops_per_pixel": fl, "kernel_ms": kern_ms,
+         "form": FORM_NAMES[prec]}
+    if prec == 2:
+        ex = cfp32_executed_flops_per_pixel(N)
+        r["executed_flops_per_pixel"] = ex
+        r["executed_tflops"] = ex * npix / (kern_ms / 1e3) / 1e12
+        # instruction issue: one warp instruction per clock per scheduler, the
+        # rate the FP32 FMA loop reaches (one FFMA warp instruction per clock)
+        issue_peak = PEAKS["fp32_tflops"] / 2.0 / 32.0          # T warp instructions / s
+        r["issue"] = {"peak_t_warp_inst_per_s": issue_peak,
+                      "inst_per_pixel": NCU_INST_PER_PIXEL_CFP32}
+        if NCU_INST_PER_PIXEL_CFP32:
+            ach = NCU_INST_PER_PIXEL_CFP32 * npix / (kern_ms / 1e3) / 1e12
+            r["issue"].update({"achieved_t_warp_inst_per_s": ach, "frac": ach / issue_peak})
+    return r
 
 
 def max_over_ranks(ms: float, device) -> float:
@@ -447,7 +493,6 @@ def run_gaussian(R, slots, steps, rhos=(3.0, 5.0), N=NDEG):
     from paper_1811_02308_gb300 import synth
     f0, th0, s0, _ = slots[0][0]
     npix = H_ * W_
-    peak = SM_COUNT * SM_MAX_MHZ * 1e6 * FP64_FLOP_PER_SM_CLK / 1e12
     out = {}
     for rho in rhos:
         taps = synth.gaussian_taps(rho)
@@ -480,18 +525,8 @@ def run_gaussian(R, slots, steps, rhos=(3.0, 5.0), N=NDEG):
             row = {"value": npix * steps / (total_ms / 1e3) / 1e6, "unit": "Mpix/s", "kernel_ms": kern_ms,
                    "status": st, "psnr_vs_bruteforce_db": psnr(g, bf),
                    "fp64_redo_frac": nredo / ((steps + 3) * npix)}
-            if prec == 2 and rho == 5.0:
-                fl32 = fp32_flops_per_pixel(N)
-                a32 = fl32 * npix / (kern_ms / 1e3) / 1e12
-                peak32 = SM_COUNT * SM_MAX_MHZ * 1e6 * FP32_FLOP_PER_SM_CLK / 1e12
-                row["roofline"] = {"bound": "alu", "pipe": "fp32", "achieved": a32, "peak": peak32,
-                                   "unit": "TFLOP/s", "frac": a32 / peak32, "traffic": NCU_TRAFFIC_BYTES_SEP,
-                                   "flops_per_pixel": fl32}
-            fl = fp64_flops_per_pixel(N, prec)
-            if fl > 0:
-                a = fl * npix / (kern_ms / 1e3) / 1e12
-                row["fp64_roofline"] = {"achieved": a, "peak": peak, "unit": "TFLOP/s", "frac": a / peak,
-                                        "flops_per_pixel": fl}
+            row["roofline"] = alu_roofline(prec, N, npix, kern_ms,
+                                           NCU_TRAFFIC_BYTES_SEP if (prec == 2 and rho == 5.0) else None)
             forms[FORM_NAMES[prec]] = row
         fabf.fabf_set_precision(ctx, 0)
         best = "fp64"
@@ -711,6 +746,7 @@ def main():
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     build.build()
+    PEAKS.update(fabf.fabf_pipe_peaks(local))
     ctx = fabf.Context(device=local)
     dev = torch.device("cuda", local)
     R = Runner(torch, fabf, ctx, dev)
@@ -791,7 +827,6 @@ def main():
                                                                   use_f64=u, stream=R.sh), 3, 1)
         bf_ms["fp64" if use64 else "fp32"] = ms / 3
 
-    peak = SM_COUNT * SM_MAX_MHZ * 1e6 * FP64_FLOP_PER_SM_CLK / 1e12
     form_rows = {}
     for prec, r in forms.items():
         n_calls = args.steps + args.warmup
@@ -800,11 +835,8 @@ def main():
                "fallback_frac": r["fallback"] / (n_calls * npix),
                "fp64_redo_frac": r["redo"] / (n_calls * npix)}
         row.update(acc[prec])
-        fl = fp64_flops_per_pixel(NDEG, prec)
-        if fl > 0:
-            a = fl * npix / (r["kernel_ms"] / 1e3) / 1e12
-            row["fp64_roofline"] = {"achieved": a, "peak": peak, "unit": "TFLOP/s", "frac": a / peak,
-                                    "flops_per_pixel": fl}
+        row["roofline"] = alu_roofline(prec, NDEG, npix, r["kernel_ms"],
+                                       (NCU_TRAFFIC_BYTES, NCU_TRAFFIC_BYTES_FP64FIT, NCU_TRAFFIC_BYTES_CFP32)[prec])
         form_rows[FORM_NAMES[prec]] = row
     # headline: fastest form as accurate as FP64 (PSNR vs brute force within 0.01 dB)
     best = 0
@@ -814,25 +846,9 @@ def main():
         if ok and form_rows[FORM_NAMES[prec]]["value"] > form_rows[FORM_NAMES[best]]["value"]:
             best = prec
     head = form_rows[FORM_NAMES[best]]
-    fl = fp64_flops_per_pixel(NDEG, best)
-    kern_ms = forms[best]["kernel_ms"]
-    if fl > 0:
-        achieved = fl * npix / (kern_ms / 1e3) / 1e12
-        roofline = {"bound": "alu", "pipe": "fp64", "achieved": achieved, "peak": peak,
-                    "unit": "TFLOP/s", "frac": achieved / peak,
-                    "traffic": args.traffic_bytes if args.traffic_bytes is not None else (
-                        NCU_TRAFFIC_BYTES if best == 0 else None),
-                    "peak_source": "nominal FP64 (152 SM x 4 flop/clk x 2070 MHz)",
-                    "flops_per_pixel": fl, "kernel_ms": kern_ms, "form": FORM_NAMES[best]}
-    else:
-        fl32 = fp32_flops_per_pixel(NDEG)
-        achieved = fl32 * npix / (kern_ms / 1e3) / 1e12
-        peak32 = SM_COUNT * SM_MAX_MHZ * 1e6 * FP32_FLOP_PER_SM_CLK / 1e12
-        roofline = {"bound": "alu", "pipe": "fp32", "achieved": achieved, "peak": peak32,
-                    "unit": "TFLOP/s", "frac": achieved / peak32,
-                    "traffic": args.traffic_bytes if args.traffic_bytes is not None else NCU_TRAFFIC_BYTES_CFP32,
-                    "peak_source": "nominal FP32 FMA (152 SM x 256 flop/clk x 2070 MHz)",
-                    "flops_per_pixel": fl32, "kernel_ms": kern_ms, "form": FORM_NAMES[best]}
+    roofline = dict(head["roofline"])
+    if args.traffic_bytes is not None:
+        roofline["traffic"] = args.traffic_bytes
 
     # ---- end to end through the C ABI with pinned host buffers --------------
     f, th, s = host[0]
@@ -872,6 +888,7 @@ def main():
                        "precision": FORM_NAMES[best], "parallelism": "replicas" if ws > 1 else "single",
                        "l2": "inputs rotate over 8 slots of 34 MB (> 126 MB L2)"},
             "plain_fp64": form_rows["fp64"], "forms": form_rows, "roofline": roofline, "e2e": e2e,
+            "pipe_peaks": dict(PEAKS, source=PEAK_SOURCE),
             "clocks": clk.summary(), "gpu_launches": args.steps,
             "bruteforce_gpu": {k: {"ms_per_frame": v, "value": npix / (v / 1e3) / 1e6, "unit": "Mpix/s"}
                                for k, v in bf_ms.items()}}

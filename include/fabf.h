@@ -132,7 +132,7 @@ int fabf_get_status(fabf_ctx* ctx, void* cuda_stream, int* status, uint64_t* n_f
 
 /* As fabf_get_status, and *n_fp64_redo (may be NULL) receives the number of
  * pixels the binary32 precision forms recomputed on the FP64 path because
- * their own error estimate exceeded 0.02 gray levels (or T2 <= 0, or the
+ * their own error estimate exceeded 0.25 gray levels (or T2 <= 0, or the
  * binary32 integrals were in a regime where they lose digits). */
 int fabf_get_status_ex(fabf_ctx* ctx, void* cuda_stream, int* status, uint64_t* n_fallback,
                        uint64_t* n_fp64_redo);
@@ -142,8 +142,13 @@ int fabf_get_status_ex(fabf_ctx* ctx, void* cuda_stream, int* status, uint64_t* 
  * counter.  The launch (counter reset + kernel) is captured once in a CUDA
  * graph and replayed by later calls with the same request array and
  * precision; tile shapes come from the autotuner when the context has
- * autotune on.  Device pointers only (FABF_EINVAL otherwise); stream-ordered
- * on cuda_stream like fabf_filter, data errors via fabf_get_status.
+ * autotune on.  Up to 4 request sets keep their own graph, job table and
+ * work counter (least recently used evicted), so calls may alternate sets
+ * on any stream without waiting: a replay of a set is ordered after that
+ * set's previous replay, and a set's table is rewritten only after its last
+ * replay has finished (the call then waits for it on the host).  Device
+ * pointers only (FABF_EINVAL otherwise); stream-ordered on cuda_stream like
+ * fabf_filter, data errors via fabf_get_status.
  * Errors: FABF_EINVAL, FABF_EUNSUPPORTED, FABF_ENOMEM, FABF_ECUDA. */
 int fabf_filter_batch(fabf_ctx* ctx, const fabf_request* reqs, int n, void* cuda_stream);
 
@@ -190,19 +195,22 @@ const char* fabf_status_str(int status);
 /* Allocation-free variant of fabf_filter (the paper has no counterpart).
  * For callers that must not allocate device memory -- a real-time thread
  * that cannot absorb cudaMalloc's device-wide synchronisation, a plugin
- * whose host framework owns every allocation, a thread in the middle of a
- * stream capture -- and therefore cannot create a context.  It runs the same
+ * whose host framework owns every allocation -- and therefore cannot create
+ * a context.  It runs the same
  * FP64 fused kernel as fabf_filter on the caller's device buffers and needs
  * no context; the kernel's scratch (its status word and fallback-pixel
  * counter, 16 bytes) lives in a 256-byte array compiled into the library,
  * which every GPU that loads the library holds until the process exits.
- *   - img, theta, sigma, out must be device pointers (FABF_EINVAL otherwise:
- *     host buffers would need device staging).  Layout, limits and the other
- *     errors as fabf_filter; the GPU is the calling thread's current device.
+ *   - img, theta, sigma, out must be device memory of the calling thread's
+ *     current device (FABF_EINVAL otherwise: host buffers would need device
+ *     staging, and another GPU's buffers are not read).  Layout, limits and
+ *     the other errors as fabf_filter.
  *   - The first call on a device looks up the array's device address (once
- *     per device); make that first call before any stream capture.
+ *     per device, cached until the process exits); the library must not be
+ *     used across a cudaDeviceReset of that device.
  *   - The call clears the scratch, enqueues the kernel on cuda_stream, then
- *     waits for the stream and returns FABF_OK, FABF_EINVAL (bad per-pixel
+ *     waits for the stream (so it must not be made while a stream capture
+ *     is active) and returns FABF_OK, FABF_EINVAL (bad per-pixel
  *     data) or FABF_ETIMEOUT; *n_fallback (may be NULL) receives the number
  *     of pixels that took the box-mean fallback.
  *   - All calls share the one array: calls whose work overlaps on the GPU
@@ -336,6 +344,25 @@ int fabf_hilbert_inverse(int N, int64_t* out);
 /* Dynamic shared memory (bytes) one CTA of the fused kernel needs for
  * (w, N) with the tallest tile (64 output rows). */
 int fabf_fused_smem_bytes(int w, int N, size_t* bytes);
+
+/* ---- measurement ---------------------------------------------------------- */
+
+/* Arithmetic pipe peaks of the calling thread's current GPU, measured with
+ * CUDA events on the legacy default stream (the paper has no counterpart:
+ * these are the denominators of the rooflines the filter's kernels are
+ * quoted against, since the filter is bound by arithmetic, not HBM).  Each
+ * figure is the best of 3 timed launches of a kernel that runs 8
+ * independent dependency chains per thread on 4 x 256-thread CTAs per SM.
+ *   out[0] FP64 fused multiply-add, TFLOP/s (an FMA counts 2 flops)
+ *   out[1] FP32 fused multiply-add, TFLOP/s
+ *   out[2] INT32 multiply-add, T ops/s
+ *   out[3] MUFU base-2 exponential (ex2.approx.f32), T ops/s
+ *   out[4] SM clock seen during the FP64 run, MHz (clock64 cycles of one CTA
+ *          over the launch's event time)
+ *   out[5] number of SMs
+ * Synchronous; allocates and frees 2 KB of device memory.  Errors:
+ * FABF_EINVAL (out NULL), FABF_ENOMEM, FABF_ECUDA. */
+int fabf_pipe_peaks(double* out);
 
 /* ---- test entry points (device pointers only, synchronous) -------------- */
 

@@ -25,6 +25,7 @@ SOURCES = [
     "fabf_sep_p1.cu",
     "fabf_sep_p2.cu",
     "fabf_apps.cu",
+    "fabf_peaks.cu",
 ]
 HEADERS = ["fabf_device.cuh", "fabf_kernels.cuh", "fabf_launch.cuh", "fabf_internal.h", "fabf_sep_kernels.cuh"]
 

@@ -141,8 +141,9 @@ static int steady_tile_rows(fabf_ctx* ctx, int w, int N, int prec)
         bool ok = true;
         for (int rep = 0; rep < 4 && ok; ++rep) {
             cudaEventRecord(e0, s);
-            ok = run_fused_prec(ctx, prec, t->img, kTuneW, t->theta, t->sigma, kTuneH, kTuneW, w, N, t->out, 1,
-                                TH, nullptr, t->status, t->nfb, s) == FABF_OK;
+            // the form's own output type: float64 for FP64, float32 otherwise
+            ok = run_fused_prec(ctx, prec, t->img, kTuneW, t->theta, t->sigma, kTuneH, kTuneW, w, N, t->out,
+                                prec == kPrecFP64 ? 1 : 0, TH, nullptr, t->status, t->nfb, s) == FABF_OK;
             cudaEventRecord(e1, s);
             if (cudaEventSynchronize(e1) != cudaSuccess) ok = false;
             float m = 0.0f;
@@ -201,15 +202,32 @@ int tile_rows_for(fabf_ctx* ctx, int w, int N, int prec, int H, int W)
 // ===========================================================================
 // Batch: one persistent launch over all tiles of n images, captured once in
 // a CUDA graph and replayed while the request set stays the same.
+//
+// Each request set that is replayed keeps its own graph, job table, tensor
+// maps and work counter (up to kBatchGraphs sets, least recently used
+// evicted), so a caller may alternate sets on a stream without waiting: no
+// replay ever reads a table that a later call rewrites.  An event recorded
+// after each replay orders the next replay of the same set after it (on any
+// stream), and a set's table is rewritten only after its last replay is done.
 // ===========================================================================
-struct BatchState {
+constexpr int kBatchGraphs = 4;
+
+struct BatchGraph {
     ImageJob* d_jobs = nullptr;
     CUtensorMap* d_tmaps = nullptr;
     unsigned long long* d_counter = nullptr;
     int cap = 0;
-    cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t exec = nullptr;
+    cudaEvent_t done = nullptr;       // recorded after the set's last replay
+    bool launched = false;
+    unsigned long long last_use = 0;
     std::vector<unsigned char> key;
+};
+
+struct BatchState {
+    BatchGraph g[kBatchGraphs];
+    cudaStream_t cap_stream = nullptr;
+    unsigned long long tick = 0;
     int launches = 0;       // graph replays (for tests)
     int captures = 0;       // graph (re)builds
 };
@@ -217,18 +235,29 @@ struct BatchState {
 void batch_destroy(BatchState* b)
 {
     if (!b) return;
-    if (b->exec) cudaGraphExecDestroy(b->exec);
+    for (BatchGraph& G : b->g) {
+        if (G.done) cudaEventSynchronize(G.done);
+        if (G.exec) cudaGraphExecDestroy(G.exec);
+        if (G.done) cudaEventDestroy(G.done);
+        cudaFree(G.d_jobs);
+        cudaFree(G.d_tmaps);
+        cudaFree(G.d_counter);
+    }
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
-    cudaFree(b->d_jobs);
-    cudaFree(b->d_tmaps);
-    cudaFree(b->d_counter);
     delete b;
 }
 
-static int batch_build(fabf_ctx* ctx, const fabf_request* reqs, int n)
+static int batch_build(fabf_ctx* ctx, BatchState* b, BatchGraph& G, const fabf_request* reqs, int n)
 {
-    BatchState* b = ctx->batch;
     const int prec = ctx->precision;
+    // The set this slot held may still be running: wait for its last replay
+    // before its table is rewritten.
+    if (G.launched) {
+        cudaError_t e = cudaEventSynchronize(G.done);
+        if (e != cudaSuccess) return cuda_status(e);
+        G.launched = false;
+    }
+    G.key.clear();
     // Heavier images first (higher N, larger w): their tiles are popped first,
     // which shortens the tail of the persistent launch.
     std::vector<int> order(n);
@@ -251,28 +280,33 @@ static int batch_build(fabf_ctx* ctx, const fabf_request* reqs, int n)
         smem = std::max(smem, sm);
     }
     cudaError_t e = cudaSuccess;
-    if (n > b->cap) {
-        cudaFree(b->d_jobs);
-        cudaFree(b->d_tmaps);
-        b->d_jobs = nullptr;
-        b->d_tmaps = nullptr;
-        b->cap = 0;
-        e = cudaMalloc(&b->d_jobs, sizeof(ImageJob) * n);
-        if (e == cudaSuccess) e = cudaMalloc(&b->d_tmaps, sizeof(CUtensorMap) * n);
+    if (!G.d_counter) e = cudaMalloc(&G.d_counter, 256);
+    if (e == cudaSuccess && !G.done) e = cudaEventCreateWithFlags(&G.done, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (n > G.cap) {
+        cudaFree(G.d_jobs);
+        cudaFree(G.d_tmaps);
+        G.d_jobs = nullptr;
+        G.d_tmaps = nullptr;
+        G.cap = 0;
+        e = cudaMalloc(&G.d_jobs, sizeof(ImageJob) * n);
+        if (e == cudaSuccess) e = cudaMalloc(&G.d_tmaps, sizeof(CUtensorMap) * n);
         if (e != cudaSuccess) return cuda_status(e);
-        b->cap = n;
+        G.cap = n;
     }
-    e = cudaMemcpy(b->d_jobs, jobs.data(), sizeof(ImageJob) * n, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(b->d_tmaps, tmaps.data(), sizeof(CUtensorMap) * n, cudaMemcpyHostToDevice);
+    // Nothing reads this slot's table now (its last replay is done), so a
+    // plain copy is safe whatever stream the caller uses.
+    e = cudaMemcpy(G.d_jobs, jobs.data(), sizeof(ImageJob) * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(G.d_tmaps, tmaps.data(), sizeof(CUtensorMap) * n, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_status(e);
 
     BatchParams p;
     std::memset(&p, 0, sizeof(p));
-    p.jobs = b->d_jobs;
-    p.tmaps = b->d_tmaps;
+    p.jobs = G.d_jobs;
+    p.tmaps = G.d_tmaps;
     p.njobs = n;
     p.total_tiles = tiles;
-    p.next_tile = b->d_counter;
+    p.next_tile = G.d_counter;
     p.status = ctx->d_status;
     p.n_fallback = ctx->d_nfb;
     const int per_sm = std::max(1, std::min(kCtasPerSm[prec < 0 || prec > 2 ? 0 : prec],
@@ -280,23 +314,23 @@ static int batch_build(fabf_ctx* ctx, const fabf_request* reqs, int n)
     long long grid = (long long)ctx->num_sms * per_sm;
     if (grid > tiles) grid = tiles;
 
-    if (b->exec) {
-        cudaGraphExecDestroy(b->exec);
-        b->exec = nullptr;
+    if (G.exec) {
+        cudaGraphExecDestroy(G.exec);
+        G.exec = nullptr;
     }
     cudaGraph_t graph = nullptr;
     e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        cudaError_t e1 = cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned long long), b->cap_stream);
+        cudaError_t e1 = cudaMemsetAsync(G.d_counter, 0, sizeof(unsigned long long), b->cap_stream);
         if (e1 == cudaSuccess) e1 = launch_batch(prec, p, (int)grid, smem, b->cap_stream);
         e = cudaStreamEndCapture(b->cap_stream, &graph);
         if (e == cudaSuccess) e = e1;
     }
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, graph, 0);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&G.exec, graph, 0);
     if (graph) cudaGraphDestroy(graph);
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
-        b->exec = nullptr;
+        G.exec = nullptr;
         return cuda_status(e);
     }
     ++b->captures;
@@ -324,11 +358,11 @@ int fabf_filter_batch(fabf_ctx* ctx, const fabf_request* reqs, int n, void* cuda
         if (!is_device_ptr(reqs[i].img) || !is_device_ptr(reqs[i].theta) || !is_device_ptr(reqs[i].sigma) ||
             !is_device_ptr(reqs[i].out))
             return FABF_EINVAL;
+    std::lock_guard<std::mutex> lock(ctx->batch_lock);
     if (!ctx->batch) {
         BatchState* b = new (std::nothrow) BatchState();
         if (!b) return FABF_ENOMEM;
-        cudaError_t e = cudaMalloc(&b->d_counter, 256);
-        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+        cudaError_t e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
         if (e != cudaSuccess) {
             batch_destroy(b);
             return cuda_status(e);
@@ -339,16 +373,33 @@ int fabf_filter_batch(fabf_ctx* ctx, const fabf_request* reqs, int n, void* cuda
     std::vector<unsigned char> key(sizeof(fabf_request) * n + sizeof(int));
     std::memcpy(key.data(), reqs, sizeof(fabf_request) * n);
     std::memcpy(key.data() + sizeof(fabf_request) * n, &ctx->precision, sizeof(int));
-    if (!b->exec || key != b->key) {
-        const int rc = batch_build(ctx, reqs, n);
-        if (rc) {
-            b->key.clear();
-            return rc;
+    BatchGraph* G = nullptr;
+    for (BatchGraph& g : b->g)
+        if (g.exec && g.key == key) G = &g;
+    if (!G) {
+        // a slot never used, else the least recently used one
+        G = &b->g[0];
+        for (BatchGraph& g : b->g) {
+            if (!g.exec) {
+                G = &g;
+                break;
+            }
+            if (g.last_use < G->last_use) G = &g;
         }
-        b->key = key;
+        const int rc = batch_build(ctx, b, *G, reqs, n);
+        if (rc) return rc;
+        G->key = key;
     }
+    G->last_use = ++b->tick;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    cudaError_t e = cudaSuccess;
+    if (G->launched) e = cudaStreamWaitEvent(s, G->done, 0);   // after this set's previous replay
+    if (e == cudaSuccess) e = cudaGraphLaunch(G->exec, s);
+    if (e == cudaSuccess) e = cudaEventRecord(G->done, s);
+    if (e != cudaSuccess) return cuda_status(e);
+    G->launched = true;
     ++b->launches;
-    return cuda_status(cudaGraphLaunch(b->exec, static_cast<cudaStream_t>(cuda_stream)));
+    return FABF_OK;
 }
 
 }  // extern "C"

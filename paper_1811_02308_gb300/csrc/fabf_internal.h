@@ -45,6 +45,7 @@ struct fabf_ctx {
     size_t stage_bytes = 0;
     std::mutex stage_lock;                   // one host-pointer call at a time uses the staging buffer
     std::mutex tune_lock;
+    std::mutex batch_lock;                   // the batch graph cache
     std::map<int, fabf::TuneEntry> tune;     // key: tune_key(w, N, precision)
     fabf::ServeState* serve = nullptr;
     fabf::BatchState* batch = nullptr;

@@ -4,12 +4,12 @@
 // fabf_filter needs a context, and fabf_create allocates the context's status
 // words with cudaMalloc.  Some callers cannot do that: code running on a
 // real-time thread where cudaMalloc's implicit device synchronisation is
-// not acceptable, code inside a framework or plugin that owns every device
-// allocation and forbids its guests from calling the CUDA allocator, or a
-// host thread that is in the middle of a stream capture where allocation
-// calls are not permitted.  This entry point takes device buffers the caller
-// already owns and keeps the kernel's only scratch -- the status word and the
-// fallback-pixel counter -- in a fixed array compiled into the library.
+// not acceptable, or code inside a framework or plugin that owns every device
+// allocation and forbids its guests from calling the CUDA allocator.  This
+// entry point takes device buffers the caller already owns and keeps the
+// kernel's only scratch -- the status word and the fallback-pixel counter --
+// in a fixed array compiled into the library.  The call waits for its stream
+// before it returns, so it must not be made while a stream capture is active.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -35,11 +35,12 @@ std::mutex g_lock;
 unsigned long long* g_scratch_ptr[kMaxDevices] = {};   // device address, per device
 
 // The array's name is only a host-side stand-in in host code; its device
-// address is looked up once per device, with that device current.
-int scratch_for_current_device(unsigned long long** out)
+// address is looked up once per device, with that device (dev) current, and
+// cached for the life of the process.  A cudaDeviceReset of that device
+// would leave the cached address stale, so the library must not be used
+// across one.
+int scratch_for_device(int dev, unsigned long long** out)
 {
-    int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess) return FABF_ECUDA;
     if (dev < 0 || dev >= kMaxDevices) return FABF_EUNSUPPORTED;
     std::lock_guard<std::mutex> g(g_lock);
     if (!g_scratch_ptr[dev]) {
@@ -55,6 +56,21 @@ int scratch_for_current_device(unsigned long long** out)
     return FABF_OK;
 }
 
+// True when p is device (or managed) memory of device dev.  Buffers of
+// another GPU are rejected: the kernel runs on the current device and its
+// tensor map would be encoded over remote memory.
+bool on_device(const void* p, int dev)
+{
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    if (a.type == cudaMemoryTypeDevice) return a.device == dev;
+    return a.type == cudaMemoryTypeManaged;
+}
+
 }  // namespace
 
 extern "C" int fabf_filter_noalloc(const uint8_t* img, const float* theta, const float* sigma, int H, int W,
@@ -63,12 +79,18 @@ extern "C" int fabf_filter_noalloc(const uint8_t* img, const float* theta, const
 {
     int rc = fabf::check_filter_args(img, theta, sigma, out, H, W, pitch, w, N);
     if (rc) return rc;
-    if (!fabf::is_device_ptr(img) || !fabf::is_device_ptr(theta) || !fabf::is_device_ptr(sigma) ||
-        !fabf::is_device_ptr(out))
-        return FABF_EINVAL;   // host buffers would need device staging, i.e. an allocation
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return FABF_ECUDA;
+    }
+    // host buffers would need device staging, i.e. an allocation; buffers of
+    // another GPU are not this call's to read
+    if (!on_device(img, dev) || !on_device(theta, dev) || !on_device(sigma, dev) || !on_device(out, dev))
+        return FABF_EINVAL;
     if (kWordsPerCall > kScratchWords) return FABF_EUNSUPPORTED;
     unsigned long long* scratch = nullptr;
-    rc = scratch_for_current_device(&scratch);
+    rc = scratch_for_device(dev, &scratch);
     if (rc) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     // The array keeps the previous call's contents: clear both words first.

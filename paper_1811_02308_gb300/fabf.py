@@ -109,6 +109,7 @@ def load(path: str | None = None):
         "fabf_luma": ([vp, vp, i, i, sz, vp, sz, vp], i),
         "fabf_filter_rgb": ([vp, vp, vp, vp, i, i, sz, i, i, vp, i, vp], i),
         "fabf_texture_filter_rgb": ([vp, vp, i, i, sz, C.POINTER(TextureCfg), vp, i, vp], i),
+        "fabf_pipe_peaks": ([C.POINTER(C.c_double)], i),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -276,8 +277,16 @@ def fabf_filter_noalloc(img, theta, sigma, w: int, N: int, out, out_is_f64: bool
     _check_inputs(img, theta, sigma, H, W, p)
     s = _stream_of(img, theta, sigma, out) if stream is None else stream
     nf = C.c_uint64(0)
-    rc = load().fabf_filter_noalloc(_ptr(img), _ptr(theta), _ptr(sigma), H, W, p, int(w), int(N),
-                                    _ptr(out), 1 if out_is_f64 else 0, s, C.byref(nf))
+    lib = load()
+    args = (_ptr(img), _ptr(theta), _ptr(sigma), H, W, p, int(w), int(N), _ptr(out), 1 if out_is_f64 else 0, s,
+            C.byref(nf))
+    dev = next((a.device for a in (img, theta, sigma, out) if _is_torch(a) and a.is_cuda), None)
+    if dev is not None:
+        import torch
+        with torch.cuda.device(dev):       # the call runs on its current device
+            rc = lib.fabf_filter_noalloc(*args)
+    else:
+        rc = lib.fabf_filter_noalloc(*args)
     return rc, nf.value
 
 
@@ -620,3 +629,13 @@ def fabf_texture_filter_rgb(ctx: Context, rgb, cfg: TextureCfg, out=None, out_is
     _check(load().fabf_texture_filter_rgb(ctx.handle, _ptr(rgb), H, W, p, C.byref(cfg), _ptr(out),
                                           1 if out_is_f64 else 0, s), "fabf_texture_filter_rgb")
     return out
+
+
+def fabf_pipe_peaks(device: int = 0) -> dict:
+    """``fabf_pipe_peaks``: this GPU's measured arithmetic pipe peaks."""
+    import torch
+    out = (C.c_double * 6)()
+    with torch.cuda.device(device):
+        _check(load().fabf_pipe_peaks(out), "fabf_pipe_peaks")
+    return {"fp64_tflops": out[0], "fp32_tflops": out[1], "int32_tops": out[2], "mufu_tops": out[3],
+            "sm_mhz": out[4], "sms": int(out[5])}

@@ -52,14 +52,14 @@ def uneven_requests(n, seed, Ns=(4, 5, 6), ws=(3, 30), hw=((128, 128), (600, 800
 # Precision variants
 # ---------------------------------------------------------------------------
 # Stated binary32 tolerance on g_hat against the FP64 form, in gray levels:
-# RMS <= 0.005 (0.01 at N = 6, whose fit amplifies more) and max <= 1.0
+# RMS <= 0.005 (0.01 at N = 6, whose fit amplifies more) and max <= 0.3
 # (the method's own error against the brute force is ~7 gray levels RMS on
-# these workloads).  The binary32 integrals
-# carry ~1e-7 relative error, which the fit's alternating coefficients
-# amplify by kappa = sum |c_k I_k| / |T2|; the kernels estimate that error
-# per pixel and recompute on the FP64 path where it exceeds 0.25 gray
-# levels, so the max bound holds with a margin for the estimate's slack.
-FP32_TOL = {3: (0.005, 1.0), 4: (0.005, 1.0), 5: (0.005, 1.0), 6: (0.01, 1.0)}
+# these workloads).  The binary32 integrals carry ~1e-7 relative error,
+# which the fit's alternating coefficients amplify by kappa = sum |c_k I_k|
+# / |T2|; the kernels estimate that error per pixel and recompute on the
+# FP64 path where it exceeds 0.25 gray levels, so the max bound is the
+# guard's level plus a margin for the estimate's slack.
+FP32_TOL = {3: (0.005, 0.3), 4: (0.005, 0.3), 5: (0.005, 0.3), 6: (0.01, 0.3)}
 
 
 @pytest.mark.parametrize("prec", [fabf.FABF_FP64FIT_FP32REC, fabf.FABF_CFP32])
@@ -128,6 +128,40 @@ def test_batch_matches_single_image_and_replays_graph(ctx, oracle_mod):
         xs = rng.integers(0, th.shape[1], 60)
         ref, _ = oracle_mod.fabf_pixels(f, th, s, w, N, ys, xs)
         assert rel(got[ys, xs], ref) <= RTOL_G
+
+
+def test_batch_sets_alternate_on_a_nonblocking_stream(ctx):
+    """Request sets alternated on a non-blocking stream with no wait in
+    between: each replay must read its own job table (more sets than the
+    graph cache holds, so some are rebuilt while others may still run)."""
+    sets = []
+    for k in range(6):
+        reqs = uneven_requests(3, 40 + k, hw=((96, 96), (300, 400)))
+        ins, outs, rq = [], [], []
+        for f, th, s, w, N in reqs:
+            d = (dev(f), dev(th), dev(s))
+            o = torch.full(th.shape, float("nan"), dtype=torch.float64, device="cuda")
+            ins.append((d, w, N))
+            outs.append(o)
+            rq.append(fabf.make_request(d[0], d[1], d[2], w, N, o))
+        sets.append((ins, outs, rq))
+    stream = torch.cuda.Stream()        # created non-blocking
+    torch.cuda.synchronize()
+    order = [0, 1, 0, 1, 2, 3, 4, 5, 0, 1, 5, 0]
+    for k in order:
+        for o in sets[k][1]:
+            o.fill_(float("nan"))       # on the current stream, before the replay
+        stream.wait_stream(torch.cuda.current_stream())
+        fabf.fabf_filter_batch(ctx, sets[k][2], stream=stream.cuda_stream)
+        torch.cuda.current_stream().wait_stream(stream)
+    torch.cuda.synchronize()
+    st, _ = fabf.fabf_get_status(ctx)
+    assert st == fabf.FABF_OK
+    for k in set(order):
+        ins, outs, _ = sets[k]
+        for (d, w, N), o in zip(ins, outs):
+            alone = fabf.fabf_filter(ctx, d[0], d[1], d[2], w, N).cpu().numpy()
+            assert np.array_equal(o.cpu().numpy(), alone), (k, w, N)
 
 
 def test_autotuned_tiles_give_identical_results():
@@ -240,6 +274,45 @@ def test_serving_alone_equals_in_mix(ctx, oracle_mod):
         assert close.mean() >= (1.0 if passes == 1 else 0.999)
         assert fabf.fabf_serve_poll(ctx, t, 0)[0] == fabf.FABF_ENOTFOUND
     assert fabf.fabf_serve_stats(ctx) == (0, 0)
+
+
+def test_serving_alone_equals_in_mix_compensated_form(ctx, oracle_mod):
+    """The served form of the bench (compensated binary32, float32 outputs):
+    each result equals the same passes through fabf_filter alone, bit for
+    bit, and the first pass is within the binary32 bound of the oracle."""
+    reqs = uneven_requests(10, 5, hw=((100, 100), (400, 500)))
+    fabf.fabf_set_precision(ctx, fabf.FABF_CFP32)
+    try:
+        tickets, outs = [], []
+        for i, (f, th, s, w, N) in enumerate(reqs):
+            passes = 1 + i % 3
+            if i % 2 == 0:
+                o = np.full(th.shape, np.nan, np.float32)
+                r = fabf.make_request(f, th, s, w, N, o, out_is_f64=False, passes=passes)
+            else:
+                o = torch.full(th.shape, float("nan"), dtype=torch.float32, device="cuda")
+                r = fabf.make_request(dev(f), dev(th), dev(s), w, N, o, out_is_f64=False, passes=passes)
+            tickets.append(fabf.fabf_serve_submit(ctx, r))
+            outs.append((o, passes))
+        for t in tickets:
+            assert wait(ctx, t) == fabf.FABF_OK
+        for (f, th, s, w, N), (o, passes) in zip(reqs, outs):
+            got = o if isinstance(o, np.ndarray) else o.cpu().numpy()
+            zeta = th - f.astype(np.float32)
+            ff, tt, ss, g = f, th, s, None
+            for p in range(passes):
+                if p > 0:
+                    ff = np.clip(np.rint(g), 0, 255).astype(np.uint8)
+                    tt = (ff.astype(np.float32) + zeta).astype(np.float32)
+                    ss = (ss * np.float32(0.8)).astype(np.float32)
+                g = fabf.fabf_filter(ctx, dev(ff), dev(tt), dev(ss), w, N, out_is_f64=False).cpu().numpy()
+            assert np.array_equal(got, g), (w, N, passes)
+            if passes == 1:
+                ref, _ = oracle_mod.fabf(f, th, s, w, N)
+                err = np.abs(got.astype(np.float64) - ref)
+                assert float(err.max()) <= FP32_TOL[N][1], (w, N, float(err.max()))
+    finally:
+        fabf.fabf_set_precision(ctx, fabf.FABF_FP64)
 
 
 def test_serving_admission_by_budget():

@@ -1,0 +1,88 @@
+"""The binary32 precision forms against the CPU oracle, element by element,
+on the timed workload: 1920x1080, 200 blobs, theta = f + zeta (zeta in
+[-20, 20]), sigma in [5, 60], box w = 20, N in {5, 6}.
+
+Each form filters the whole image on the GPU in the tile shape a single
+image gets (the size-aware tile rule); the oracle (FP64, Algorithm 1 step by
+step) computes a sample of pixels one by one: random pixels, all four
+borders and the rows and columns on both sides of every possible tile seam
+(tile heights are multiples of 8 rows, tile widths 64 columns).
+
+Bound, in gray levels: max |g_form - g_oracle| <= 0.3 and RMS <= 0.005
+(0.01 at N = 6).  The kernels estimate each pixel's binary32 error and
+recompute it on the FP64 path where the estimate exceeds 0.25 gray levels;
+0.3 leaves a margin for the estimate's slack.  The FP64 form is held to
+1e-9 relative on the same sample."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_1811_02308_gb300 import build, fabf, synth  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+MAX_GRAY = 0.3
+RMS_GRAY = {5: 0.005, 6: 0.01}
+H, W, WR = 1080, 1920, 20
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    c = fabf.Context(device=0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def workload():
+    f, th, s = synth.make_inputs(H, W, synth.config_seed(1, 0), n_blobs=200, zeta_range=(-20, 20),
+                                 sigma_range=(5, 60))
+    return f, th, s
+
+
+def sample_pixels(seed, n_random=3000):
+    rng = np.random.default_rng(seed)
+    ys = [rng.integers(0, H, n_random)]
+    xs = [rng.integers(0, W, n_random)]
+    # the four borders
+    bx = rng.integers(0, W, 150)
+    by = rng.integers(0, H, 150)
+    ys += [np.zeros(150, int), np.full(150, H - 1), by, by]
+    xs += [bx, bx, np.zeros(150, int), np.full(150, W - 1)]
+    # both sides of every horizontal seam (rows 8k - 1, 8k) and of every
+    # vertical seam (columns 64k - 1, 64k), at random positions along them
+    seam_rows = np.array([r for k in range(1, H // 8 + 1) for r in (8 * k - 1, 8 * k) if r < H])
+    seam_cols = np.array([c for k in range(1, W // 64 + 1) for c in (64 * k - 1, 64 * k) if c < W])
+    ys += [seam_rows, rng.integers(0, H, len(seam_cols))]
+    xs += [rng.integers(0, W, len(seam_rows)), seam_cols]
+    # the four corners
+    ys.append(np.array([0, 0, H - 1, H - 1]))
+    xs.append(np.array([0, W - 1, 0, W - 1]))
+    return np.concatenate(ys), np.concatenate(xs)
+
+
+@pytest.mark.parametrize("N", [5, 6])
+def test_binary32_forms_against_oracle_on_timed_workload(ctx, oracle_mod, workload, N):
+    f, th, s = workload
+    ys, xs = sample_pixels(10 + N)
+    assert len(ys) >= 2000
+    ref, _ = oracle_mod.fabf_pixels(f, th, s, WR, N, ys, xs)
+    d = [torch.from_numpy(a).cuda() for a in (f, th, s)]
+    g64 = fabf.fabf_filter(ctx, *d, WR, N).cpu().numpy()
+    err64 = np.abs(g64[ys, xs] - ref) / np.maximum(np.abs(ref), 1.0)
+    assert float(err64.max()) <= 1e-9
+    for prec in (fabf.FABF_FP64FIT_FP32REC, fabf.FABF_CFP32):
+        fabf.fabf_set_precision(ctx, prec)
+        try:
+            g = fabf.fabf_filter(ctx, *d, WR, N, out_is_f64=False).cpu().numpy()
+            st, _, n_redo = fabf.fabf_get_status_ex(ctx)
+        finally:
+            fabf.fabf_set_precision(ctx, fabf.FABF_FP64)
+        assert st == fabf.FABF_OK
+        err = np.abs(g[ys, xs].astype(np.float64) - ref)
+        mx, rms = float(err.max()), float(np.sqrt(np.mean(err * err)))
+        assert mx <= MAX_GRAY and rms <= RMS_GRAY[N], (prec, N, mx, rms, n_redo)
