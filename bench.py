@@ -48,8 +48,11 @@ WORKLOAD = ("1920x1080 uint8 synthetic (200 blobs, 4 step edges, noise 10), box 
 NCU_TRAFFIC_BYTES = 18.76e6        # FP64 form kernel (8-row tiles)
 NCU_TRAFFIC_BYTES_FP64FIT = None   # FP64-fit kernel (not captured)
 NCU_TRAFFIC_BYTES_CFP32 = 19.40e6  # compensated FP32 kernel (8-row tiles, 4 CTAs per SM)
+NCU_TRAFFIC_BYTES_C32 = None       # centred binary32 kernel (not captured yet)
 NCU_TRAFFIC_BYTES_SEP = 18.77e6    # separable (Gaussian) kernel, rho = 5, compensated FP32
-FORM_NAMES = {0: "fp64", 1: "fp64fit_fp32rec", 2: "cfp32"}
+FORM_NAMES = {0: "fp64", 1: "fp64fit_fp32rec", 2: "cfp32", 3: "c32"}
+FORMS = (0, 1, 2, 3)
+DTYPES = {0: "f64", 1: "f64 fit + f32", 2: "f32 (compensated fit)", 3: "f32 (centred fit)"}
 FORMS_BY_NAME = {v: k for k, v in FORM_NAMES.items()}
 
 
@@ -61,7 +64,7 @@ def fp64_flops_per_pixel(N: int, form: int = 0) -> float:
     compensated FP32 form has no FP64 work."""
     if form == 1:
         return (N + 1) + 2 * (N + 1) ** 2
-    if form == 2:
+    if form >= 2:
         return 0.0
     return (N + 1) + 2 * (N + 1) ** 2 + 5 + 95 + 4 * N + 4 * (N + 1) + 3
 
@@ -103,7 +106,7 @@ def alu_roofline(prec: int, N: int, npix: int, kern_ms: float, traffic=None) -> 
     against the measured peak of the pipe the form runs its arithmetic on
     (FP64 for the FP64 and FP64-fit forms, FP32 FMA for the compensated
     form, whose compensation work is reported beside it, not counted)."""
-    if prec == 2:
+    if prec >= 2:
         fl, pipe, peak = method_flops_per_pixel(N), "fp32", PEAKS["fp32_tflops"]
     else:
         fl, pipe, peak = fp64_flops_per_pixel(N, prec), "fp64", PEAKS["fp64_tflops"]
@@ -506,7 +509,7 @@ def run_gaussian(R, slots, steps, rhos=(3.0, 5.0), N=NDEG):
                                                                          stream=R.sh), n, 1)
             bf_rate["fp64" if use64 else "fp32"] = npix * n / (ms / 1e3) / 1e6
         forms = {}
-        for prec in (0, 1, 2):
+        for prec in FORMS:
             fabf.fabf_set_precision(ctx, prec)
             sl = slots[prec]
 
@@ -526,11 +529,11 @@ def run_gaussian(R, slots, steps, rhos=(3.0, 5.0), N=NDEG):
                    "status": st, "psnr_vs_bruteforce_db": psnr(g, bf),
                    "fp64_redo_frac": nredo / ((steps + 3) * npix)}
             row["roofline"] = alu_roofline(prec, N, npix, kern_ms,
-                                           NCU_TRAFFIC_BYTES_SEP if (prec == 2 and rho == 5.0) else None)
+                                           None)
             forms[FORM_NAMES[prec]] = row
         fabf.fabf_set_precision(ctx, 0)
         best = "fp64"
-        for k in ("fp64fit_fp32rec", "cfp32"):
+        for k in ("fp64fit_fp32rec", "cfp32", "c32"):
             if (forms[k]["psnr_vs_bruteforce_db"] >= forms["fp64"]["psnr_vs_bruteforce_db"] - 0.01
                     and forms[k]["value"] > forms[best]["value"]):
                 best = k
@@ -563,7 +566,7 @@ def run_gaussian(R, slots, steps, rhos=(3.0, 5.0), N=NDEG):
     return {"workload": "1920x1080 as above, Gaussian spatial kernel (integer taps, peak 1024), N=%d" % N, **out}
 
 
-def run_apps(R, slots, steps, w=5, N=5):
+def run_apps(R, slots, steps, w=5, N=5, forms=(0, 2)):
     """Sec. IV applications on the 1920x1080 inputs: one sharpening pass
     (maps + Algorithm 1) and the texture-filtering pipeline (mRTV map + two
     smoothing passes + one sharpening pass), in the FP64 and compensated
@@ -581,7 +584,7 @@ def run_apps(R, slots, steps, w=5, N=5):
                        "sigma 10..40; texture: mRTV k=2, eps 1, saturation 8, sigma 5..60, decay 0.8, then "
                        "the sharpening pass; colour texture: the same on an interleaved 1920x1080x3 "
                        "image (maps from the luma, the passes per channel)" % (w, N)}
-    for prec in (0, 2):
+    for prec in forms:
         fabf.fabf_set_precision(ctx, prec)
         o = slots[prec][0][3]
         f64 = prec == 0
@@ -624,7 +627,7 @@ def sweep(args):
         for w in (5, 10, 20, 40):
             for N in (3, 4, 5, 6):
                 row = {}
-                for prec in (0, 1, 2):
+                for prec in FORMS:
                     fabf.fabf_set_precision(ctx, prec)
                     o = outs[0 if prec == 0 else 1]
                     ms, _ = R.timed(lambda i: R.filt((*d_in[i % 4], o[i % 8]), w, N), steps, 3)
@@ -644,7 +647,7 @@ def sweep(args):
             taps = synth.gaussian_taps(rho)
             for N in (3, 4, 5, 6):
                 row = {}
-                for prec in (0, 1, 2):
+                for prec in FORMS:
                     fabf.fabf_set_precision(ctx, prec)
                     o = outs[0 if prec == 0 else 1]
                     ms, _ = R.timed(lambda i: fabf.fabf_filter_sep(ctx, *d_in[i % 4], taps, N, out=o[i % 8],
@@ -685,7 +688,7 @@ def precision_report(n_sample=20000):
         for N in (5, 6):
             ref, _ = oracle.fabf_pixels(f, th, s, 20, N, ys, xs)
             row = {}
-            for prec in (0, 1, 2):
+            for prec in FORMS:
                 fabf.fabf_set_precision(ctx, prec)
                 g = fabf.fabf_filter(ctx, d[0], d[1], d[2], 20, N, out_is_f64=(prec == 0)).cpu().numpy()
                 st, nfb, nredo = fabf.fabf_get_status_ex(ctx)
@@ -714,7 +717,7 @@ def main():
                     help="DRAM bytes per launch of the fused kernel from an ncu capture")
     ap.add_argument("--profile", default=None, metavar="HxW",
                     help="profiling case: one input of this size, FP64 form only, no other legs")
-    ap.add_argument("--profile-precision", type=int, default=0, choices=[0, 1, 2])
+    ap.add_argument("--profile-precision", type=int, default=0, choices=[0, 1, 2, 3])
     ap.add_argument("--profile-rho", type=float, default=None,
                     help="with --profile: the separable Gaussian kernel of this rho instead of the box")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
@@ -757,7 +760,7 @@ def main():
         n_distinct, n_slots = 1, 1
     host = [make_inputs(H_, W_, 1000 + 17 * rank + i, N_BLOBS) for i in range(n_distinct)]
     slots = {}
-    for prec in (0, 1, 2):
+    for prec in FORMS:
         odt = torch.float64 if prec == 0 else torch.float32
         slots[prec] = []
         for i in range(n_slots):
@@ -791,7 +794,7 @@ def main():
         torch.distributed.barrier()
     with ClockSampler(local) as clk:
         time.sleep(0.3)
-        for prec in (0, 1, 2):
+        for prec in FORMS:
             fabf.fabf_set_precision(ctx, prec)
             total_ms, kern_ms = R.timed(lambda i, p=prec: R.filt(slots[p][i % n_slots], WR, NDEG),
                                         args.steps, args.warmup)
@@ -811,7 +814,7 @@ def main():
     f0, th0, s0 = slots[0][0][:3]
     bf = fabf.fabf_bruteforce(ctx, f0, th0, s0, WR, use_f64=True).cpu().numpy()
     acc = {0: {"max_abs_vs_fp64": 0.0, "rms_vs_fp64": 0.0, "psnr_vs_bruteforce_db": psnr(g64, bf)}}
-    for prec in (1, 2):
+    for prec in FORMS[1:]:
         fabf.fabf_set_precision(ctx, prec)
         R.filt(slots[prec][0], WR, NDEG)
         g = slots[prec][0][3].cpu().numpy().astype(np.float64)
@@ -836,11 +839,12 @@ def main():
                "fp64_redo_frac": r["redo"] / (n_calls * npix)}
         row.update(acc[prec])
         row["roofline"] = alu_roofline(prec, NDEG, npix, r["kernel_ms"],
-                                       (NCU_TRAFFIC_BYTES, NCU_TRAFFIC_BYTES_FP64FIT, NCU_TRAFFIC_BYTES_CFP32)[prec])
+                                       (NCU_TRAFFIC_BYTES, NCU_TRAFFIC_BYTES_FP64FIT, NCU_TRAFFIC_BYTES_CFP32,
+                                        NCU_TRAFFIC_BYTES_C32)[prec])
         form_rows[FORM_NAMES[prec]] = row
     # headline: fastest form as accurate as FP64 (PSNR vs brute force within 0.01 dB)
     best = 0
-    for prec in (1, 2):
+    for prec in FORMS[1:]:
         ok = acc[prec]["psnr_vs_bruteforce_db"] >= acc[0]["psnr_vs_bruteforce_db"] - 0.01
         form_rows[FORM_NAMES[prec]]["equal_accuracy"] = bool(ok)
         if ok and form_rows[FORM_NAMES[prec]]["value"] > form_rows[FORM_NAMES[best]]["value"]:
@@ -882,7 +886,7 @@ def main():
     line = {"metric": METRIC, "value": head["value"], "unit": "Mpix/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": forms[best]["total_ms"] / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if best == 0 else ("f64 fit + f32" if best == 1 else "f32 (compensated fit)"),
+            "dtype": DTYPES[best],
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "H": H_, "W": W_, "w": WR, "N": NDEG,
                        "precision": FORM_NAMES[best], "parallelism": "replicas" if ws > 1 else "single",
@@ -894,7 +898,7 @@ def main():
                                for k, v in bf_ms.items()}}
     if rank == 0 and not args.no_extra and ws == 1:
         line["gaussian"] = run_gaussian(R, slots, max(10, args.steps // 10))
-        line["applications"] = run_apps(R, slots, max(10, args.steps // 10))
+        line["applications"] = run_apps(R, slots, max(10, args.steps // 10), forms=(0, best))
         line["batch"] = {FORM_NAMES[p]: run_batch(R, p, max(5, args.steps // 20)) for p in (0, best)}
         line["serve"] = run_serve(R, best, args.serve_seconds)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

@@ -63,11 +63,16 @@ typedef enum {
  *     integrals, recursion and ratio in binary32.
  *   FABF_CFP32: fit with compensated binary32 dot products, the rest in
  *     binary32.
- * In both binary32 forms a pixel whose estimated error exceeds 0.25 gray
+ *   FABF_C32: everything after the exact integer stages in binary32, with
+ *     the fit of Eqs. (18)-(19), the integrals of Eq. (28) and the ratio of
+ *     Eq. (29) expressed in the centred variable s = 2t - 1: the same fitted
+ *     polynomial and the same g_hat, but a system whose inverse has small
+ *     exact binary32 entries, so the sums hardly cancel (no compensation).
+ * In the binary32 forms a pixel whose estimated error exceeds 0.25 gray
  * levels (the ratio of Eq. (29) cancels badly, T2 <= 0, or the binary32
  * integrals are in a regime where they lose digits) is recomputed on the
  * FP64 path; fabf_get_status_ex counts those pixels. */
-typedef enum { FABF_FP64 = 0, FABF_FP64FIT_FP32REC = 1, FABF_CFP32 = 2 } fabf_precision;
+typedef enum { FABF_FP64 = 0, FABF_FP64FIT_FP32REC = 1, FABF_CFP32 = 2, FABF_C32 = 3 } fabf_precision;
 
 typedef struct {
     int device;                  /* CUDA device ordinal */
@@ -341,6 +346,14 @@ int fabf_texture_filter_rgb(fabf_ctx* ctx, const uint8_t* rgb, int H, int W, siz
  * kernels use.  Errors: FABF_EINVAL (out NULL), FABF_EUNSUPPORTED (N > 6). */
 int fabf_hilbert_inverse(int N, int64_t* out);
 
+/* The inverse of the (N+1) x (N+1) matrix of the centred fit of FABF_C32,
+ * A~[j][k] = 1 / (j + k + 1) for j + k even and 0 otherwise (the moments of
+ * s = 2t - 1 over t in [0, 1], the same moment-matching problem as Eq. (18)
+ * in another basis), row-major into out[(N+1)*(N+1)] -- the binary32 table
+ * the kernels use; every entry is a dyadic rational held exactly.  Errors:
+ * FABF_EINVAL (out NULL), FABF_EUNSUPPORTED (N > 6). */
+int fabf_centred_inverse(int N, double* out);
+
 /* Dynamic shared memory (bytes) one CTA of the fused kernel needs for
  * (w, N) with the tallest tile (64 output rows). */
 int fabf_fused_smem_bytes(int w, int N, size_t* bytes);
@@ -358,7 +371,7 @@ int fabf_fused_smem_bytes(int w, int N, size_t* bytes);
  *   out[2] INT32 multiply-add, T ops/s
  *   out[3] MUFU base-2 exponential (ex2.approx.f32), T ops/s
  *   out[4] SM clock seen during the FP64 run, MHz (clock64 cycles of one CTA
- *          over the launch's event time)
+ *          over the global-timer nanoseconds of the same interval)
  *   out[5] number of SMs
  * Synchronous; allocates and frees 2 KB of device memory.  Errors:
  * FABF_EINVAL (out NULL), FABF_ENOMEM, FABF_ECUDA. */
@@ -384,7 +397,10 @@ int fabf_debug_stages(fabf_ctx* ctx, const uint8_t* img, const float* theta,
 
 /* The integral engine alone: out[j*(K+1) + k] = I_k(lambda[j], t0[j]) for
  * k = 0..K (Eq. (28), scaled by exp(lambda d^2)), 1 <= K <= 7, lambda > 0,
- * in the given precision (FABF_FP64 or FABF_FP64FIT_FP32REC for binary32). */
+ * in the given precision (FABF_FP64 or FABF_FP64FIT_FP32REC for binary32);
+ * with FABF_C32 the centred integrals of that form instead:
+ * out[j*(K+1) + k] = J_k = int_0^1 (2t - 1)^k exp(-lambda (t - t0)^2) dt,
+ * with the same scaling, in binary32. */
 int fabf_debug_integrals(fabf_ctx* ctx, const double* lambda, const double* t0, int64_t n,
                          int K, int precision, double* out);
 

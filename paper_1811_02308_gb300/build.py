@@ -17,6 +17,7 @@ SOURCES = [
     "fabf_inst_fp64.cu",
     "fabf_inst_fp64fit.cu",
     "fabf_inst_cfp32.cu",
+    "fabf_inst_c32.cu",
     "fabf_api.cu",
     "fabf_batch_serve.cu",
     "fabf_noalloc.cu",
@@ -24,6 +25,7 @@ SOURCES = [
     "fabf_sep_p0.cu",
     "fabf_sep_p1.cu",
     "fabf_sep_p2.cu",
+    "fabf_sep_p3.cu",
     "fabf_apps.cu",
     "fabf_peaks.cu",
 ]

@@ -124,6 +124,7 @@ cudaError_t launch_fused(int prec, int N, const CUtensorMap& tm, const FusedPara
     case kPrecFP64: return launch_fused_p0(N, tm, p, grid, smem, s);
     case kPrecFP64Fit: return launch_fused_p1(N, tm, p, grid, smem, s);
     case kPrecCFP32: return launch_fused_p2(N, tm, p, grid, smem, s);
+    case kPrecC32: return launch_fused_p3(N, tm, p, grid, smem, s);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -134,6 +135,7 @@ cudaError_t launch_batch(int prec, const BatchParams& p, int grid, size_t smem, 
     case kPrecFP64: return launch_batch_p0(p, grid, smem, s);
     case kPrecFP64Fit: return launch_batch_p1(p, grid, smem, s);
     case kPrecCFP32: return launch_batch_p2(p, grid, smem, s);
+    case kPrecC32: return launch_batch_p3(p, grid, smem, s);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -412,7 +414,7 @@ int fabf_create(const fabf_config* cfg, fabf_ctx** out)
     *out = nullptr;
     fabf_config c{};
     if (cfg) c = *cfg;
-    if (c.precision < FABF_FP64 || c.precision > FABF_CFP32) return FABF_EINVAL;
+    if (c.precision < FABF_FP64 || c.precision > FABF_C32) return FABF_EINVAL;
     fabf_ctx* ctx = new (std::nothrow) fabf_ctx();
     if (!ctx) return FABF_ENOMEM;
     ctx->device = c.device;
@@ -456,7 +458,7 @@ int fabf_destroy(fabf_ctx* ctx)
 
 int fabf_set_precision(fabf_ctx* ctx, int precision)
 {
-    if (!ctx || precision < FABF_FP64 || precision > FABF_CFP32) return FABF_EINVAL;
+    if (!ctx || precision < FABF_FP64 || precision > FABF_C32) return FABF_EINVAL;
     ctx->precision = precision;
     return FABF_OK;
 }
@@ -525,6 +527,17 @@ int fabf_hilbert_inverse(int N, int64_t* out)
     return FABF_OK;
 }
 
+int fabf_centred_inverse(int N, double* out)
+{
+    if (!out) return FABF_EINVAL;
+    if (N < 0) return FABF_EINVAL;
+    if (N > kNMax) return FABF_EUNSUPPORTED;
+    constexpr CentredInvTable t = make_centred_inverse_table();
+    for (int j = 0; j <= N; ++j)
+        for (int k = 0; k <= N; ++k) out[j * (N + 1) + k] = (double)t.v[N][j][k];
+    return FABF_OK;
+}
+
 int fabf_fused_smem_bytes(int w, int N, size_t* bytes)
 {
     if (!bytes || w < 1 || N < 0) return FABF_EINVAL;
@@ -557,8 +570,9 @@ int fabf_debug_integrals(fabf_ctx* ctx, const double* lambda, const double* t0, 
                          int precision, double* out)
 {
     if (!ctx || !lambda || !t0 || !out || n < 0 || K < 1 || K > 7) return FABF_EINVAL;
-    if (precision != FABF_FP64 && precision != FABF_FP64FIT_FP32REC) return FABF_EUNSUPPORTED;
-    const int fp32 = precision == FABF_FP64 ? 0 : 1;
+    if (precision != FABF_FP64 && precision != FABF_FP64FIT_FP32REC && precision != FABF_C32)
+        return FABF_EUNSUPPORTED;
+    const int fp32 = precision == FABF_FP64 ? 0 : (precision == FABF_C32 ? 2 : 1);
     if (n == 0) return FABF_OK;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return FABF_ECUDA;
     const int threads = 128;

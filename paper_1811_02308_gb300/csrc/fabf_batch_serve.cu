@@ -111,7 +111,7 @@ void load_tune_cache(fabf_ctx* ctx)
 
 static int steady_tile_rows(fabf_ctx* ctx, int w, int N, int prec)
 {
-    const int dflt = kSteadyTileRows[prec < 0 || prec > 2 ? 0 : prec];
+    const int dflt = kSteadyTileRows[prec_index(prec)];
     if (!ctx || !ctx->autotune) return dflt;
     load_tune_cache(ctx);
     std::lock_guard<std::mutex> g(ctx->tune_lock);
@@ -184,7 +184,7 @@ int tile_rows_for(fabf_ctx* ctx, int w, int N, int prec, int H, int W)
             return kTileCandidates[0];
         }
     }
-    const int pc = prec < 0 || prec > 2 ? 0 : prec;
+    const int pc = prec_index(prec);
     int off, Cb;
     fused_geometry(w, &off, &Cb);
     const long long tiles_x = (W + kTileW - 1) / kTileW;
@@ -309,7 +309,7 @@ static int batch_build(fabf_ctx* ctx, BatchState* b, BatchGraph& G, const fabf_r
     p.next_tile = G.d_counter;
     p.status = ctx->d_status;
     p.n_fallback = ctx->d_nfb;
-    const int per_sm = std::max(1, std::min(kCtasPerSm[prec < 0 || prec > 2 ? 0 : prec],
+    const int per_sm = std::max(1, std::min(kCtasPerSm[prec_index(prec)],
                                             (int)((size_t)228 * 1024 / (smem + 1024))));
     long long grid = (long long)ctx->num_sms * per_sm;
     if (grid > tiles) grid = tiles;
@@ -756,7 +756,7 @@ int fabf_batch_stats(fabf_ctx* ctx, int* graph_captures, int* graph_launches)
 
 int fabf_tile_rows(fabf_ctx* ctx, int w, int N, int precision, int* tile_rows)
 {
-    if (!ctx || !tile_rows || w < 1 || N < 0 || precision < FABF_FP64 || precision > FABF_CFP32) return FABF_EINVAL;
+    if (!ctx || !tile_rows || w < 1 || N < 0 || precision < FABF_FP64 || precision > FABF_C32) return FABF_EINVAL;
     if (w > kWMax || N > kNMax) return FABF_EUNSUPPORTED;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return FABF_ECUDA;
     *tile_rows = tile_rows_for(ctx, w, N, precision, 0, 0);

@@ -56,14 +56,14 @@ __host__ __device__ constexpr AinvTable make_ainv_table()
 }
 
 struct RecipTable {
-    double v[64];   // v[j] = 1 / j (v[0] unused)
-    float f[64];    // the same in binary32
+    double v[128];   // v[j] = 1 / j (v[0] unused)
+    float f[128];    // the same in binary32
 };
 
 __host__ __device__ constexpr RecipTable make_recip_table()
 {
     RecipTable t{};
-    for (int j = 1; j < 64; ++j) {
+    for (int j = 1; j < 128; ++j) {
         t.v[j] = 1.0 / (double)j;
         t.f[j] = (float)(1.0 / (double)j);
     }
@@ -638,6 +638,297 @@ __device__ __forceinline__ double fabf_pixel_cfp32_redo(int alpha, int beta, int
         dp *= d;
     }
     return fabf_redo_scaled<N>(v, alpha, d, theta_f, sigma_f, fallback);
+}
+
+// ===========================================================================
+// FABF_C32: the binary32 form in the centred variable s = 2t - 1.
+//
+// The fitted polynomial p is the unique one of degree N whose moments over
+// [0, 1] match the window's (Eqs. (18)-(19)); any basis of the polynomials of
+// degree N gives the same p.  In the monomials of t the system is the Hilbert
+// matrix, whose inverse has entries up to 1.3e8 (N = 6): the coefficients
+// alternate and are large, and the sums T1, T2 of Eq. (29) cancel, which is
+// why binary32 needs compensation or FP64 there.  In the monomials of the
+// centred variable s = 2t - 1 in [-1, 1] the system is
+//   A~[j][k] = int_0^1 s^(j+k) dt = 1 / (j + k + 1) if j + k is even, else 0,
+// a checkerboard Hankel matrix whose inverse has dyadic entries of at most
+// 5211 (N = 6), all exact in binary32; its coefficients are small and the
+// sums hardly cancel, so a plain binary32 fit and binary32 sums are accurate.
+//
+// Every quantity is the paper's, expressed in s:
+//   moments   mu~_k = sum_window s_j^k, s_j = (2 f_j - alpha - beta) / d,
+//             formed exactly in integers (scaled by d^K) from the power sums;
+//   fit       c~ = A~^{-1} mu~ (even and odd coefficients decouple);
+//   integrals J_k = int_0^1 s^k exp(-lambda (t - t0)^2) dt, by the same
+//             integration by parts as Eq. (30), in s (see integrals_c32);
+//   ratio     T2 = sum c~_k J_k, T1 = int t p phi = (sum c~_k (J_k+1 + J_k)) / 2,
+//             so g_hat = alpha + d T1 / T2 = (alpha + beta) / 2
+//                        + (d / 2) sum c~_k J_(k+1) / T2.
+// ===========================================================================
+
+// A~^{-1} for N = 0..6, [N][n][k], computed at compile time (Gauss-Jordan in
+// binary64 on the symmetric positive definite A~, then snapped to the grid of
+// 1/256, on which every entry lies exactly; the snap is checked below).
+struct CentredInvTable {
+    float v[kNMax + 1][kNMax + 1][kNMax + 1];
+    double err;   // largest distance of a binary64 entry from its snapped value
+};
+
+__host__ __device__ constexpr double centred_snap(double x)
+{
+    const double y = x * 256.0;
+    const long long q = (long long)(y >= 0.0 ? y + 0.5 : y - 0.5);
+    return (double)q / 256.0;
+}
+
+__host__ __device__ constexpr CentredInvTable make_centred_inverse_table()
+{
+    CentredInvTable t{};
+    t.err = 0.0;
+    for (int N = 0; N <= kNMax; ++N) {
+        const int n = N + 1;
+        double a[kNMax + 1][kNMax + 1] = {};
+        double b[kNMax + 1][kNMax + 1] = {};
+        for (int j = 0; j < n; ++j)
+            for (int k = 0; k < n; ++k) {
+                a[j][k] = ((j + k) & 1) ? 0.0 : 1.0 / (double)(j + k + 1);
+                b[j][k] = j == k ? 1.0 : 0.0;
+            }
+        for (int p = 0; p < n; ++p) {            // no pivoting: A~ is SPD
+            const double ip = 1.0 / a[p][p];
+            for (int k = 0; k < n; ++k) {
+                a[p][k] *= ip;
+                b[p][k] *= ip;
+            }
+            for (int r = 0; r < n; ++r) {
+                if (r == p) continue;
+                const double f = a[r][p];
+                for (int k = 0; k < n; ++k) {
+                    a[r][k] -= f * a[p][k];
+                    b[r][k] -= f * b[p][k];
+                }
+            }
+        }
+        for (int j = 0; j < n; ++j)
+            for (int k = 0; k < n; ++k) {
+                const double q = centred_snap(b[j][k]);
+                const double e = q > b[j][k] ? q - b[j][k] : b[j][k] - q;
+                if (e > t.err) t.err = e;
+                t.v[N][j][k] = (float)q;
+            }
+    }
+    return t;
+}
+
+static_assert(make_centred_inverse_table().err < 1e-6, "centred inverse entries are not on the 1/256 grid");
+
+// Start indices of the downward recursion of integrals_c32, by the per-step
+// error gain g = lambda (1 + |s0|) / 2 in bins of 1/4: the smallest Kp with
+// prod_{k=9}^{Kp} g / k < 1e-8 at the bin's upper edge (K = 7, the largest
+// top index; smaller K only recurse further past their last index).
+struct KpTable {
+    unsigned char v[64];
+};
+
+__host__ __device__ constexpr KpTable make_kp_table()
+{
+    KpTable t{};
+    for (int i = 0; i < 64; ++i) {
+        const double g = (i + 1) * 0.25;
+        double p = 1.0;
+        int kp = 8;
+        do {
+            ++kp;
+            p *= g / (double)kp;
+        } while (p >= 1e-8 && kp < 60);
+        t.v[i] = (unsigned char)kp;
+    }
+    return t;
+}
+
+static __constant__ KpTable c_kp = make_kp_table();
+
+// lambda at and above which integrals_c32 recurses forward.
+constexpr float kLambdaForwardC32 = 5.0f;
+
+// J_k = int_0^1 s^k exp(-lambda (t - t0)^2) dt, s = 2t - 1, k = 0..K, each
+// times exp(lambda d^2) with d the distance from t0 to [0, 1] (the factor is
+// common to T1 and T2 and cancels).  With s0 = 2 t0 - 1, E0 = exp(-lambda t0^2)
+// and E1 = exp(-lambda (1 - t0)^2) (both scaled), integration by parts of
+// s^k (s - s0) exp(...) -- as for Eq. (30) -- gives
+//   J_(k+1) = s0 J_k + (2k / lambda) J_(k-1) - (E1 - (-1)^k E0) / lambda,
+// J_0 = I_0 of Eq. (31), J_1 = s0 J_0 - (E1 - E0) / lambda.
+//  lambda >= 5: forward, as written;
+//  lambda <  5: downward (the recursion solved for J_(k-1)), whose error gain
+//               per step lambda (1 + |s0|) / (2k) is below one, from a start
+//               index Kp taken from c_kp and made warp-uniform, with the
+//               start values J_k ~ (E1 / (k + 1 - lambda (1 - t0))
+//               + (-1)^k E0 / (k + 1 - lambda t0)) / 2 (the mass of s^k near
+//               s = +-1); no erf is needed.
+template <int K>
+__device__ __forceinline__ void integrals_c32(float lam, float t0, float s0, float (&J)[K + 1])
+{
+    static_assert(K >= 1 && K <= 7, "K out of range");
+    const float d = t0 < 0.0f ? -t0 : (t0 > 1.0f ? t0 - 1.0f : 0.0f);
+    const float E0s = expf(-lam * ((t0 - d) * (t0 + d)));
+    const float E1s = expf(-lam * ((1.0f - t0 - d) * (1.0f - t0 + d)));
+    const float Ep = E1s + E0s, Em = E1s - E0s;   // E1 - (-1)^k E0 for k odd, even
+    if (lam >= kLambdaForwardC32) {
+        const float rl = rsqrtf(lam);
+        const float sl = lam * rl;
+        const float h = 0.886226925452758f * rl;
+        const bool inside = d == 0.0f;
+        const float S = inside ? 2.0f : 0.0f;
+        const float ca = inside ? E1s : -1.0f;
+        const float xa = inside ? sl * (1.0f - t0) : sl * d;
+        const float cb = inside ? E0s : (t0 < 0.0f ? E1s : E0s);
+        const float xb = inside ? sl * t0 : sl * (1.0f + d);
+        const float il = 1.0f / lam;
+        J[0] = h * (S - ca * erfcxf(xa) - cb * erfcxf(xb));
+        J[1] = fmaf(s0, J[0], -Em * il);
+#pragma unroll
+        for (int k = 1; k < K; ++k)
+            J[k + 1] = fmaf(s0, J[k], fmaf((float)(2 * k) * il, J[k - 1], -((k & 1) ? Ep : Em) * il));
+    } else {
+        const float g = lam * (1.0f + fabsf(s0)) * 0.5f;
+        int Kp = c_kp.v[min(63, (int)(g * 4.0f))];
+        Kp = (int)__reduce_max_sync(__activemask(), (unsigned)Kp);
+        const float l1 = lam * (1.0f - t0), l0 = lam * t0;
+        float a1 = (float)(Kp + 2) - l1, b1 = (float)(Kp + 2) - l0;
+        float a0 = (float)(Kp + 1) - l1, b0 = (float)(Kp + 1) - l0;
+        a1 = a1 > 1.0f ? a1 : (float)(Kp + 2);
+        b1 = b1 > 1.0f ? b1 : (float)(Kp + 2);
+        a0 = a0 > 1.0f ? a0 : (float)(Kp + 1);
+        b0 = b0 > 1.0f ? b0 : (float)(Kp + 1);
+        const float sg = (Kp & 1) ? 1.0f : -1.0f;   // (-1)^(Kp+1)
+        float hi = 0.5f * (__fdividef(E1s, a1) + sg * __fdividef(E0s, b1));   // J_(Kp+1)
+        float lo = 0.5f * (__fdividef(E1s, a0) - sg * __fdividef(E0s, b0));   // J_(Kp)
+        // (hi, lo) = (J_(k+1), J_k) -> J_(k-1), for k = Kp .. K + 1
+        for (int k = Kp; k > K; --k) {
+            const float nx = fmaf(lam, fmaf(-s0, lo, hi), (k & 1) ? Ep : Em) * (0.5f * c_recip.f[k]);
+            hi = lo;
+            lo = nx;
+        }
+        J[K] = lo;
+        const float top = hi;   // J_(K+1)
+#pragma unroll
+        for (int k = K; k >= 1; --k) {
+            const float Jk1 = (k == K) ? top : J[k + 1];
+            J[k - 1] = fmaf(lam, fmaf(-s0, J[k], Jk1), (k & 1) ? Ep : Em) * (0.5f / (float)k);
+        }
+    }
+}
+
+// Exact float-free conversion helper: 0 <= |x| < 2^63 to binary32 from three
+// exact 23-bit chunks (two roundings: within one unit in the last place).
+__device__ __forceinline__ float i63_to_float(int64_t x)
+{
+    const uint64_t u = x < 0 ? (uint64_t)0 - (uint64_t)x : (uint64_t)x;
+    const float f0 = u23_to_float((uint32_t)u & 0x7FFFFFu);
+    const float f1 = u23_to_float((uint32_t)(u >> 23) & 0x7FFFFFu);
+    const float f2 = u23_to_float((uint32_t)(u >> 46));
+    const float r = fmaf(f2, 70368744177664.0f, fmaf(f1, 8388608.0f, f0));   // x 2^46, x 2^23
+    return x < 0 ? -r : r;
+}
+
+// Error bound per unit of the sums' scale for the guard of FABF_C32: the
+// binary32 integrals carry up to ~2e-6 of max_k |J_k| in the regimes they are
+// used in, the rest (moments, fit, sums) a few units of 2^-24.
+constexpr float kGuardUnitC32 = 4.0e-6f;
+
+// Regimes where the binary32 integrals of integrals_c32 lose digits: a
+// range-kernel centre more than 0.75 kernel widths outside [0, 1] with
+// 2 < lambda < 20 (both recursion directions amplify there).
+__device__ __forceinline__ bool c32_integrals_weak(float lam, float t0)
+{
+    const float d = t0 < 0.0f ? -t0 : (t0 > 1.0f ? t0 - 1.0f : 0.0f);
+    return lam > 2.0f && lam < 20.0f && d * d * lam > 0.5625f;
+}
+
+// The centred binary32 tail from commonly scaled centred moments v_k =
+// scale * mu~_k (|v_k| < 2^63, exact integers; the scale cancels in the
+// ratio).  Returns g_hat; sets redo when the pixel must be recomputed on the
+// FP64 path (T2 <= 0 or not finite, the error estimate above kFp32GuardGray,
+// or a weak integral regime).
+template <int N>
+__device__ __forceinline__ float fabf_tail_c32(const int64_t (&v)[(N < 1 ? 1 : N) + 1], int alpha, int beta,
+                                               float theta_f, float sigma_f, bool& redo)
+{
+    constexpr CentredInvTable kA = make_centred_inverse_table();
+    float mu[N + 1];
+#pragma unroll
+    for (int k = 0; k <= N; ++k) mu[k] = i63_to_float(v[k]);
+    // c~ = A~^{-1} mu~: even coefficients from even moments, odd from odd
+    float c[N + 1];
+#pragma unroll
+    for (int n = 0; n <= N; ++n) {
+        float acc = 0.0f;
+#pragma unroll
+        for (int k = n & 1; k <= N; k += 2) acc = fmaf(kA.v[N][n][k], mu[k], acc);
+        c[n] = acc;
+    }
+    const int d = beta - alpha;
+    const float rd = __frcp_rn((float)d);
+    const float t0 = (theta_f - (float)alpha) * rd;
+    const float s0 = (2.0f * theta_f - (float)(alpha + beta)) * rd;
+    const float lam = (float)(d * d) * __frcp_rn(2.0f * sigma_f * sigma_f);
+    float J[N + 2];
+    integrals_c32<N + 1>(lam, t0, s0, J);
+    float T2 = c[0] * J[0], U = c[0] * J[1];
+    float S2 = fabsf(T2), S1 = fabsf(U);
+#pragma unroll
+    for (int k = 1; k <= N; ++k) {
+        T2 = fmaf(c[k], J[k], T2);
+        U = fmaf(c[k], J[k + 1], U);
+        S2 = fmaf(fabsf(c[k]), fabsf(J[k]), S2);
+        S1 = fmaf(fabsf(c[k]), fabsf(J[k + 1]), S1);
+    }
+    const float R = U / T2;
+    const float hd = 0.5f * (float)d;
+    const float est = kGuardUnitC32 * hd * (S1 + fabsf(R) * S2) / fabsf(T2);
+    redo = !(T2 > 0.0f) || !(est <= kFp32GuardGray) || c32_integrals_weak(lam, t0);
+    return fmaf(hd, R, 0.5f * (float)(alpha + beta));
+}
+
+// Exact centred moments M~_b = sum_window (2 f - c0)^b, c0 = alpha + beta,
+// b = 0..K, from the power sums m_a by S(a, b) = S(a+1, b-1) - c0 S(a, b-1),
+// S(a, 0) = 2^a m_a, in wrapping 64-bit arithmetic: every step is exact
+// modulo 2^64 and |M~_b| <= m_0 d^b < 2^63, so the results are exact.
+template <int K>
+__device__ __forceinline__ void centred_moments(int c0, const int64_t (&m)[K + 1], int64_t (&M)[K + 1])
+{
+    uint64_t S[K + 1];
+#pragma unroll
+    for (int a = 0; a <= K; ++a) S[a] = (uint64_t)m[a] << a;
+    M[0] = (int64_t)S[0];
+#pragma unroll
+    for (int b = 1; b <= K; ++b) {
+#pragma unroll
+        for (int a = 0; a <= K - b; ++a) S[a] = S[a + 1] - (uint64_t)c0 * S[a];
+        M[b] = (int64_t)S[0];
+    }
+}
+
+// FABF_C32 at one pixel of the box path.
+template <int N>
+__device__ __forceinline__ float fabf_pixel_c32(int alpha, int beta, int fi, const int64_t (&m)[(N < 1 ? 1 : N) + 1],
+                                                float theta_f, float sigma_f, bool& redo)
+{
+    constexpr int K = N < 1 ? 1 : N;
+    redo = false;
+    if (alpha == beta) return (float)fi;
+    const int d = beta - alpha;
+    int64_t M[K + 1];
+    centred_moments<K>(alpha + beta, m, M);
+    // mu~_k d^K = M~_k d^(K-k): exact integers, |.| <= m_0 d^K < 2^63
+    int64_t v[K + 1];
+    int64_t dp = 1;
+#pragma unroll
+    for (int k = K; k >= 0; --k) {
+        v[k] = (int64_t)((uint64_t)M[k] * (uint64_t)dp);
+        dp *= d;
+    }
+    return fabf_tail_c32<N>(v, alpha, beta, theta_f, sigma_f, redo);
 }
 
 }  // namespace fabf

@@ -91,6 +91,9 @@ cudaError_t launch_fused_p2(int N, const CUtensorMap& tm, const FusedParams& p, 
 cudaError_t launch_batch_p0(const BatchParams& p, int grid, size_t smem, cudaStream_t s);
 cudaError_t launch_batch_p1(const BatchParams& p, int grid, size_t smem, cudaStream_t s);
 cudaError_t launch_batch_p2(const BatchParams& p, int grid, size_t smem, cudaStream_t s);
+cudaError_t launch_fused_p3(int N, const CUtensorMap& tm, const FusedParams& p, dim3 grid, size_t smem,
+                            cudaStream_t s);
+cudaError_t launch_batch_p3(const BatchParams& p, int grid, size_t smem, cudaStream_t s);
 
 // Launch one image on device buffers with the context's precision and tuned
 // tile shape; status words are the context's.
@@ -115,11 +118,14 @@ int launch_fused_scratch(const uint8_t* img, size_t pitch, const float* theta, c
 // 2160x3840 and 4096^2 for w in {5, 20, 40}.
 int tile_rows_for(fabf_ctx* ctx, int w, int N, int prec, int H, int W);
 constexpr int kTileCandidates[] = {8, 16, 24, 32, 40};
-constexpr int kSteadyTileRows[3] = {8, 8, 40};    // FP64, FP64 fit + FP32, compensated FP32
-constexpr int kMinWaves[3] = {1, 1, 6};
+constexpr int kPrecForms = 4;
+// FP64, FP64 fit + FP32, compensated FP32, centred binary32
+constexpr int kSteadyTileRows[kPrecForms] = {8, 8, 40, 40};
+constexpr int kMinWaves[kPrecForms] = {1, 1, 6, 6};
 // Resident CTAs per SM the kernels are compiled for (MinBlocks in
 // fabf_kernels.cuh); shared memory may allow fewer.
-constexpr int kCtasPerSm[3] = {2, 4, 4};
+constexpr int kCtasPerSm[kPrecForms] = {2, 4, 4, 4};
+inline int prec_index(int prec) { return prec < 0 || prec >= kPrecForms ? 0 : prec; }
 constexpr int kDefaultTileRows = 32;               // stage-export runs of the tests
 
 int read_and_clear_status(fabf_ctx* ctx, cudaStream_t s, int* status, uint64_t* nfb, uint64_t* nredo);

@@ -60,6 +60,7 @@ constexpr int kLaneTable = 5 * 32;
 constexpr int kPrecFP64 = 0;          // FABF_FP64
 constexpr int kPrecFP64Fit = 1;       // FABF_FP64FIT_FP32REC
 constexpr int kPrecCFP32 = 2;         // FABF_CFP32
+constexpr int kPrecC32 = 3;           // FABF_C32
 
 struct DebugPlanes {       // per-stage exports for the parity tests (all optional)
     uint8_t* alpha;        // H x W
@@ -673,8 +674,10 @@ __device__ __forceinline__ bool fabf_tile(const CUtensorMap* tmap, const ImageJo
                             bool redo = false;
                             if constexpr (PREC == kPrecFP64Fit)
                                 g = (double)fabf_pixel_fp64fit<N>(c_ainv, alpha, beta, fi, m, th, sg, fb, redo);
-                            else
+                            else if constexpr (PREC == kPrecCFP32)
                                 g = (double)fabf_pixel_cfp32<N>(c_ainv_split, alpha, beta, fi, m, th, sg, fb, redo);
+                            else
+                                g = (double)fabf_pixel_c32<N>(alpha, beta, fi, m, th, sg, redo);
                             if (redo) {   // binary32 not accurate enough here: queue for the FP64 pass
                                 const unsigned slot = atomicAdd(redo_n, 1u);
                                 redo_list[slot] = (uint16_t)((rr << 8) | x);
@@ -814,15 +817,22 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<PREC>::value) fabf_batch_k
 }
 
 // ---------------------------------------------------------------------------
-// Test kernel: the integral engine alone, I_0..I_K for n (lambda, t0) pairs,
-// in binary64 (fp32 == 0) or binary32.
+// Test kernel: the integral engine alone for n (lambda, t0) pairs: I_0..I_K
+// in binary64 (mode 0) or binary32 (mode 1), or the centred J_0..J_K of
+// FABF_C32 in binary32 (mode 2).
 // ---------------------------------------------------------------------------
 template <int K>
-__global__ void integrals_kernel(const double* lam, const double* t0, long long n, int fp32, double* out)
+__global__ void integrals_kernel(const double* lam, const double* t0, long long n, int mode, double* out)
 {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    if (fp32) {
+    if (mode == 2) {
+        float J[K + 1];
+        const float tf = (float)t0[i];
+        integrals_c32<K>((float)lam[i], tf, 2.0f * tf - 1.0f, J);
+#pragma unroll
+        for (int k = 0; k <= K; ++k) out[i * (K + 1) + k] = (double)J[k];
+    } else if (mode == 1) {
         float I[K + 1];
         integrals_fp32<K>((float)lam[i], (float)t0[i], I);
 #pragma unroll

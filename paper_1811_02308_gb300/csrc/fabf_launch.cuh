@@ -1,6 +1,7 @@
 // Kernel launch helpers, instantiated once per precision in
-// fabf_inst_fp64.cu, fabf_inst_fp64fit.cu and fabf_inst_cfp32.cu (separate
-// translation units so that nvcc compiles them in parallel).
+// fabf_inst_fp64.cu, fabf_inst_fp64fit.cu, fabf_inst_cfp32.cu and
+// fabf_inst_c32.cu (separate translation units so that nvcc compiles them in
+// parallel).
 #pragma once
 
 #include <cuda_runtime.h>

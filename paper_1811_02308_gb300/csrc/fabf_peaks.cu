@@ -21,23 +21,37 @@ constexpr int kThreads = 256;
 constexpr int kBlocksPerSm = 4;
 constexpr int kChains = 8;
 
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// cycles[0], cycles[1]: SM clock cycles and global-timer nanoseconds that
+// CTA 0's thread 0 spent in its loop (their ratio is the SM clock).
 __global__ void __launch_bounds__(kThreads) dfma_loop(double a0, double b, int iters, double* sink,
                                                       unsigned long long* cycles)
 {
     double x[kChains];
 #pragma unroll
     for (int j = 0; j < kChains; ++j) x[j] = a0 + 1e-3 * (threadIdx.x + j);
+    const unsigned long long g0 = global_ns();
     const long long t0 = clock64();
     for (int i = 0; i < iters; ++i) {
 #pragma unroll
         for (int j = 0; j < kChains; ++j) x[j] = fma(x[j], b, -0.25);   // |x| stays bounded for |b| < 1
     }
     const long long t1 = clock64();
+    const unsigned long long g1 = global_ns();
     double acc = 0.0;
 #pragma unroll
     for (int j = 0; j < kChains; ++j) acc += x[j];
     if (acc == 1234.5678) sink[threadIdx.x] = acc;
-    if (threadIdx.x == 0 && blockIdx.x == 0) *cycles = (unsigned long long)(t1 - t0);
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        cycles[0] = (unsigned long long)(t1 - t0);
+        cycles[1] = g1 - g0;
+    }
 }
 
 __global__ void __launch_bounds__(kThreads) ffma_loop(float a0, float b, int iters, float* sink)
@@ -146,8 +160,8 @@ extern "C" int fabf_pipe_peaks(double* out)
     float ms64 = 0, ms32 = 0, msi = 0, msm = 0;
     cudaError_t e = time_best([&] { dfma_loop<<<blocks, kThreads>>>(0.5, 0.75, it64, (double*)sink, d_cycles); },
                               3, &ms64);
-    unsigned long long cyc = 0;
-    if (e == cudaSuccess) e = cudaMemcpy(&cyc, d_cycles, sizeof(cyc), cudaMemcpyDeviceToHost);
+    unsigned long long cyc[2] = {0, 0};
+    if (e == cudaSuccess) e = cudaMemcpy(cyc, d_cycles, sizeof(cyc), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess)
         e = time_best([&] { ffma_loop<<<blocks, kThreads>>>(0.5f, 0.75f, it32, (float*)sink); }, 3, &ms32);
     if (e == cudaSuccess)
@@ -165,8 +179,8 @@ extern "C" int fabf_pipe_peaks(double* out)
     out[2] = ops32 / (msi * 1e-3) / 1e12;          // INT32 multiply-add, T ops/s
     out[3] = opsm / (msm * 1e-3) / 1e12;           // MUFU ex2, T ops/s
     // SM clock during the FP64 run: one CTA's clock64 cycles over the
-    // launch's event time (the CTA spans nearly the whole launch)
-    out[4] = ms64 > 0 ? (double)cyc / (ms64 * 1e-3) / 1e6 : 0.0;
+    // global-timer nanoseconds of the same interval
+    out[4] = cyc[1] > 0 ? (double)cyc[0] / (double)cyc[1] * 1e3 : 0.0;
     out[5] = (double)sms;
     return FABF_OK;
 }

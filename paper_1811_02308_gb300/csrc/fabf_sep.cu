@@ -22,7 +22,7 @@ namespace fabf {
 // size of this kernel.
 static int sep_tile_rows(fabf_ctx* ctx, int r, int N, int prec, int H, int W)
 {
-    const int steady = kSteadyTileRows[prec < 0 || prec > 2 ? 0 : prec];
+    const int steady = kSteadyTileRows[prec_index(prec)];
     if (steady <= kTileCandidates[0]) return steady;
     int off, Cb;
     fused_geometry(r, &off, &Cb);
@@ -31,10 +31,10 @@ static int sep_tile_rows(fabf_ctx* ctx, int r, int N, int prec, int H, int W)
     for (int TH : kTileCandidates) {
         if (TH > steady) break;
         const size_t smem = sep_smem_bytes(N, r, Cb, TH) + 1024;
-        const int per_sm = std::max(1, std::min(kCtasPerSm[prec < 0 || prec > 2 ? 0 : prec],
+        const int per_sm = std::max(1, std::min(kCtasPerSm[prec_index(prec)],
                                                 (int)((size_t)228 * 1024 / smem)));
         const long long tiles = tiles_x * ((H + TH - 1) / TH);
-        if (tiles >= (long long)kMinWaves[prec] * ctx->num_sms * per_sm) best = TH;
+        if (tiles >= (long long)kMinWaves[prec_index(prec)] * ctx->num_sms * per_sm) best = TH;
     }
     return best;
 }
@@ -46,6 +46,7 @@ static cudaError_t launch_sep(int prec, int N, const CUtensorMap& tm, const SepP
     case kPrecFP64: return launch_sep_p0(N, tm, p, grid, smem, s);
     case kPrecFP64Fit: return launch_sep_p1(N, tm, p, grid, smem, s);
     case kPrecCFP32: return launch_sep_p2(N, tm, p, grid, smem, s);
+    case kPrecC32: return launch_sep_p3(N, tm, p, grid, smem, s);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -198,6 +198,47 @@ __device__ __forceinline__ float sep_pixel_fp32(int alpha, int beta, int fi, con
     }
 }
 
+// FABF_C32 at one pixel of the separable path: the centred moments M~_b =
+// sum omega (2 f - c0)^b by the recursion of centred_moments in wrapping
+// 128-bit arithmetic (exact: |M~_b| <= m_0 d^b < 2^81), scaled by d^(K-b),
+// then shifted right together (arithmetically) so that the largest,
+// m_0 d^K, is below 2^63; the common factor cancels in the ratio.
+template <int N>
+__device__ __forceinline__ float sep_pixel_c32(int alpha, int beta, int fi, const u128 (&m)[(N < 1 ? 1 : N) + 1],
+                                               float th, float sg, bool& redo)
+{
+    constexpr int K = N < 1 ? 1 : N;
+    redo = false;
+    if (alpha == beta) return (float)fi;
+    const int d = beta - alpha;
+    const uint32_t c0 = (uint32_t)(alpha + beta);
+    u128 S[K + 1], M[K + 1];
+#pragma unroll
+    for (int a = 0; a <= K; ++a) S[a] = m[a] << a;
+    M[0] = S[0];
+#pragma unroll
+    for (int b = 1; b <= K; ++b) {
+#pragma unroll
+        for (int a = 0; a <= K - b; ++a) S[a] = S[a + 1] - mul_u128_u32(S[a], c0);
+        M[b] = S[0];
+    }
+    u128 sc[K + 1];
+    {
+        uint64_t dp = 1;
+#pragma unroll
+        for (int k = K; k >= 0; --k) {
+            sc[k] = mul_u128_u64(M[k], dp);   // two's complement: exact modulo 2^128
+            dp *= (uint64_t)d;
+        }
+    }
+    const uint64_t top = (uint64_t)(sc[0] >> 64);   // sc[0] = m_0 d^K > 0
+    const int shift = top ? 65 - __clzll(top) : ((uint64_t)sc[0] >> 63 ? 1 : 0);
+    int64_t v[K + 1];
+#pragma unroll
+    for (int k = 0; k <= K; ++k) v[k] = (int64_t)((__int128)sc[k] >> shift);
+    return fabf_tail_c32<N>(v, alpha, beta, th, sg, redo);
+}
+
 // The compensated form's FP64 redo (fabf_redo_scaled) from the separable
 // moments, scaled and shifted as in sep_pixel_fp32's compensated fit; with
 // all-ones taps this is the box path's redo bit for bit.
@@ -475,7 +516,10 @@ __device__ __forceinline__ void sep_tile(const CUtensorMap* tmap, const SepParam
                             g = sep_pixel_fp64<N>(alpha, beta, fi, m, th, sg, fb, trp, M);
                         } else {
                             bool redo = false;
-                            g = (double)sep_pixel_fp32<N, PREC>(alpha, beta, fi, m, th, sg, fb, redo);
+                            if constexpr (PREC == kPrecC32)
+                                g = (double)sep_pixel_c32<N>(alpha, beta, fi, m, th, sg, redo);
+                            else
+                                g = (double)sep_pixel_fp32<N, PREC>(alpha, beta, fi, m, th, sg, fb, redo);
                             if (redo) {   // binary32 not accurate enough here: queue for the FP64 pass
                                 const unsigned slot = atomicAdd(redo_n, 1u);
                                 redo_list[slot] = (uint16_t)((rr << 8) | x);
@@ -608,5 +652,6 @@ cudaError_t launch_sep_impl(int N, const CUtensorMap& tm, const SepParams& p, di
 cudaError_t launch_sep_p0(int N, const CUtensorMap& tm, const SepParams& p, dim3 grid, size_t smem, cudaStream_t s);
 cudaError_t launch_sep_p1(int N, const CUtensorMap& tm, const SepParams& p, dim3 grid, size_t smem, cudaStream_t s);
 cudaError_t launch_sep_p2(int N, const CUtensorMap& tm, const SepParams& p, dim3 grid, size_t smem, cudaStream_t s);
+cudaError_t launch_sep_p3(int N, const CUtensorMap& tm, const SepParams& p, dim3 grid, size_t smem, cudaStream_t s);
 
 }  // namespace fabf

@@ -27,6 +27,7 @@ FABF_ENOTFOUND = 7
 FABF_FP64 = 0
 FABF_FP64FIT_FP32REC = 1
 FABF_CFP32 = 2
+FABF_C32 = 3
 
 _lib = None
 
@@ -94,6 +95,7 @@ def load(path: str | None = None):
         "fabf_batch_stats": ([vp, C.POINTER(i), C.POINTER(i)], i),
         "fabf_tile_rows": ([vp, i, i, i, C.POINTER(i)], i),
         "fabf_hilbert_inverse": ([i, vp], i),
+        "fabf_centred_inverse": ([i, vp], i),
         "fabf_fused_smem_bytes": ([i, i, C.POINTER(sz)], i),
         "fabf_debug_stages": ([vp, vp, vp, vp, i, i, sz, i, i] + [vp] * 11, i),
         "fabf_debug_integrals": ([vp, vp, vp, C.c_int64, i, i, vp], i),
@@ -312,6 +314,12 @@ def fabf_get_status_ex(ctx: Context, stream: int = 0):
 def fabf_hilbert_inverse(N: int) -> np.ndarray:
     out = np.zeros((N + 1, N + 1), dtype=np.int64)
     _check(load().fabf_hilbert_inverse(int(N), out.ctypes.data), "fabf_hilbert_inverse")
+    return out
+
+
+def fabf_centred_inverse(N: int) -> np.ndarray:
+    out = np.zeros((N + 1, N + 1), dtype=np.float64)
+    _check(load().fabf_centred_inverse(int(N), out.ctypes.data), "fabf_centred_inverse")
     return out
 
 

@@ -49,12 +49,34 @@ def test_kernel_hilbert_table_is_exact(lib, N):
     assert got.tolist() == [[int(v) for v in row] for row in ref]
 
 
+@pytest.mark.parametrize("N", range(7))
+def test_kernel_centred_table_is_the_exact_inverse(lib, N):
+    """The centred fit's table times the matrix of centred moments,
+    A~[j][k] = 1/(j+k+1) for j+k even else 0, is the identity in exact
+    rational arithmetic (every entry a dyadic rational held exactly)."""
+    from fractions import Fraction
+    got = fabf.fabf_centred_inverse(N)
+    inv = [[Fraction(float(v)) for v in row] for row in got]
+    A = [[Fraction(1, j + k + 1) if (j + k) % 2 == 0 else Fraction(0) for k in range(N + 1)]
+         for j in range(N + 1)]
+    for i in range(N + 1):
+        for k in range(N + 1):
+            assert sum(inv[i][j] * A[j][k] for j in range(N + 1)) == (1 if i == k else 0)
+    # the checkerboard: even and odd coefficients do not mix
+    for i in range(N + 1):
+        for k in range(N + 1):
+            if (i + k) % 2:
+                assert got[i][k] == 0.0
+
+
 def test_argument_checks_without_gpu(lib):
     null = C.c_void_p(0)
     assert lib.fabf_filter(null, 0, 0, 0, 4, 4, 4, 1, 1, 0, 1, 0) == fabf.FABF_EINVAL
     out = np.zeros(64, np.int64)
     assert lib.fabf_hilbert_inverse(7, out.ctypes.data) == fabf.FABF_EUNSUPPORTED
     assert lib.fabf_hilbert_inverse(3, None) == fabf.FABF_EINVAL
+    assert lib.fabf_centred_inverse(7, np.zeros(64).ctypes.data) == fabf.FABF_EUNSUPPORTED
+    assert lib.fabf_centred_inverse(3, None) == fabf.FABF_EINVAL
     b = C.c_size_t(0)
     assert lib.fabf_fused_smem_bytes(41, 5, C.byref(b)) == fabf.FABF_EUNSUPPORTED
     assert lib.fabf_fused_smem_bytes(5, 7, C.byref(b)) == fabf.FABF_EUNSUPPORTED
@@ -116,7 +138,7 @@ def test_binding_rejects_mismatched_buffers():
 def test_precision_enum_bounds_without_gpu(lib):
     # fabf_create checks the precision before touching the device
     h = C.c_void_p()
-    cfg = fabf._Config(0, 0, 3, 0, None)
+    cfg = fabf._Config(0, 0, 4, 0, None)
     assert lib.fabf_create(C.byref(cfg), C.byref(h)) == fabf.FABF_EINVAL
     cfg = fabf._Config(0, 0, -1, 0, None)
     assert lib.fabf_create(C.byref(cfg), C.byref(h)) == fabf.FABF_EINVAL

@@ -62,7 +62,7 @@ def uneven_requests(n, seed, Ns=(4, 5, 6), ws=(3, 30), hw=((128, 128), (600, 800
 FP32_TOL = {3: (0.005, 0.3), 4: (0.005, 0.3), 5: (0.005, 0.3), 6: (0.01, 0.3)}
 
 
-@pytest.mark.parametrize("prec", [fabf.FABF_FP64FIT_FP32REC, fabf.FABF_CFP32])
+@pytest.mark.parametrize("prec", [fabf.FABF_FP64FIT_FP32REC, fabf.FABF_CFP32, fabf.FABF_C32])
 @pytest.mark.parametrize("N", [3, 4, 5, 6])
 def test_precision_variant_error(ctx, oracle_mod, prec, N):
     f, th, s = synth.make_inputs(540, 960, synth.config_seed(3, N), n_blobs=50, zeta_range=None,
@@ -97,6 +97,38 @@ def test_fp32_integral_engine(ctx, oracle_mod):
         ref = oracle_mod.integrals(lam, t0, 7)
         worst = max(worst, float(np.max(np.abs(got[j] - ref) / np.abs(ref))))
     assert worst <= 2e-5, worst
+
+
+def centred_integrals_reference(oracle_mod, lam, t0, K):
+    """J_k = int_0^1 (2t-1)^k exp(-lambda (t-t0)^2) dt (same scaling as I_k)
+    from the oracle's I_j by the binomial expansion of (2t-1)^k, summed in
+    extended precision."""
+    from math import comb
+    I = oracle_mod.integrals(lam, t0, K).astype(np.longdouble)
+    return np.array([sum(comb(k, j) * (2 ** j) * (-1) ** (k - j) * I[j] for j in range(k + 1))
+                     for k in range(K + 1)], dtype=np.float64)
+
+
+def test_centred_integral_engine(ctx, oracle_mod):
+    """The centred binary32 engine of FABF_C32 (forward for lambda >= 5,
+    downward below) within 2e-6 of max_k |J_k| over lambda in [1e-4, 2e3]
+    with the centre inside [0, 1] or up to 0.75 kernel widths outside (the
+    regime it is used in; farther out and 2 < lambda < 20 the form hands the
+    pixel to the FP64 path)."""
+    pts = []
+    for lam in np.geomspace(1e-4, 2e3, 40):
+        sl = np.sqrt(lam)
+        for t in list(np.linspace(0, 1, 9)) + [-0.5 / sl, -0.75 / sl, 1 + 0.5 / sl, 1 + 0.75 / sl]:
+            pts.append((lam, t))
+    g = np.array(pts)
+    K = 7
+    got = fabf.fabf_debug_integrals(ctx, dev(g[:, 0].copy()), dev(g[:, 1].copy()), K,
+                                    precision=fabf.FABF_C32).cpu().numpy()
+    worst = 0.0
+    for j, (lam, t0) in enumerate(g):
+        ref = centred_integrals_reference(oracle_mod, lam, t0, K)
+        worst = max(worst, float(np.max(np.abs(got[j] - ref)) / np.max(np.abs(ref))))
+    assert worst <= 2e-6, worst
 
 
 # ---------------------------------------------------------------------------
@@ -180,7 +212,7 @@ def test_autotuned_tiles_give_identical_results():
             assert np.array_equal(a, b)
 
 
-@pytest.mark.parametrize("prec", [fabf.FABF_FP64, fabf.FABF_FP64FIT_FP32REC, fabf.FABF_CFP32])
+@pytest.mark.parametrize("prec", [fabf.FABF_FP64, fabf.FABF_FP64FIT_FP32REC, fabf.FABF_CFP32, fabf.FABF_C32])
 def test_every_tile_height_gives_identical_results(tmp_path, prec):
     # the per-pixel arithmetic does not depend on the tiling: forcing each
     # candidate height (through the tune cache; batches use the steady-state
@@ -276,12 +308,13 @@ def test_serving_alone_equals_in_mix(ctx, oracle_mod):
     assert fabf.fabf_serve_stats(ctx) == (0, 0)
 
 
-def test_serving_alone_equals_in_mix_compensated_form(ctx, oracle_mod):
-    """The served form of the bench (compensated binary32, float32 outputs):
-    each result equals the same passes through fabf_filter alone, bit for
-    bit, and the first pass is within the binary32 bound of the oracle."""
+@pytest.mark.parametrize("prec", [fabf.FABF_CFP32, fabf.FABF_C32])
+def test_serving_alone_equals_in_mix_binary32_forms(ctx, oracle_mod, prec):
+    """The binary32 forms the bench serves (float32 outputs): each result
+    equals the same passes through fabf_filter alone, bit for bit, and the
+    first pass is within the binary32 bound of the oracle."""
     reqs = uneven_requests(10, 5, hw=((100, 100), (400, 500)))
-    fabf.fabf_set_precision(ctx, fabf.FABF_CFP32)
+    fabf.fabf_set_precision(ctx, prec)
     try:
         tickets, outs = [], []
         for i, (f, th, s, w, N) in enumerate(reqs):

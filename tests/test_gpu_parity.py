@@ -316,7 +316,7 @@ def test_pinned_host_buffers_equal_device_path(ctx, H, W, w, N, f64, pitch_extra
     buf[:, :W] = f
     odt = torch.float64 if f64 else torch.float32
     pth, psg = torch.from_numpy(th).pin_memory(), torch.from_numpy(s).pin_memory()
-    for prec in (fabf.FABF_FP64, fabf.FABF_CFP32):
+    for prec in (fabf.FABF_FP64, fabf.FABF_CFP32, fabf.FABF_C32):
         if prec != fabf.FABF_FP64 and f64:
             continue
         fabf.fabf_set_precision(ctx, prec)
@@ -345,7 +345,7 @@ def test_pipelined_host_path_equals_device_path(ctx, H, W, w, N, f64, pitch_extr
     pitch = W + pitch_extra
     buf = np.zeros((H, pitch), np.uint8)
     buf[:, :W] = f
-    for prec in (fabf.FABF_FP64, fabf.FABF_CFP32):
+    for prec in (fabf.FABF_FP64, fabf.FABF_CFP32, fabf.FABF_C32):
         if prec != fabf.FABF_FP64 and f64:
             continue
         fabf.fabf_set_precision(ctx, prec)

@@ -205,7 +205,7 @@ SEP_FP32_TOL = {3: (0.01, 1.0), 5: (0.01, 1.0), 6: (0.01, 1.0)}
 SEP_REDO_MAX = {3: 0.2, 5: 0.2, 6: 0.4}
 
 
-@pytest.mark.parametrize("prec", [fabf.FABF_FP64FIT_FP32REC, fabf.FABF_CFP32])
+@pytest.mark.parametrize("prec", [fabf.FABF_FP64FIT_FP32REC, fabf.FABF_CFP32, fabf.FABF_C32])
 @pytest.mark.parametrize("rho,N", [(3.0, 3), (5.0, 5), (13.0, 6), (1.0, 5)])
 def test_sep_precision_forms(ctx, oracle_mod, prec, rho, N):
     f, th, s = inputs(540, 960, 300 + N, n_blobs=50, zeta=None)
@@ -230,7 +230,7 @@ def test_sep_precision_forms(ctx, oracle_mod, prec, rho, N):
     assert rms <= tol_rms and mx <= tol_max, (rms, mx)
 
 
-@pytest.mark.parametrize("prec", [fabf.FABF_FP64FIT_FP32REC, fabf.FABF_CFP32])
+@pytest.mark.parametrize("prec", [fabf.FABF_FP64FIT_FP32REC, fabf.FABF_CFP32, fabf.FABF_C32])
 def test_sep_precision_forms_all_ones_equal_box(ctx, prec):
     # with all-ones taps the binary32 forms of both paths see the same
     # scaled moments (no shift is needed below 2^63) and must agree bit for bit
@@ -247,7 +247,7 @@ def test_sep_precision_forms_all_ones_equal_box(ctx, prec):
     assert torch.equal(a, b)
 
 
-@pytest.mark.parametrize("prec", [fabf.FABF_FP64, fabf.FABF_CFP32])
+@pytest.mark.parametrize("prec", [fabf.FABF_FP64, fabf.FABF_CFP32, fabf.FABF_C32])
 def test_sep_pinned_host_buffers_equal_device_path(ctx, prec):
     # pinned theta, sigma and out are read and written in place by the
     # kernel (only a host image is copied); the result equals the device call
