@@ -54,6 +54,7 @@ def load_library(path: str):
     I = C.c_int
     lib.oracle_hilbert_inverse.argtypes = [I, i64p]
     lib.oracle_integrals.argtypes = [C.c_double, C.c_double, I, f64p]
+    lib.oracle_fit.argtypes = [I, f64p, f64p]
     lib.oracle_bounds.argtypes = [u8p, I, I, L, I, u8p, u8p]
     lib.oracle_moments.argtypes = [u8p, I, I, L, I, I, i64p]
     lib.oracle_shifted_moments.argtypes = [u8p, I, I, L, I, I, i64p]
@@ -139,6 +140,16 @@ def integrals(lam: float, t0: float, K: int) -> np.ndarray:
     _check(_load().oracle_integrals(float(lam), float(t0), int(K), _ptr(out, C.c_double)),
            "integrals")
     return out
+
+
+def fit(N: int, mu) -> np.ndarray:
+    """The fit step of Algorithm 1 on given moments: c = A^{-1} mu (Eq. (19)),
+    fused multiply-adds over ascending k; any common scale of mu carries
+    through to c."""
+    mu = np.ascontiguousarray(mu, dtype=np.float64)
+    c = np.zeros(N + 1, np.float64)
+    _check(_load().oracle_fit(int(N), _ptr(mu, C.c_double), _ptr(c, C.c_double)), "fit")
+    return c
 
 
 def bounds(f, w):

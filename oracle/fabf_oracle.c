@@ -256,15 +256,22 @@ int oracle_integrals(double lam, double t0, int K, double* I)
  * (Eq. (25)), the integrals (Eq. (28)), and the ratio (Eq. (29)) with the
  * reading R5 for a non-positive denominator.  Writes c[N+1], t0lam[2],
  * I[N+2], T[2], *g and ORs bit1 into *flags on the fallback. */
-static void fabf_tail(int N, const int64_t* Ainv, int alpha, int d, const double* mu, double th,
-                      double s, double* g_out, double* c, double* t0lam, double* I, double* T,
-                      int* flags)
+/* The fit of Algorithm 1: c = A^{-1} mu (Eq. (19)), each coefficient a chain
+ * of fused multiply-adds over ascending k starting from zero. */
+static void fit(int N, const int64_t* Ainv, const double* mu, double* c)
 {
     for (int n = 0; n <= N; ++n) {
         double acc = 0.0;
         for (int k = 0; k <= N; ++k) acc = fma((double)Ainv[n * (N + 1) + k], mu[k], acc);
         c[n] = acc;
     }
+}
+
+static void fabf_tail(int N, const int64_t* Ainv, int alpha, int d, const double* mu, double th,
+                      double s, double* g_out, double* c, double* t0lam, double* I, double* T,
+                      int* flags)
+{
+    fit(N, Ainv, mu, c);
     const double t0 = (th - (double)alpha) / (double)d;
     const double lam = (double)(d * d) / (2.0 * s * s);
     oracle_integrals(lam, t0, N + 1, I);
@@ -332,6 +339,17 @@ static int fabf_pixel(const uint8_t* f, const float* theta, const float* sigma,
 /* ------------------------------------------------------------------ */
 /* Exported entry points                                               */
 /* ------------------------------------------------------------------ */
+
+/* The fit step alone on given moments mu[0..N]: c[0..N] = A^{-1} mu as in
+ * Algorithm 1 (the moments may carry any common scale; the fit is linear). */
+int oracle_fit(int N, const double* mu, double* c)
+{
+    if (N < 0 || N > ORACLE_NMAX || !mu || !c) return 1;
+    int64_t Ainv[(ORACLE_NMAX + 1) * (ORACLE_NMAX + 1)];
+    oracle_hilbert_inverse(N, Ainv);
+    fit(N, Ainv, mu, c);
+    return 0;
+}
 
 /* alpha, beta: H x W uint8, row stride W. */
 int oracle_bounds(const uint8_t* f, int H, int W, long pitch, int w,

@@ -105,7 +105,7 @@ static __constant__ RecipTable c_recip = make_recip_table();
 //  lambda >= 1: Eq. (31) for I_0 (erf; scaled erfc when t0 is outside
 //               [0, 1]), Eq. (32) for I_1, Eq. (30) forward for I_2..I_K.
 //  lambda <  1: Eq. (30) solved for I_{k-2} and run downwards from a start
-//               index Kp >= K + 1 (chosen from lambda, made warp-uniform)
+//               index Kp >= K + 1 (chosen from lambda and t0, made warp-uniform)
 //               with the start values I_k ~ E_1 / (k + 1 + 2 lambda (t0-1))
 //               (mass of t^k near t = 1).  The recursion's own error
 //               amplification is below one in that direction, so the start
@@ -113,9 +113,49 @@ static __constant__ RecipTable c_recip = make_recip_table();
 // ---------------------------------------------------------------------------
 constexpr double kLambdaForward = 1.0;
 
-__device__ __forceinline__ int backward_start_index(double lam)
+// Start index of the binary64 downward recursion: one step maps (I_k,
+// I_(k-1)) to (I_(k-1), I_(k-2)) and multiplies an error in the pair by the
+// spectral radius of its homogeneous part,
+//   rho_k = (a + sqrt(a^2 + 4b)) / 2,  a = 2 lambda |t0| / (k-1), b = 2 lambda / (k-1);
+// Kp is the smallest index with prod_{k=K+2}^{Kp+1} rho_k < 1e-13 (the start
+// values carry a relative error of at most a few percent), at the upper
+// corner of a bin of (lambda, |t0|) (bins of 1/32 in lambda < 1 and 1/2 in
+// |t0| < 4), for K = 7.
+struct KpTableF64 {
+    unsigned char v[32][8];   // [lambda bin][|t0| bin]
+};
+
+__host__ __device__ constexpr double ct_sqrt64(double x)
 {
-    return lam <= 0.1 ? 24 : (lam <= 0.3 ? 32 : (lam <= 0.7 ? 40 : 48));
+    double r = x > 1.0 ? x : 1.0;
+    for (int i = 0; i < 60; ++i) r = 0.5 * (r + x / r);
+    return r;
+}
+
+__host__ __device__ constexpr KpTableF64 make_kp_table_f64()
+{
+    KpTableF64 t{};
+    for (int i = 0; i < 32; ++i)
+        for (int j = 0; j < 8; ++j) {
+            const double lam = (i + 1) / 32.0, at0 = (j + 1) * 0.5;
+            double p = 1.0;
+            int kp = 8;   // K + 1
+            do {
+                ++kp;     // the step that produces I_(kp-2) from I_kp, I_(kp-1)
+                const double a = 2.0 * lam * at0 / (kp - 1), b = 2.0 * lam / (kp - 1);
+                p *= 0.5 * (a + ct_sqrt64(a * a + 4.0 * b));
+            } while (p >= 1e-13 && kp < 62);
+            t.v[i][j] = (unsigned char)kp;
+        }
+    return t;
+}
+
+static __constant__ KpTableF64 c_kp64 = make_kp_table_f64();
+
+__device__ __forceinline__ int backward_start_index(double lam, double t0)
+{
+    const float lf = (float)lam, af = fabsf((float)t0);
+    return c_kp64.v[min(31, (int)(lf * 32.0f))][min(7, (int)(af * 2.0f))];
 }
 
 template <int K>
@@ -151,7 +191,7 @@ __device__ __forceinline__ void integrals_fp64(double lam, double t0, double (&I
     } else {
         const double d = t0 < 0.0 ? -t0 : (t0 > 1.0 ? t0 - 1.0 : 0.0);
         const double E1s = exp(-lam * ((1.0 - t0 - d) * (1.0 - t0 + d)));   // exp(-lam (1-t0)^2 + lam d^2)
-        int Kp = backward_start_index(lam);
+        int Kp = backward_start_index(lam, t0);
         Kp = __reduce_max_sync(__activemask(), (unsigned)Kp);
         const double l2 = 2.0 * lam;
         const double q = l2 * (t0 - 1.0);
@@ -276,13 +316,16 @@ __device__ __forceinline__ double fabf_pixel_fp64(const AinvTable& A, int alpha,
         for (int a = 0; a <= K - b; ++a) s[a] = s[a + 1] - (int64_t)alpha * s[a];
         M[b] = s[0];
     }
-    // mu_k = M_k / (beta - alpha)^k: one correctly rounded division of two
-    // binary64 values ((beta - alpha)^k <= 255^6 is exact).
+    // Scaled moments mu'_k = d^K mu_k = M_k d^(K-k), mu_k = M_k / d^k of
+    // Eq. (24): exact integers (<= m_0 255^6 < 2^63), each rounded once to
+    // binary64 by the conversion, with no division.  The common factor d^K
+    // carries through the (linear) fit into c, T1 and T2 and cancels in the
+    // ratio of Eq. (29), and mu'_1 / mu'_0 = mu_1 / mu_0 for the fallback.
     double mu[K + 1];
     int64_t dk = 1;
 #pragma unroll
-    for (int k = 0; k <= K; ++k) {
-        mu[k] = (double)M[k] / (double)dk;
+    for (int k = K; k >= 0; --k) {
+        mu[k] = (double)(M[k] * dk);
         dk *= d;
     }
     if (tr) {
@@ -722,34 +765,47 @@ __host__ __device__ constexpr CentredInvTable make_centred_inverse_table()
 
 static_assert(make_centred_inverse_table().err < 1e-6, "centred inverse entries are not on the 1/256 grid");
 
-// Start indices of the downward recursion of integrals_c32, by the per-step
-// error gain g = lambda (1 + |s0|) / 2 in bins of 1/4: the smallest Kp with
-// prod_{k=9}^{Kp} g / k < 1e-8 at the bin's upper edge (K = 7, the largest
-// top index; smaller K only recurse further past their last index).
-struct KpTable {
-    unsigned char v[64];
+// Start indices of the downward recursion of integrals_c32.  One step maps
+// (J_(k+1), J_k) to (J_k, J_(k-1)); an error in the pair is multiplied by
+// the spectral radius of the step's homogeneous part,
+//   rho_k = (a + sqrt(a^2 + 4b)) / 2,  a = lambda |s0| / (2k), b = lambda / (2k).
+// Kp is the smallest index with prod_{k=9}^{Kp} rho_k < 1e-8, taken at the
+// upper corner of a bin of (lambda, |s0|) (bins of 1/4 in lambda < 6 and
+// 1/2 in |s0| < 4; K = 7, the largest top index -- smaller K only recurse
+// further past their last index).
+__host__ __device__ constexpr double ct_sqrt(double x)
+{
+    double r = x > 1.0 ? x : 1.0;
+    for (int i = 0; i < 60; ++i) r = 0.5 * (r + x / r);
+    return r;
+}
+
+struct KpTableC32 {
+    unsigned char v[24][8];   // [lambda bin][|s0| bin]
 };
 
-__host__ __device__ constexpr KpTable make_kp_table()
+__host__ __device__ constexpr KpTableC32 make_kp_table_c32()
 {
-    KpTable t{};
-    for (int i = 0; i < 64; ++i) {
-        const double g = (i + 1) * 0.25;
-        double p = 1.0;
-        int kp = 8;
-        do {
-            ++kp;
-            p *= g / (double)kp;
-        } while (p >= 1e-8 && kp < 60);
-        t.v[i] = (unsigned char)kp;
-    }
+    KpTableC32 t{};
+    for (int i = 0; i < 24; ++i)
+        for (int j = 0; j < 8; ++j) {
+            const double lam = (i + 1) * 0.25, as0 = (j + 1) * 0.5;
+            double p = 1.0;
+            int kp = 8;
+            do {
+                ++kp;
+                const double a = lam * as0 / (2.0 * kp), b = lam / (2.0 * kp);
+                p *= 0.5 * (a + ct_sqrt(a * a + 4.0 * b));
+            } while (p >= 1e-8 && kp < 63);
+            t.v[i][j] = (unsigned char)kp;
+        }
     return t;
 }
 
-static __constant__ KpTable c_kp = make_kp_table();
+static __constant__ KpTableC32 c_kp32 = make_kp_table_c32();
 
 // lambda at and above which integrals_c32 recurses forward.
-constexpr float kLambdaForwardC32 = 5.0f;
+constexpr float kLambdaForwardC32 = 6.0f;
 
 // J_k = int_0^1 s^k exp(-lambda (t - t0)^2) dt, s = 2t - 1, k = 0..K, each
 // times exp(lambda d^2) with d the distance from t0 to [0, 1] (the factor is
@@ -758,10 +814,10 @@ constexpr float kLambdaForwardC32 = 5.0f;
 // s^k (s - s0) exp(...) -- as for Eq. (30) -- gives
 //   J_(k+1) = s0 J_k + (2k / lambda) J_(k-1) - (E1 - (-1)^k E0) / lambda,
 // J_0 = I_0 of Eq. (31), J_1 = s0 J_0 - (E1 - E0) / lambda.
-//  lambda >= 5: forward, as written;
-//  lambda <  5: downward (the recursion solved for J_(k-1)), whose error gain
-//               per step lambda (1 + |s0|) / (2k) is below one, from a start
-//               index Kp taken from c_kp and made warp-uniform, with the
+//  lambda >= 6: forward, as written;
+//  lambda <  6: downward (the recursion solved for J_(k-1)), which damps
+//               errors once k exceeds about lambda (1 + |s0|) / 2, from a
+//               start index Kp taken from c_kp32 and made warp-uniform, with the
 //               start values J_k ~ (E1 / (k + 1 - lambda (1 - t0))
 //               + (-1)^k E0 / (k + 1 - lambda t0)) / 2 (the mass of s^k near
 //               s = +-1); no erf is needed.
@@ -790,8 +846,8 @@ __device__ __forceinline__ void integrals_c32(float lam, float t0, float s0, flo
         for (int k = 1; k < K; ++k)
             J[k + 1] = fmaf(s0, J[k], fmaf((float)(2 * k) * il, J[k - 1], -((k & 1) ? Ep : Em) * il));
     } else {
-        const float g = lam * (1.0f + fabsf(s0)) * 0.5f;
-        int Kp = c_kp.v[min(63, (int)(g * 4.0f))];
+        const int bl = min(23, (int)(lam * 4.0f)), bs = min(7, (int)(fabsf(s0) * 2.0f));
+        int Kp = c_kp32.v[bl][bs];
         Kp = (int)__reduce_max_sync(__activemask(), (unsigned)Kp);
         const float l1 = lam * (1.0f - t0), l0 = lam * t0;
         float a1 = (float)(Kp + 2) - l1, b1 = (float)(Kp + 2) - l0;
@@ -832,17 +888,18 @@ __device__ __forceinline__ float i63_to_float(int64_t x)
 }
 
 // Error bound per unit of the sums' scale for the guard of FABF_C32: the
-// binary32 integrals carry up to ~2e-6 of max_k |J_k| in the regimes they are
+// binary32 integrals carry up to ~1e-5 of max_k |J_k| in the regimes they are
 // used in, the rest (moments, fit, sums) a few units of 2^-24.
-constexpr float kGuardUnitC32 = 4.0e-6f;
+constexpr float kGuardUnitC32 = 1.0e-5f;
 
 // Regimes where the binary32 integrals of integrals_c32 lose digits: a
-// range-kernel centre more than 0.75 kernel widths outside [0, 1] with
-// 2 < lambda < 20 (both recursion directions amplify there).
+// range-kernel centre more than half a kernel width outside [0, 1]
+// (sqrt(lambda) d > 0.5) with 2 < lambda < 20 (both recursion directions
+// amplify there).
 __device__ __forceinline__ bool c32_integrals_weak(float lam, float t0)
 {
     const float d = t0 < 0.0f ? -t0 : (t0 > 1.0f ? t0 - 1.0f : 0.0f);
-    return lam > 2.0f && lam < 20.0f && d * d * lam > 0.5625f;
+    return lam > 2.0f && lam < 20.0f && d * d * lam > 0.25f;
 }
 
 // The centred binary32 tail from commonly scaled centred moments v_k =

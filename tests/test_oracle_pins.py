@@ -220,6 +220,27 @@ def test_fit_matches_target_moments(oracle_mod, N):
             assert abs(mom - mu_ex[k]) <= Fraction(1, 10 ** 6) * mu_ex[0]
 
 
+@pytest.mark.parametrize("N", [0, 1, 3, 6])
+def test_fit_step_recovers_a_known_polynomial(oracle_mod, N):
+    """The fit step alone: given the exact moments mu_k = int_0^1 t^k p(t) dt
+    = sum_j c_j / (j + k + 1) of a polynomial p with small integer
+    coefficients (rounded once to binary64), the oracle's fit returns those
+    coefficients within the dot product's forward-error bound, and a common
+    scale of the moments scales the coefficients (the fit is linear)."""
+    rng = np.random.default_rng(90 + N)
+    c_true = [int(v) for v in rng.integers(-9, 10, N + 1)]
+    mu_ex = [sum(Fraction(c_true[j], j + k + 1) for j in range(N + 1)) for k in range(N + 1)]
+    mu = np.array([float(v) for v in mu_ex])
+    c = oracle_mod.fit(N, mu)
+    Ainv = scipy.linalg.invhilbert(N + 1, exact=True)
+    gamma = (N + 1) * U / (1 - (N + 1) * U)
+    for n in range(N + 1):
+        scale = sum(abs(int(Ainv[n][k])) * abs(mu_ex[k]) for k in range(N + 1))
+        assert abs(Fraction(c[n]) - c_true[n]) <= (Fraction(gamma) + 2 * U * (1 + Fraction(gamma))) * scale
+    c8 = oracle_mod.fit(N, mu * 8.0)       # a power-of-two scale is exact
+    assert np.array_equal(c8, 8.0 * c)
+
+
 # ---------------------------------------------------------------------------
 # Whole Algorithm 1: special cases with closed forms
 # ---------------------------------------------------------------------------
