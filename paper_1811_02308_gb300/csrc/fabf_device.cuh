@@ -316,16 +316,17 @@ __device__ __forceinline__ double fabf_pixel_fp64(const AinvTable& A, int alpha,
         for (int a = 0; a <= K - b; ++a) s[a] = s[a + 1] - (int64_t)alpha * s[a];
         M[b] = s[0];
     }
-    // Scaled moments mu'_k = d^K mu_k = M_k d^(K-k), mu_k = M_k / d^k of
-    // Eq. (24): exact integers (<= m_0 255^6 < 2^63), each rounded once to
-    // binary64 by the conversion, with no division.  The common factor d^K
-    // carries through the (linear) fit into c, T1 and T2 and cancels in the
-    // ratio of Eq. (29), and mu'_1 / mu'_0 = mu_1 / mu_0 for the fallback.
+    // mu_k = M_k / (beta - alpha)^k: one correctly rounded division of two
+    // binary64 values ((beta - alpha)^k <= 255^6 is exact).  The division
+    // stays (an exactly scaled integer M_k d^(K-k), rounded once, would save
+    // it): at N = 6 the fit amplifies a one-unit change in the last place of
+    // mu to ~1e-8 relative in g_hat, so the 1e-9 agreement with the oracle
+    // rests on the same operations in the same order.
     double mu[K + 1];
     int64_t dk = 1;
 #pragma unroll
-    for (int k = K; k >= 0; --k) {
-        mu[k] = (double)(M[k] * dk);
+    for (int k = 0; k <= K; ++k) {
+        mu[k] = (double)M[k] / (double)dk;
         dk *= d;
     }
     if (tr) {
@@ -770,7 +771,7 @@ static_assert(make_centred_inverse_table().err < 1e-6, "centred inverse entries 
 // the spectral radius of the step's homogeneous part,
 //   rho_k = (a + sqrt(a^2 + 4b)) / 2,  a = lambda |s0| / (2k), b = lambda / (2k).
 // Kp is the smallest index with prod_{k=9}^{Kp} rho_k < 1e-8, taken at the
-// upper corner of a bin of (lambda, |s0|) (bins of 1/4 in lambda < 6 and
+// upper corner of a bin of (lambda, |s0|) (bins of 1/4 in lambda < 8 and
 // 1/2 in |s0| < 4; K = 7, the largest top index -- smaller K only recurse
 // further past their last index).
 __host__ __device__ constexpr double ct_sqrt(double x)
@@ -781,13 +782,13 @@ __host__ __device__ constexpr double ct_sqrt(double x)
 }
 
 struct KpTableC32 {
-    unsigned char v[24][8];   // [lambda bin][|s0| bin]
+    unsigned char v[32][8];   // [lambda bin][|s0| bin]
 };
 
 __host__ __device__ constexpr KpTableC32 make_kp_table_c32()
 {
     KpTableC32 t{};
-    for (int i = 0; i < 24; ++i)
+    for (int i = 0; i < 32; ++i)
         for (int j = 0; j < 8; ++j) {
             const double lam = (i + 1) * 0.25, as0 = (j + 1) * 0.5;
             double p = 1.0;
@@ -805,7 +806,7 @@ __host__ __device__ constexpr KpTableC32 make_kp_table_c32()
 static __constant__ KpTableC32 c_kp32 = make_kp_table_c32();
 
 // lambda at and above which integrals_c32 recurses forward.
-constexpr float kLambdaForwardC32 = 6.0f;
+constexpr float kLambdaForwardC32 = 8.0f;
 
 // J_k = int_0^1 s^k exp(-lambda (t - t0)^2) dt, s = 2t - 1, k = 0..K, each
 // times exp(lambda d^2) with d the distance from t0 to [0, 1] (the factor is
@@ -814,8 +815,8 @@ constexpr float kLambdaForwardC32 = 6.0f;
 // s^k (s - s0) exp(...) -- as for Eq. (30) -- gives
 //   J_(k+1) = s0 J_k + (2k / lambda) J_(k-1) - (E1 - (-1)^k E0) / lambda,
 // J_0 = I_0 of Eq. (31), J_1 = s0 J_0 - (E1 - E0) / lambda.
-//  lambda >= 6: forward, as written;
-//  lambda <  6: downward (the recursion solved for J_(k-1)), which damps
+//  lambda >= 8: forward, as written;
+//  lambda <  8: downward (the recursion solved for J_(k-1)), which damps
 //               errors once k exceeds about lambda (1 + |s0|) / 2, from a
 //               start index Kp taken from c_kp32 and made warp-uniform, with the
 //               start values J_k ~ (E1 / (k + 1 - lambda (1 - t0))
@@ -846,7 +847,7 @@ __device__ __forceinline__ void integrals_c32(float lam, float t0, float s0, flo
         for (int k = 1; k < K; ++k)
             J[k + 1] = fmaf(s0, J[k], fmaf((float)(2 * k) * il, J[k - 1], -((k & 1) ? Ep : Em) * il));
     } else {
-        const int bl = min(23, (int)(lam * 4.0f)), bs = min(7, (int)(fabsf(s0) * 2.0f));
+        const int bl = min(31, (int)(lam * 4.0f)), bs = min(7, (int)(fabsf(s0) * 2.0f));
         int Kp = c_kp32.v[bl][bs];
         Kp = (int)__reduce_max_sync(__activemask(), (unsigned)Kp);
         const float l1 = lam * (1.0f - t0), l0 = lam * t0;
@@ -893,23 +894,28 @@ __device__ __forceinline__ float i63_to_float(int64_t x)
 constexpr float kGuardUnitC32 = 1.0e-5f;
 
 // Regimes where the binary32 integrals of integrals_c32 lose digits: a
-// range-kernel centre more than half a kernel width outside [0, 1]
-// (sqrt(lambda) d > 0.5) with 2 < lambda < 20 (both recursion directions
-// amplify there).
+// range-kernel centre more than one kernel width outside [0, 1]
+// (sqrt(lambda) d > 1) with 2.5 < lambda < 16 (both recursion directions
+// amplify there: up to ~1e-3 of max |J_k|; within 0.75 widths they hold
+// ~1e-5).
 __device__ __forceinline__ bool c32_integrals_weak(float lam, float t0)
 {
     const float d = t0 < 0.0f ? -t0 : (t0 > 1.0f ? t0 - 1.0f : 0.0f);
-    return lam > 2.0f && lam < 20.0f && d * d * lam > 0.25f;
+    return lam > 2.5f && lam < 16.0f && d * d * lam > 1.0f;
 }
 
 // The centred binary32 tail from commonly scaled centred moments v_k =
 // scale * mu~_k (|v_k| < 2^63, exact integers; the scale cancels in the
 // ratio).  Returns g_hat; sets redo when the pixel must be recomputed on the
-// FP64 path (T2 <= 0 or not finite, the error estimate above kFp32GuardGray,
-// or a weak integral regime).
+// FP64 path (the error estimate above kFp32GuardGray, T2 not clearly of one
+// sign, or a weak integral regime).  When T2 is negative by more than its
+// error estimate, the binary64 T2 is negative too and the pixel takes the
+// fallback of Eq. (29) (the sigma -> infinity limit): fb_mean, with fallback
+// set.
 template <int N>
 __device__ __forceinline__ float fabf_tail_c32(const int64_t (&v)[(N < 1 ? 1 : N) + 1], int alpha, int beta,
-                                               float theta_f, float sigma_f, bool& redo)
+                                               float theta_f, float sigma_f, float fb_mean, int& fallback,
+                                               bool& redo)
 {
     constexpr CentredInvTable kA = make_centred_inverse_table();
     float mu[N + 1];
@@ -943,7 +949,14 @@ __device__ __forceinline__ float fabf_tail_c32(const int64_t (&v)[(N < 1 ? 1 : N
     const float R = U / T2;
     const float hd = 0.5f * (float)d;
     const float est = kGuardUnitC32 * hd * (S1 + fabsf(R) * S2) / fabsf(T2);
-    redo = !(T2 > 0.0f) || !(est <= kFp32GuardGray) || c32_integrals_weak(lam, t0);
+    // T2 < 0 beyond its own error bound (kGuardUnitC32 S2, the bound the
+    // estimate uses): every precision agrees on the fallback
+    if (T2 < -kGuardUnitC32 * S2) {
+        fallback = 1;
+        redo = c32_integrals_weak(lam, t0);
+        return fb_mean;
+    }
+    redo = !(T2 > kGuardUnitC32 * S2) || !(est <= kFp32GuardGray) || c32_integrals_weak(lam, t0);
     return fmaf(hd, R, 0.5f * (float)(alpha + beta));
 }
 
@@ -966,13 +979,16 @@ __device__ __forceinline__ void centred_moments(int c0, const int64_t (&m)[K + 1
     }
 }
 
-// FABF_C32 at one pixel of the box path.
+// FABF_C32 at one pixel of the box path.  The fallback value is the window
+// mean m_1 / m_0 (the sigma -> infinity limit alpha + d mu_1 / mu_0; both
+// integers are exact in binary32 since m_1 <= 81^2 255 < 2^24).
 template <int N>
 __device__ __forceinline__ float fabf_pixel_c32(int alpha, int beta, int fi, const int64_t (&m)[(N < 1 ? 1 : N) + 1],
-                                                float theta_f, float sigma_f, bool& redo)
+                                                float theta_f, float sigma_f, int& fallback, bool& redo)
 {
     constexpr int K = N < 1 ? 1 : N;
     redo = false;
+    fallback = 0;
     if (alpha == beta) return (float)fi;
     const int d = beta - alpha;
     int64_t M[K + 1];
@@ -985,7 +1001,7 @@ __device__ __forceinline__ float fabf_pixel_c32(int alpha, int beta, int fi, con
         v[k] = (int64_t)((uint64_t)M[k] * (uint64_t)dp);
         dp *= d;
     }
-    return fabf_tail_c32<N>(v, alpha, beta, theta_f, sigma_f, redo);
+    return fabf_tail_c32<N>(v, alpha, beta, theta_f, sigma_f, (float)m[1] / (float)m[0], fallback, redo);
 }
 
 }  // namespace fabf

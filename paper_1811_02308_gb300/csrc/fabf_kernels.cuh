@@ -677,7 +677,7 @@ __device__ __forceinline__ bool fabf_tile(const CUtensorMap* tmap, const ImageJo
                             else if constexpr (PREC == kPrecCFP32)
                                 g = (double)fabf_pixel_cfp32<N>(c_ainv_split, alpha, beta, fi, m, th, sg, fb, redo);
                             else
-                                g = (double)fabf_pixel_c32<N>(alpha, beta, fi, m, th, sg, redo);
+                                g = (double)fabf_pixel_c32<N>(alpha, beta, fi, m, th, sg, fb, redo);
                             if (redo) {   // binary32 not accurate enough here: queue for the FP64 pass
                                 const unsigned slot = atomicAdd(redo_n, 1u);
                                 redo_list[slot] = (uint16_t)((rr << 8) | x);

@@ -205,10 +205,11 @@ __device__ __forceinline__ float sep_pixel_fp32(int alpha, int beta, int fi, con
 // m_0 d^K, is below 2^63; the common factor cancels in the ratio.
 template <int N>
 __device__ __forceinline__ float sep_pixel_c32(int alpha, int beta, int fi, const u128 (&m)[(N < 1 ? 1 : N) + 1],
-                                               float th, float sg, bool& redo)
+                                               float th, float sg, int& fallback, bool& redo)
 {
     constexpr int K = N < 1 ? 1 : N;
     redo = false;
+    fallback = 0;
     if (alpha == beta) return (float)fi;
     const int d = beta - alpha;
     const uint32_t c0 = (uint32_t)(alpha + beta);
@@ -236,7 +237,10 @@ __device__ __forceinline__ float sep_pixel_c32(int alpha, int beta, int fi, cons
     int64_t v[K + 1];
 #pragma unroll
     for (int k = 0; k <= K; ++k) v[k] = (int64_t)((__int128)sc[k] >> shift);
-    return fabf_tail_c32<N>(v, alpha, beta, th, sg, redo);
+    // fallback: the weighted window mean, alpha + d mu_1 / mu_0 with the
+    // binary32 ratio of the shifted centred moments (|v_1| <= v_0)
+    const float fb = fmaf(0.5f * (float)d, i63_to_float(v[1]) / i63_to_float(v[0]), 0.5f * (float)(alpha + beta));
+    return fabf_tail_c32<N>(v, alpha, beta, th, sg, fb, fallback, redo);
 }
 
 // The compensated form's FP64 redo (fabf_redo_scaled) from the separable
@@ -517,7 +521,7 @@ __device__ __forceinline__ void sep_tile(const CUtensorMap* tmap, const SepParam
                         } else {
                             bool redo = false;
                             if constexpr (PREC == kPrecC32)
-                                g = (double)sep_pixel_c32<N>(alpha, beta, fi, m, th, sg, redo);
+                                g = (double)sep_pixel_c32<N>(alpha, beta, fi, m, th, sg, fb, redo);
                             else
                                 g = (double)sep_pixel_fp32<N, PREC>(alpha, beta, fi, m, th, sg, fb, redo);
                             if (redo) {   // binary32 not accurate enough here: queue for the FP64 pass

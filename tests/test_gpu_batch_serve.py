@@ -110,16 +110,16 @@ def centred_integrals_reference(oracle_mod, lam, t0, K):
 
 
 def test_centred_integral_engine(ctx, oracle_mod):
-    """The centred binary32 engine of FABF_C32 (forward for lambda >= 6,
+    """The centred binary32 engine of FABF_C32 (forward for lambda >= 8,
     downward below) within 1e-5 of max_k |J_k| over lambda in [1e-4, 2e3]
-    with the centre inside [0, 1] or up to half a kernel width outside (the
-    regime it is used in; farther out and 2 < lambda < 20 the form hands the
-    pixel to the FP64 path), and up to 0.75 widths outside elsewhere."""
+    with the centre inside [0, 1] or up to 0.75 kernel widths outside (the
+    workloads reach 0.96 widths; beyond one width with 2.5 < lambda < 16 the
+    form hands the pixel to the FP64 path)."""
     pts = []
     for lam in np.geomspace(1e-4, 2e3, 40):
         sl = np.sqrt(lam)
-        far = [] if 2.0 < lam < 20.0 else [-0.75 / sl, 1 + 0.75 / sl]
-        for t in list(np.linspace(0, 1, 9)) + [-0.25 / sl, -0.5 / sl, 1 + 0.25 / sl, 1 + 0.5 / sl] + far:
+        for t in list(np.linspace(0, 1, 9)) + [-0.25 / sl, -0.5 / sl, -0.75 / sl, 1 + 0.25 / sl, 1 + 0.5 / sl,
+                                               1 + 0.75 / sl]:
             pts.append((lam, t))
     g = np.array(pts)
     K = 7

@@ -1,9 +1,8 @@
 """Parity of the CUDA path (through the C ABI) with the CPU oracle.
 
-Bar: integer stages (alpha, beta, m_k, M_k) bit-exact; the FP64 form's
-exactly scaled moments mu'_k = M_k d^(K-k) and its fit c bit-exact against
-the oracle's fit of the same moments (same IEEE operations in the same
-order), t0 and lambda bit-exact; the integrals I_k within 1e-12 relative inside the
+Bar: integer stages (alpha, beta, m_k, M_k) bit-exact; the FP64 shift-scale
+mu_k, fit c, t0 and lambda bit-exact (same IEEE operations in the same
+order on both sides); the integrals I_k within 1e-12 relative inside the
 workloads' domain; the output g_hat within 1e-9 relative (floor 1 gray
 level): |g_gpu - g_oracle| <= 1e-9 * max(|g_oracle|, 1)."""
 import numpy as np
@@ -82,17 +81,11 @@ def test_stages_match_oracle(ctx, oracle_mod, H, W, w, N, seed):
     if len(ys) > 600:
         pick = rng.choice(len(ys), 600, replace=False)
         ys, xs = ys[pick], xs[pick]
-    K = max(N, 1)
     for y, x in zip(ys, xs):
         tr = oracle_mod.fabf_trace(f, th, s, w, N, y, x)
-        # The kernel fits the exactly scaled moments mu'_k = d^K mu_k =
-        # M_k d^(K-k) (one rounding each, no division; the factor cancels in
-        # Eq. (29)): the same bits as the oracle's fit applied to them.
-        d = int(tr["beta"]) - int(tr["alpha"])
-        mu_s = np.array([float(int(tr["M"][k]) * d ** (K - k)) for k in range(N + 1)])
-        assert np.array_equal(mu[:, y, x], mu_s), (y, x)
-        assert np.array_equal(c[:, y, x], oracle_mod.fit(N, mu_s)), (y, x)
-        np.testing.assert_allclose(mu_s / float(d) ** K, tr["mu"], rtol=1e-15, atol=0)
+        assert np.array_equal(mu[:, y, x], tr["mu"]), (y, x)
+        assert np.array_equal(c[:, y, x], tr["c"]), (y, x)
+        assert np.array_equal(c[:, y, x], oracle_mod.fit(N, tr["mu"])), (y, x)
         assert t0lam[0, y, x] == tr["t0"] and t0lam[1, y, x] == tr["lam"]
         np.testing.assert_allclose(I[:, y, x], tr["I"], rtol=1e-12, atol=0)
         assert bool(flags[y, x] & 2) == tr["fallback"], (y, x, T[:, y, x], tr["T1"], tr["T2"])
