@@ -237,9 +237,9 @@ __device__ __forceinline__ float sep_pixel_c32(int alpha, int beta, int fi, cons
     int64_t v[K + 1];
 #pragma unroll
     for (int k = 0; k <= K; ++k) v[k] = (int64_t)((__int128)sc[k] >> shift);
-    // fallback: the weighted window mean, alpha + d mu_1 / mu_0 with the
-    // binary32 ratio of the shifted centred moments (|v_1| <= v_0)
-    const float fb = fmaf(0.5f * (float)d, i63_to_float(v[1]) / i63_to_float(v[0]), 0.5f * (float)(alpha + beta));
+    // fallback: the weighted window mean m_1 / m_0 (m_0 < 2^32, m_1 < 2^40),
+    // as the box path forms it
+    const float fb = (float)(int64_t)m[1] / (float)(int64_t)m[0];
     return fabf_tail_c32<N>(v, alpha, beta, th, sg, fb, fallback, redo);
 }
 
