@@ -121,7 +121,7 @@ constexpr int kTileCandidates[] = {8, 16, 24, 32, 40};
 constexpr int kPrecForms = 4;
 // FP64, FP64 fit + FP32, compensated FP32, centred binary32
 constexpr int kSteadyTileRows[kPrecForms] = {8, 8, 40, 40};
-constexpr int kMinWaves[kPrecForms] = {1, 1, 6, 6};
+constexpr int kMinWaves[kPrecForms] = {1, 1, 6, 3};
 // Resident CTAs per SM the kernels are compiled for (MinBlocks in
 // fabf_kernels.cuh); shared memory may allow fewer.
 constexpr int kCtasPerSm[kPrecForms] = {2, 4, 4, 4};

@@ -520,78 +520,66 @@ __device__ __forceinline__ bool fabf_tile(const CUtensorMap* tmap, const ImageJo
                 }
             }
         }
-        // 2b. Vertical extrema of column ce, on the threads the sums leave
-        //     idle (thread Cb + ce where it exists, else thread ce after its
-        //     sums), so the two run in different warps.
+        // 2b. Vertical extrema, four columns per thread: the bytes of tile
+        //     columns 4g .. 4g+3 are one 32-bit word, combined with per-byte
+        //     SIMD minimum / maximum.  G = Cb / 4 threads take the minima
+        //     (threads Cb .. Cb + G - 1, which the sums leave idle) and G the
+        //     maxima (threads 256 - G .. 255; Cb <= 160 keeps the two sets
+        //     apart), so each warp runs one of the two operations.
         {
             const int tid = (int)threadIdx.x;
-            const int ce = tid >= Cb ? tid - Cb : (tid + Cb >= kThreads ? tid : -1);
-            if (ce >= 0 && ce < Cb) {
-                const int Xe = xs + ce;
-                if (Xe >= 0 && Xe < J.W) {
-                    // Window of chunk row rr: tile rows [r0 + rr, r0 + rr + 2w]
-                    // = [r0 + rr, r0 + 7] u [r0 + 8, r0 + rr + 2w] (2w + 1 >= 8,
-                    // i.e. w >= 4): suffix extrema of the chunk's own rows, then
-                    // prefix extrema from r0 + 8 that grow by one row per rr --
-                    // 2w + 8 row visits per chunk.  For w < 4 every window is
-                    // visited directly (2w + 1 < 8 rows).  The suffix extrema
-                    // wait in this thread's own entries of the shared rows.
-                    uint8_t qmn = 255, qmx = 0;
-                    const bool split = 2 * w + 1 >= kChunk;
+            const int G = Cb >> 2;
+            const bool is_min = tid >= Cb && tid < Cb + G;
+            const bool is_max = tid >= kThreads - G;
+            if (is_min || is_max) {
+                const int g4 = 4 * (is_min ? tid - Cb : tid - (kThreads - G));
+                // bytes of columns outside the image take the identity (the
+                // staged tile holds 0 there)
+                uint32_t outside = 0u;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int Xe = xs + g4 + j;
+                    if (Xe < 0 || Xe >= J.W) outside |= 0xFFu << (8 * j);
+                }
+                const uint32_t ident = is_min ? 0xFFFFFFFFu : 0u;
+                auto op = [is_min](uint32_t x, uint32_t y) { return is_min ? __vminu4(x, y) : __vmaxu4(x, y); };
+                const uint32_t* tw = reinterpret_cast<const uint32_t*>(tile) + (g4 >> 2);
+                uint32_t* vw = reinterpret_cast<uint32_t*>(is_min ? vmin : vmax) + (g4 >> 2);
+                const int Cw = Cb >> 2;                     // words per tile row
+                // Window of chunk row rr: tile rows [r0 + rr, r0 + rr + 2w]
+                // = [r0 + rr, r0 + 7] u [r0 + 8, r0 + rr + 2w] (2w + 1 >= 8,
+                // i.e. w >= 4): suffix extrema of the chunk's own rows, then
+                // prefix extrema from r0 + 8 that grow by one row per rr --
+                // 2w + 8 row visits per chunk.  For w < 4 every window is
+                // visited directly (2w + 1 < 8 rows).  The suffix extrema
+                // wait in this thread's own words of the shared rows.
+                const bool split = 2 * w + 1 >= kChunk;
+                uint32_t q = ident;
+                if (split) {
+                    uint32_t acc = ident;
+#pragma unroll
+                    for (int rr = kChunk - 1; rr >= 0; --rr) {
+                        const int t = r0 + rr;
+                        if (t >= rowlo && t <= rowhi) acc = op(acc, tw[t * Cw]);
+                        vw[rr * Cw] = acc;
+                    }
+                    const int a = max(r0 + kChunk, rowlo), b = min(r0 + 2 * w, rowhi);
+                    for (int t = a; t <= b; ++t) q = op(q, tw[t * Cw]);
+                }
+#pragma unroll
+                for (int rr = 0; rr < kChunk; ++rr) {
+                    const int r = r0 + rr;
+                    uint32_t res;
                     if (split) {
-                        uint8_t mn = 255, mx = 0;
-#pragma unroll
-                        for (int rr = kChunk - 1; rr >= 0; --rr) {
-                            const int t = r0 + rr;
-                            if (t >= rowlo && t <= rowhi) {
-                                const uint8_t v = tile[t * Cb + ce];
-                                mn = v < mn ? v : mn;
-                                mx = v > mx ? v : mx;
-                            }
-                            vmin[rr * Cb + ce] = mn;
-                            vmax[rr * Cb + ce] = mx;
-                        }
-                        const int a = max(r0 + kChunk, rowlo), b = min(r0 + 2 * w, rowhi);
-                        for (int t = a; t <= b; ++t) {
-                            const uint8_t v = tile[t * Cb + ce];
-                            qmn = v < qmn ? v : qmn;
-                            qmx = v > qmx ? v : qmx;
-                        }
+                        const int t = r + 2 * w;            // the row entering the prefix part
+                        if (rr > 0 && t >= rowlo && t <= rowhi) q = op(q, tw[t * Cw]);
+                        res = op(vw[rr * Cw], q);
+                    } else {
+                        res = ident;
+                        const int a = max(r, rowlo), b = min(r + 2 * w, rowhi);
+                        for (int t = a; t <= b; ++t) res = op(res, tw[t * Cw]);
                     }
-#pragma unroll
-                    for (int rr = 0; rr < kChunk; ++rr) {
-                        const int r = r0 + rr;
-                        uint8_t mn, mx;
-                        if (split) {
-                            const int t = r + 2 * w;        // the row entering the prefix part
-                            if (rr > 0 && t >= rowlo && t <= rowhi) {
-                                const uint8_t v = tile[t * Cb + ce];
-                                qmn = v < qmn ? v : qmn;
-                                qmx = v > qmx ? v : qmx;
-                            }
-                            const uint8_t sn = vmin[rr * Cb + ce], sx = vmax[rr * Cb + ce];
-                            mn = sn < qmn ? sn : qmn;
-                            mx = sx > qmx ? sx : qmx;
-                        } else {
-                            mn = 255;
-                            mx = 0;
-                            const int a = max(r, rowlo), b = min(r + 2 * w, rowhi);
-                            for (int t = a; t <= b; ++t) {
-                                const uint8_t v = tile[t * Cb + ce];
-                                mn = v < mn ? v : mn;
-                                mx = v > mx ? v : mx;
-                            }
-                        }
-                        vmin[rr * Cb + ce] = mn;
-                        vmax[rr * Cb + ce] = mx;
-                    }
-                } else {
-                    // outside the image: the identities of min and max
-#pragma unroll
-                    for (int rr = 0; rr < kChunk; ++rr) {
-                        vmin[rr * Cb + ce] = 255;
-                        vmax[rr * Cb + ce] = 0;
-                    }
+                    vw[rr * Cw] = is_min ? (res | outside) : (res & ~outside);
                 }
             }
         }
