@@ -521,18 +521,18 @@ __device__ __forceinline__ bool fabf_tile(const CUtensorMap* tmap, const ImageJo
             }
         }
         // 2b. Vertical extrema, four columns per thread: the bytes of tile
-        //     columns 4g .. 4g+3 are one 32-bit word, combined with per-byte
-        //     SIMD minimum / maximum.  G = Cb / 4 threads take the minima
-        //     (threads Cb .. Cb + G - 1, which the sums leave idle) and G the
-        //     maxima (threads 256 - G .. 255; Cb <= 160 keeps the two sets
-        //     apart), so each warp runs one of the two operations.
+        //     columns 4g .. 4g+3 are one 32-bit word, split into two words
+        //     of 16-bit lanes (bytes 0, 2 and bytes 1, 3) that the native
+        //     16-bit SIMD minimum combines.  Thread Cb + 2g takes the minima
+        //     of group g and thread Cb + 2g + 1 the maxima, as minima of the
+        //     complemented bytes (255 - v reverses the order), so the two run
+        //     the same instructions; these threads are the ones the sums
+        //     leave idle (Cb / 2 <= 256 - Cb for Cb <= 160).
         {
-            const int tid = (int)threadIdx.x;
-            const int G = Cb >> 2;
-            const bool is_min = tid >= Cb && tid < Cb + G;
-            const bool is_max = tid >= kThreads - G;
-            if (is_min || is_max) {
-                const int g4 = 4 * (is_min ? tid - Cb : tid - (kThreads - G));
+            const int e = (int)threadIdx.x - Cb;
+            if (e >= 0 && e < (Cb >> 1)) {
+                const int g4 = 4 * (e >> 1);
+                const uint32_t inv = (e & 1) ? 0xFFFFFFFFu : 0u;   // maxima: complemented bytes
                 // bytes of columns outside the image take the identity (the
                 // staged tile holds 0 there)
                 uint32_t outside = 0u;
@@ -541,11 +541,16 @@ __device__ __forceinline__ bool fabf_tile(const CUtensorMap* tmap, const ImageJo
                     const int Xe = xs + g4 + j;
                     if (Xe < 0 || Xe >= J.W) outside |= 0xFFu << (8 * j);
                 }
-                const uint32_t ident = is_min ? 0xFFFFFFFFu : 0u;
-                auto op = [is_min](uint32_t x, uint32_t y) { return is_min ? __vminu4(x, y) : __vmaxu4(x, y); };
                 const uint32_t* tw = reinterpret_cast<const uint32_t*>(tile) + (g4 >> 2);
-                uint32_t* vw = reinterpret_cast<uint32_t*>(is_min ? vmin : vmax) + (g4 >> 2);
+                uint32_t* vw = reinterpret_cast<uint32_t*>((e & 1) ? vmax : vmin) + (g4 >> 2);
                 const int Cw = Cb >> 2;                     // words per tile row
+                // running minima as (even bytes, odd bytes) in 16-bit lanes
+                auto add = [&](uint32_t& m0, uint32_t& m1, int t) {
+                    const uint32_t v = tw[t * Cw] ^ inv;
+                    m0 = __vminu2(m0, __byte_perm(v, 0u, 0x4240));
+                    m1 = __vminu2(m1, __byte_perm(v, 0u, 0x4341));
+                };
+                constexpr uint32_t kId = 0x00FF00FFu;
                 // Window of chunk row rr: tile rows [r0 + rr, r0 + rr + 2w]
                 // = [r0 + rr, r0 + 7] u [r0 + 8, r0 + rr + 2w] (2w + 1 >= 8,
                 // i.e. w >= 4): suffix extrema of the chunk's own rows, then
@@ -554,32 +559,46 @@ __device__ __forceinline__ bool fabf_tile(const CUtensorMap* tmap, const ImageJo
                 // visited directly (2w + 1 < 8 rows).  The suffix extrema
                 // wait in this thread's own words of the shared rows.
                 const bool split = 2 * w + 1 >= kChunk;
-                uint32_t q = ident;
+                uint32_t q0 = kId, q1 = kId;
                 if (split) {
-                    uint32_t acc = ident;
+                    uint32_t s0 = kId, s1 = kId;
 #pragma unroll
                     for (int rr = kChunk - 1; rr >= 0; --rr) {
                         const int t = r0 + rr;
-                        if (t >= rowlo && t <= rowhi) acc = op(acc, tw[t * Cw]);
-                        vw[rr * Cw] = acc;
+                        if (t >= rowlo && t <= rowhi) add(s0, s1, t);
+                        vw[rr * Cw] = __byte_perm(s0, s1, 0x6240);
                     }
+                    // rows r0 + 8 .. r0 + 2w in two independent chains
                     const int a = max(r0 + kChunk, rowlo), b = min(r0 + 2 * w, rowhi);
-                    for (int t = a; t <= b; ++t) q = op(q, tw[t * Cw]);
+                    uint32_t p0 = kId, p1 = kId;
+                    int t = a;
+                    for (; t + 1 <= b; t += 2) {
+                        add(q0, q1, t);
+                        add(p0, p1, t + 1);
+                    }
+                    if (t <= b) add(q0, q1, t);
+                    q0 = __vminu2(q0, p0);
+                    q1 = __vminu2(q1, p1);
                 }
 #pragma unroll
                 for (int rr = 0; rr < kChunk; ++rr) {
                     const int r = r0 + rr;
-                    uint32_t res;
+                    uint32_t m0, m1;
                     if (split) {
                         const int t = r + 2 * w;            // the row entering the prefix part
-                        if (rr > 0 && t >= rowlo && t <= rowhi) q = op(q, tw[t * Cw]);
-                        res = op(vw[rr * Cw], q);
+                        if (rr > 0 && t >= rowlo && t <= rowhi) add(q0, q1, t);
+                        const uint32_t sv = vw[rr * Cw];
+                        m0 = __vminu2(q0, __byte_perm(sv, 0u, 0x4240));
+                        m1 = __vminu2(q1, __byte_perm(sv, 0u, 0x4341));
                     } else {
-                        res = ident;
+                        m0 = kId;
+                        m1 = kId;
                         const int a = max(r, rowlo), b = min(r + 2 * w, rowhi);
-                        for (int t = a; t <= b; ++t) res = op(res, tw[t * Cw]);
+                        for (int t = a; t <= b; ++t) add(m0, m1, t);
                     }
-                    vw[rr * Cw] = is_min ? (res | outside) : (res & ~outside);
+                    // back from the complement for the maxima; outside
+                    // columns get 255 (minima) or 0 (maxima)
+                    vw[rr * Cw] = ((__byte_perm(m0, m1, 0x6240) | outside) ^ inv);
                 }
             }
         }
