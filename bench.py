@@ -367,11 +367,22 @@ def psnr(a, b):
     return float("inf") if mse == 0 else 10.0 * math.log10(255.0 ** 2 / mse)
 
 
-def run_batch(R, prec, steps, seed=2000, n_images=64):
+def run_batch(R, prec, steps, seed=2000, n_images=64, autotune=True):
     """Config 2: 64 images, H in logU[128, 1536], W in logU[128, 2048],
     w in {3..30}, N in {4, 5, 6}, fields as config 1; one persistent launch
-    per step replayed from the captured CUDA graph."""
+    per step replayed from the captured CUDA graph.  With autotune, the batch
+    runs on a context whose autotuner picks each (w, N) key's tile height
+    and tile staging (timed on a synthetic 2048x4096 image when the graph is
+    first built, outside the timed steps)."""
     torch, fabf = R.torch, R.fabf
+    if autotune:
+        with fabf.Context(device=R.ctx.device, precision=prec, autotune=1) as tctx:
+            t0 = time.perf_counter()
+            out = run_batch(Runner(torch, fabf, tctx, R.dev), prec, steps, seed, n_images, autotune=False)
+            out["autotune"] = True
+            out["tune_and_capture_s"] = out.pop("build_s")
+            out["total_s"] = time.perf_counter() - t0
+            return out
     rng = np.random.default_rng(seed)
     reqs, keep, npix = [], [], 0
     for i in range(n_images):
@@ -393,20 +404,22 @@ def run_batch(R, prec, steps, seed=2000, n_images=64):
         if rc != 0:
             raise fabf.FabfError(rc, "fabf_filter_batch")
 
+    t_build = time.perf_counter()
+    step(0)                                   # autotune (if on) and graph capture
+    torch.cuda.synchronize(R.dev)
+    t_build = time.perf_counter() - t_build
     total_ms, _ = R.timed(step, steps, 3)
     caps, launches = fabf.fabf_batch_stats(R.ctx)
     fabf.fabf_set_precision(R.ctx, 0)
     return {"form": FORM_NAMES[prec], "images": n_images, "mpix_per_batch": npix / 1e6,
             "value": npix * steps / (total_ms / 1e3) / 1e6, "unit": "Mpix/s",
-            "ms_per_batch": total_ms / steps, "graph_captures": caps, "graph_launches": launches}
+            "ms_per_batch": total_ms / steps, "graph_captures": caps, "graph_launches": launches,
+            "autotune": False, "build_s": t_build}
 
 
-def run_serve(R, prec, seconds, rate=200.0, seed=4000, pool_size=16):
-    """Config 4: Poisson arrivals (mean `rate` req/s), sizes log-uniform
-    256^2..4096^2, w in {5..40}, N in {4, 5, 6}, 1-3 passes, 16 GB budget.
-    Inputs are drawn from a pool of pre-generated images in pinned host
-    memory; latency is arrival -> completion seen by the poller."""
-    torch, fabf = R.torch, R.fabf
+def serve_pool(torch, seed=4000, pool_size=16):
+    """Config 4's request images: sizes log-uniform 256^2..4096^2, fields as
+    config 1, in pinned host memory (with two pinned outputs each)."""
     rng = np.random.default_rng(seed)
     pool = []
     for i in range(pool_size):
@@ -416,6 +429,19 @@ def run_serve(R, prec, seconds, rate=200.0, seed=4000, pool_size=16):
         pool.append((torch.from_numpy(f).pin_memory(), torch.from_numpy(th).pin_memory(),
                      torch.from_numpy(s).pin_memory(),
                      [torch.empty((H, W), dtype=torch.float32).pin_memory() for _ in range(2)]))
+    return pool
+
+
+def run_serve(R, prec, seconds, rate=200.0, seed=4000, pool=None):
+    """Config 4: Poisson arrivals (mean `rate` req/s), sizes log-uniform
+    256^2..4096^2, w in {5..40}, N in {4, 5, 6}, 1-3 passes, 16 GB budget.
+    Inputs are drawn from a pool of pre-generated images in pinned host
+    memory; latency is arrival -> completion seen by the poller."""
+    torch, fabf = R.torch, R.fabf
+    rng = np.random.default_rng(seed + int(rate))
+    if pool is None:
+        pool = serve_pool(torch, seed)
+    pool_size = len(pool)
     with fabf.Context(device=R.ctx.device, precision=prec, mem_budget_bytes=16 << 30) as sctx:
         # warm up the kernels and the serving worker
         f, th, s, ob = pool[0]
@@ -479,10 +505,23 @@ def run_serve(R, prec, seconds, rate=200.0, seed=4000, pool_size=16):
         wall = time.perf_counter() - t0
     lat_ms = np.array(lat) * 1e3
     return {"form": FORM_NAMES[prec], "requests": int(len(lat)), "offered_rate": rate,
+            "achieved_rate": len(lat) / wall,
             "seconds": wall, "p50_ms": float(np.percentile(lat_ms, 50)),
             "p99_ms": float(np.percentile(lat_ms, 99)), "mean_ms": float(lat_ms.mean()),
             "value": pix_passes[0] / wall / 1e6, "unit": "Mpix/s (pixel-passes)",
             "eagain_retries": eagain[0], "budget_bytes": 16 << 30}
+
+
+def serve_legs(R, prec, seconds, sweep_rates=(800.0, 2000.0, 4000.0), sweep_seconds=5.0):
+    """Config 4 at its 200 req/s for `seconds`, then a saturation sweep of
+    higher offered rates (p50 / p99 latency and served Mpix/s at each)."""
+    pool = serve_pool(R.torch)
+    main = run_serve(R, prec, seconds, 200.0, pool=pool)
+    main["saturation_sweep"] = [
+        {k: v for k, v in run_serve(R, prec, sweep_seconds, r, pool=pool).items()
+         if k in ("offered_rate", "achieved_rate", "requests", "p50_ms", "p99_ms", "value", "eagain_retries")}
+        for r in sweep_rates]
+    return main
 
 
 def run_gaussian(R, slots, steps, rhos=(3.0, 5.0), N=NDEG):
@@ -665,43 +704,81 @@ def sweep(args):
     return 0
 
 
-def precision_report(n_sample=20000):
-    """Config 3: 4096x4096 (2000 blobs), w = 20, N in {5, 6}, sigma in
-    [5, 60]; every form's max / RMS error against the FP64 CPU oracle on a
-    random pixel sample, and PSNR of the whole image against the GPU FP64
-    brute-force filter."""
-    import torch
+def config1_sweep(R, slots, best, steps, ws_=(5, 20, 40), Ns=(3, 5, 6)):
+    """Config 1 on the same rotating 1920x1080 inputs at w in {5, 20, 40}
+    and N in {3, 5, 6}: Mpix/s of the plain FP64 form and of the headline
+    form, with the headline form's FP64-redo fraction."""
+    fabf = R.fabf
+    out = {"workload": WORKLOAD.replace("box w=20, N=5", "box w, N as keyed"), "steps": steps}
+    for w in ws_:
+        for N in Ns:
+            row = {}
+            for prec in (0, best):
+                fabf.fabf_set_precision(R.ctx, prec)
+                sl = slots[prec]
+                total_ms, _ = R.timed(lambda i: R.filt(sl[i % len(sl)], w, N), steps, 3)
+                st, nfb, nredo = fabf.fabf_get_status_ex(R.ctx, R.sh)
+                row[FORM_NAMES[prec]] = H_ * W_ * steps / (total_ms / 1e3) / 1e6
+                if prec == best:
+                    row["redo_frac_" + FORM_NAMES[prec]] = nredo / ((steps + 3) * H_ * W_)
+            out["w=%d,N=%d" % (w, N)] = row
+    fabf.fabf_set_precision(R.ctx, 0)
+    return out
 
+
+def accuracy_vs_oracle(R, slots, n_sample=4000):
+    """Every form's error against the CPU oracle, on oracle samples: the
+    timed 1920x1080 workload (w = 20, N in {5, 6}; random pixels, borders and
+    tile seams) and the 4096x4096 precision workload (2000 blobs, theta = f,
+    w = 20, N in {5, 6}; random pixels), with each form's PSNR against the
+    GPU FP64 brute force on the whole 4096x4096 image."""
     import oracle
-    from paper_1811_02308_gb300 import build, fabf, synth
-    build.build()
+    from paper_1811_02308_gb300 import synth
+    torch, fabf = R.torch, R.fabf
     oracle.build()
+    rep = {"sample_pixels": n_sample}
+    # timed workload
+    f0, th0, s0 = (a.cpu().numpy() for a in slots[0][0][:3])
+    rng = np.random.default_rng(71)
+    seam_r = np.array([r for k in range(1, H_ // 8 + 1) for r in (8 * k - 1, 8 * k) if r < H_])
+    seam_c = np.array([c for k in range(1, W_ // 64 + 1) for c in (64 * k - 1, 64 * k) if c < W_])
+    ys = np.concatenate([rng.integers(0, H_, n_sample), np.zeros(64, int), np.full(64, H_ - 1),
+                         rng.integers(0, H_, 128), seam_r, rng.integers(0, H_, len(seam_c))])
+    xs = np.concatenate([rng.integers(0, W_, n_sample), rng.integers(0, W_, 128), np.zeros(64, int),
+                         np.full(64, W_ - 1), rng.integers(0, W_, len(seam_r)), seam_c])
+    for N in (NDEG, 6):
+        ref, _ = oracle.fabf_pixels(f0, th0, s0, WR, N, ys, xs)
+        row = {}
+        for prec in FORMS:
+            fabf.fabf_set_precision(R.ctx, prec)
+            o = slots[prec][0][3]
+            R.filt((*slots[0][0][:3], o), WR, N)
+            g = o.cpu().numpy()[ys, xs].astype(np.float64)
+            e = np.abs(g - ref)
+            row[FORM_NAMES[prec]] = {"max_abs": float(e.max()), "rms": float(np.sqrt(np.mean(e * e))),
+                                     "max_rel": float(np.max(e / np.maximum(np.abs(ref), 1.0)))}
+        rep["1920x1080 w=%d N=%d" % (WR, N)] = row
+    # 4096x4096 precision workload
     f, th, s = synth.make_inputs(4096, 4096, synth.config_seed(3, 0), n_blobs=2000, zeta_range=None,
                                  sigma_range=(5, 60))
-    d = [torch.from_numpy(a).cuda() for a in (f, th, s)]
-    rng = np.random.default_rng(3)
+    d = [torch.from_numpy(a).to(R.dev) for a in (f, th, s)]
+    bf = fabf.fabf_bruteforce(R.ctx, d[0], d[1], d[2], 20, use_f64=True).cpu().numpy()
     ys, xs = rng.integers(0, 4096, n_sample), rng.integers(0, 4096, n_sample)
-    rep = {"workload": "4096x4096 uint8 synthetic (2000 blobs), box w=20, theta=f, sigma in [5,60]",
-           "sample_pixels": n_sample}
-    with fabf.Context(device=0) as ctx:
-        bf = fabf.fabf_bruteforce(ctx, d[0], d[1], d[2], 20, use_f64=True).cpu().numpy()
-        for N in (5, 6):
-            ref, _ = oracle.fabf_pixels(f, th, s, 20, N, ys, xs)
-            row = {}
-            for prec in FORMS:
-                fabf.fabf_set_precision(ctx, prec)
-                g = fabf.fabf_filter(ctx, d[0], d[1], d[2], 20, N, out_is_f64=(prec == 0)).cpu().numpy()
-                st, nfb, nredo = fabf.fabf_get_status_ex(ctx)
-                e = np.abs(g[ys, xs].astype(np.float64) - ref)
-                row[FORM_NAMES[prec]] = {"max_abs_vs_oracle": float(e.max()),
-                                         "rms_vs_oracle": float(np.sqrt(np.mean(e * e))),
-                                         "max_rel_vs_oracle": float(np.max(e / np.maximum(np.abs(ref), 1))),
-                                         "psnr_vs_bruteforce_db": psnr(g, bf),
-                                         "fallback_frac": nfb / g.size, "fp64_redo_frac": nredo / g.size,
-                                         "status": st}
-            rep["N=%d" % N] = row
-    print(json.dumps({"precision_report": rep}), flush=True)
-    return 0
+    for N in (5, 6):
+        ref, _ = oracle.fabf_pixels(f, th, s, 20, N, ys, xs)
+        row = {}
+        for prec in FORMS:
+            fabf.fabf_set_precision(R.ctx, prec)
+            g = fabf.fabf_filter(R.ctx, d[0], d[1], d[2], 20, N, out_is_f64=(prec == 0)).cpu().numpy()
+            st, nfb, nredo = fabf.fabf_get_status_ex(R.ctx)
+            e = np.abs(g[ys, xs].astype(np.float64) - ref)
+            row[FORM_NAMES[prec]] = {"max_abs": float(e.max()), "rms": float(np.sqrt(np.mean(e * e))),
+                                     "max_rel": float(np.max(e / np.maximum(np.abs(ref), 1.0))),
+                                     "psnr_vs_bruteforce_db": psnr(g, bf), "fp64_redo_frac": nredo / g.size,
+                                     "status": st}
+        rep["4096x4096 w=20 N=%d" % N] = row
+    fabf.fabf_set_precision(R.ctx, 0)
+    return rep
 
 
 def main():
@@ -720,21 +797,16 @@ def main():
     ap.add_argument("--profile-precision", type=int, default=0, choices=[0, 1, 2, 3])
     ap.add_argument("--profile-rho", type=float, default=None,
                     help="with --profile: the separable Gaussian kernel of this rho instead of the box")
-    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--serve-seconds", type=float, default=30.0)
     ap.add_argument("--no-extra", action="store_true", help="skip the batch and serve legs")
     ap.add_argument("--sweep", action="store_true",
                     help="1920x1080: every form for w in {5,10,20,40} x N in {3..6}, plus the GPU "
                          "brute force per w; prints one JSON line")
-    ap.add_argument("--precision-report", action="store_true",
-                    help="4096x4096 w=20 N in {5,6}: each form's error against the FP64 oracle "
-                         "(sampled pixels) and PSNR against the GPU brute force; prints one JSON line")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return reference_arm(args)
-    if args.precision_report:
-        return precision_report()
     if args.sweep:
         return sweep(args)
 
@@ -900,8 +972,12 @@ def main():
         line["gaussian"] = run_gaussian(R, slots, max(10, args.steps // 10))
         line["applications"] = run_apps(R, slots, max(10, args.steps // 10), forms=(0, best))
         line["batch"] = {FORM_NAMES[p]: run_batch(R, p, max(5, args.steps // 20)) for p in (0, best)}
-        line["serve"] = run_serve(R, best, args.serve_seconds)
+        line["serve"] = serve_legs(R, best, args.serve_seconds)
+        line["config1_sweep"] = config1_sweep(R, slots, best, max(10, args.steps // 2))
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        # the oracle's leg: its speed on the host cores, and every form's
+        # error against it
+        line["accuracy_vs_oracle"] = accuracy_vs_oracle(R, slots)
         line["cpu_baseline"] = cpu_baseline(host[0])
         line["cpu_baseline_all_cores"] = cpu_baseline_all_cores()
     if rank == 0:

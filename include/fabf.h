@@ -78,7 +78,7 @@ typedef struct {
     int device;                  /* CUDA device ordinal */
     size_t mem_budget_bytes;     /* device bytes the serving loop may hold (0 = 16 GiB) */
     int precision;               /* fabf_precision used by fabf_filter / batch / serve */
-    int autotune;                /* nonzero: pick tile shapes by measurement */
+    int autotune;                /* nonzero: pick tile shapes and staging by measurement */
     const char* tune_cache_path; /* optional file for autotuner results (may be NULL) */
 } fabf_config;
 
@@ -185,13 +185,16 @@ int fabf_batch_stats(fabf_ctx* ctx, int* graph_captures, int* graph_launches);
 
 /* Steady-state output rows per tile (many tiles in flight, as in a batch)
  * the context uses for (w, N, precision): the autotuner's measured choice
- * among 8, 16, 24, 32 and 40 when autotune is on (the first query of a key
- * times each candidate on a synthetic 2048x4096 image and caches the result,
- * in tune_cache_path too), else 8 (FABF_FP64, FABF_FP64FIT_FP32REC) or 40
- * (FABF_CFP32).  A single-image call uses the tallest candidate no taller
- * than this that still fills the SMs with at least 6 waves of resident CTAs
- * (compensated form), else 8.  Make the first query of a key
- * before any stream capture. */
+ * among 8, 16, 24, 32 and 40 when autotune is on, else 8 (FABF_FP64,
+ * FABF_FP64FIT_FP32REC) or 40 (FABF_CFP32, FABF_C32).  The autotuner's first
+ * query of a key times every candidate height with each tile staging (TMA
+ * tensor copies, and plain cooperative loads) on a synthetic 2048x4096 image
+ * in the form's own output type, keeps the fastest pair, and caches it (in
+ * tune_cache_path too, as lines "w N precision rows ms plain").  A
+ * single-image call uses the tallest candidate no taller than this that
+ * still fills the SMs with at least 6 (FABF_CFP32) or 3 (FABF_C32) waves of
+ * resident CTAs, else 8.  Make the first query of a key before any stream
+ * capture. */
 int fabf_tile_rows(fabf_ctx* ctx, int w, int N, int precision, int* tile_rows);
 
 /* Text of a fabf_status value (static storage). */

@@ -141,7 +141,7 @@ cudaError_t launch_batch(int prec, const BatchParams& p, int grid, size_t smem, 
 }
 
 size_t make_job(ImageJob* J, CUtensorMap* tm, const uint8_t* img, size_t pitch, const float* theta,
-                const float* sigma, int H, int W, int w, int N, void* out, int out_f64, int TH)
+                const float* sigma, int H, int W, int w, int N, void* out, int out_f64, int TH, bool allow_tma)
 {
     std::memset(J, 0, sizeof(*J));
     J->img = img;
@@ -159,7 +159,7 @@ size_t make_job(ImageJob* J, CUtensorMap* tm, const uint8_t* img, size_t pitch, 
     J->tiles_x = (W + kTileW - 1) / kTileW;
     J->tiles_y = (H + TH - 1) / TH;
     std::memset(tm, 0, sizeof(*tm));
-    J->use_tma = encode_image_tmap(tm, img, H, W, pitch, J->Cb, TH + 2 * w) ? 1 : 0;
+    J->use_tma = allow_tma && encode_image_tmap(tm, img, H, W, pitch, J->Cb, TH + 2 * w) ? 1 : 0;
     return fused_smem_bytes(N, w, J->Cb, TH);
 }
 
@@ -202,13 +202,14 @@ int read_and_clear_status(fabf_ctx* ctx, cudaStream_t s, int* status, uint64_t* 
 
 int run_fused_prec(fabf_ctx* ctx, int prec, const uint8_t* img, size_t pitch, const float* theta,
                    const float* sigma, int H, int W, int w, int N, void* out, int out_f64, int TH,
-                   const DebugPlanes* dbg, unsigned* status, unsigned long long* nfb, cudaStream_t s)
+                   const DebugPlanes* dbg, unsigned* status, unsigned long long* nfb, cudaStream_t s,
+                   bool allow_tma)
 {
     (void)ctx;
     FusedParams p;
     std::memset(&p, 0, sizeof(p));
     CUtensorMap tm;
-    const size_t smem = make_job(&p.job, &tm, img, pitch, theta, sigma, H, W, w, N, out, out_f64, TH);
+    const size_t smem = make_job(&p.job, &tm, img, pitch, theta, sigma, H, W, w, N, out, out_f64, TH, allow_tma);
     p.status = status;
     p.n_fallback = nfb;
     if (dbg) p.dbg = *dbg;
@@ -224,7 +225,7 @@ int run_fused(fabf_ctx* ctx, const uint8_t* img, size_t pitch, const float* thet
     const int prec = dbg ? kPrecFP64 : ctx->precision;
     const int TH = dbg ? kDefaultTileRows : tile_rows_for(ctx, w, N, prec, H, W);
     return run_fused_prec(ctx, prec, img, pitch, theta, sigma, H, W, w, N, out, out_f64, TH, dbg,
-                          ctx->d_status, ctx->d_nfb, s);
+                          ctx->d_status, ctx->d_nfb, s, dbg ? true : tile_staging_tma(ctx, w, N, prec));
 }
 
 // Launch the fused FP64 kernel on device buffers with caller-provided status

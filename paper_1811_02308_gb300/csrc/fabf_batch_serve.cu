@@ -100,23 +100,31 @@ void load_tune_cache(fabf_ctx* ctx)
     if (ctx->tune_cache_path.empty() || !ctx->tune.empty()) return;
     FILE* fp = std::fopen(ctx->tune_cache_path.c_str(), "r");
     if (!fp) return;
-    int w, N, prec, TH;
-    float ms;
-    while (std::fscanf(fp, "%d %d %d %d %f", &w, &N, &prec, &TH, &ms) == 5)
-        if (TH >= 8 && TH <= kTileHMax && TH % 8 == 0) ctx->tune[tune_key(w, N, prec)] = TuneEntry{TH, ms};
+    // lines "w N precision TH ms [plain]" (plain staging flag optional, 0 = TMA)
+    char line[256];
+    while (std::fgets(line, sizeof(line), fp)) {
+        int w, N, prec, TH, plain = 0;
+        float ms;
+        const int n = std::sscanf(line, "%d %d %d %d %f %d", &w, &N, &prec, &TH, &ms, &plain);
+        if (n >= 5 && TH >= 8 && TH <= kTileHMax && TH % 8 == 0)
+            ctx->tune[tune_key(w, N, prec)] = TuneEntry{TH, ms, plain ? 1 : 0};
+    }
     std::fclose(fp);
 }
 
 }  // namespace
 
-static int steady_tile_rows(fabf_ctx* ctx, int w, int N, int prec)
+// The tuned (or default) tile shape and staging of (w, N, prec).  With
+// autotune on, the first query of a key times every candidate height with
+// each staging (TMA and plain cooperative loads) and keeps the fastest.
+static TuneEntry tune_entry(fabf_ctx* ctx, int w, int N, int prec)
 {
-    const int dflt = kSteadyTileRows[prec_index(prec)];
+    const TuneEntry dflt{kSteadyTileRows[prec_index(prec)], 0.0f, 0};
     if (!ctx || !ctx->autotune) return dflt;
     load_tune_cache(ctx);
     std::lock_guard<std::mutex> g(ctx->tune_lock);
     auto it = ctx->tune.find(tune_key(w, N, prec));
-    if (it != ctx->tune.end()) return it->second.TH;
+    if (it != ctx->tune.end()) return it->second;
 
     // the timing image lives only for this measurement (about 140 MB)
     TuneImage timg;
@@ -134,41 +142,55 @@ static int steady_tile_rows(fabf_ctx* ctx, int w, int N, int prec)
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    int best = dflt;
+    int best = dflt.TH, best_plain = 0;
     float best_ms = 1e30f;
-    for (int TH : kTileCandidates) {
-        float ms = 1e30f;
-        bool ok = true;
-        for (int rep = 0; rep < 4 && ok; ++rep) {
-            cudaEventRecord(e0, s);
-            // the form's own output type: float64 for FP64, float32 otherwise
-            ok = run_fused_prec(ctx, prec, t->img, kTuneW, t->theta, t->sigma, kTuneH, kTuneW, w, N, t->out,
-                                prec == kPrecFP64 ? 1 : 0, TH, nullptr, t->status, t->nfb, s) == FABF_OK;
-            cudaEventRecord(e1, s);
-            if (cudaEventSynchronize(e1) != cudaSuccess) ok = false;
-            float m = 0.0f;
-            cudaEventElapsedTime(&m, e0, e1);
-            if (rep > 0) ms = std::min(ms, m);      // first run is the warm-up
+    for (int plain = 0; plain < 2; ++plain)
+        for (int TH : kTileCandidates) {
+            float ms = 1e30f;
+            bool ok = true;
+            for (int rep = 0; rep < 4 && ok; ++rep) {
+                cudaEventRecord(e0, s);
+                // the form's own output type: float64 for FP64, float32 otherwise
+                ok = run_fused_prec(ctx, prec, t->img, kTuneW, t->theta, t->sigma, kTuneH, kTuneW, w, N, t->out,
+                                    prec == kPrecFP64 ? 1 : 0, TH, nullptr, t->status, t->nfb, s,
+                                    plain == 0) == FABF_OK;
+                cudaEventRecord(e1, s);
+                if (cudaEventSynchronize(e1) != cudaSuccess) ok = false;
+                float m = 0.0f;
+                cudaEventElapsedTime(&m, e0, e1);
+                if (rep > 0) ms = std::min(ms, m);      // first run is the warm-up
+            }
+            if (ok && ms < best_ms) {
+                best_ms = ms;
+                best = TH;
+                best_plain = plain;
+            }
         }
-        if (ok && ms < best_ms) {
-            best_ms = ms;
-            best = TH;
-        }
-    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaStreamDestroy(s);
     free_tune_image(timg);
     (void)cudaGetLastError();
-    ctx->tune[tune_key(w, N, prec)] = TuneEntry{best, best_ms};
+    const TuneEntry got{best, best_ms, best_plain};
+    ctx->tune[tune_key(w, N, prec)] = got;
     if (!ctx->tune_cache_path.empty()) {
         FILE* fp = std::fopen(ctx->tune_cache_path.c_str(), "a");
         if (fp) {
-            std::fprintf(fp, "%d %d %d %d %.5f\n", w, N, prec, best, best_ms);
+            std::fprintf(fp, "%d %d %d %d %.5f %d\n", w, N, prec, best, best_ms, best_plain);
             std::fclose(fp);
         }
     }
-    return best;
+    return got;
+}
+
+static int steady_tile_rows(fabf_ctx* ctx, int w, int N, int prec)
+{
+    return tune_entry(ctx, w, N, prec).TH;
+}
+
+bool tile_staging_tma(fabf_ctx* ctx, int w, int N, int prec)
+{
+    return tune_entry(ctx, w, N, prec).plain == 0;
 }
 
 int tile_rows_for(fabf_ctx* ctx, int w, int N, int prec, int H, int W)
@@ -274,7 +296,7 @@ static int batch_build(fabf_ctx* ctx, BatchState* b, BatchGraph& G, const fabf_r
         const fabf_request& r = reqs[order[i]];
         const int TH = tile_rows_for(ctx, r.w, r.N, prec, 0, 0);
         const size_t sm = make_job(&jobs[i], &tmaps[i], r.img, r.pitch, r.theta, r.sigma, r.H, r.W, r.w, r.N,
-                                   r.out, r.out_is_f64, TH);
+                                   r.out, r.out_is_f64, TH, tile_staging_tma(ctx, r.w, r.N, prec));
         jobs[i].tile_begin = tiles;
         tiles += (long long)jobs[i].tiles_x * jobs[i].tiles_y;
         smem = std::max(smem, sm);

@@ -22,6 +22,7 @@ struct BatchState;
 struct TuneEntry {
     int TH;         // output rows per tile
     float ms;       // measured time of the tuning image (0 = not measured)
+    int plain;      // 1: stage tiles with plain loads, 0: with TMA (where the image allows it)
 };
 
 }  // namespace fabf
@@ -77,7 +78,8 @@ bool encode_image_tmap(CUtensorMap* tm, const uint8_t* img, int H, int W, size_t
 // tensor map is encoded (and J->use_tma set) when the image allows TMA.
 // Returns the dynamic shared memory one tile needs.
 size_t make_job(ImageJob* J, CUtensorMap* tm, const uint8_t* img, size_t pitch, const float* theta,
-                const float* sigma, int H, int W, int w, int N, void* out, int out_f64, int TH);
+                const float* sigma, int H, int W, int w, int N, void* out, int out_f64, int TH,
+                bool allow_tma = true);
 
 cudaError_t launch_fused(int prec, int N, const CUtensorMap& tm, const FusedParams& p, dim3 grid, size_t smem,
                          cudaStream_t s);
@@ -101,7 +103,8 @@ int run_fused(fabf_ctx* ctx, const uint8_t* img, size_t pitch, const float* thet
               int W, int w, int N, void* out, int out_f64, const DebugPlanes* dbg, cudaStream_t s);
 int run_fused_prec(fabf_ctx* ctx, int prec, const uint8_t* img, size_t pitch, const float* theta,
                    const float* sigma, int H, int W, int w, int N, void* out, int out_f64, int TH,
-                   const DebugPlanes* dbg, unsigned* status, unsigned long long* nfb, cudaStream_t s);
+                   const DebugPlanes* dbg, unsigned* status, unsigned long long* nfb, cudaStream_t s,
+                   bool allow_tma = true);
 
 // FP64 launch with caller-provided status words (allocation-free entry point).
 int launch_fused_scratch(const uint8_t* img, size_t pitch, const float* theta, const float* sigma, int H,
@@ -117,6 +120,9 @@ int launch_fused_scratch(const uint8_t* img, size_t pitch, const float* theta, c
 // with tall tiles leaves SMs idle in the last wave.  Measured at 720p, 1080p,
 // 2160x3840 and 4096^2 for w in {5, 20, 40}.
 int tile_rows_for(fabf_ctx* ctx, int w, int N, int prec, int H, int W);
+// Tile staging for (w, N, prec): TMA (true) unless the context has autotune
+// on and the autotuner measured plain cooperative loads faster.
+bool tile_staging_tma(fabf_ctx* ctx, int w, int N, int prec);
 constexpr int kTileCandidates[] = {8, 16, 24, 32, 40};
 constexpr int kPrecForms = 4;
 // FP64, FP64 fit + FP32, compensated FP32, centred binary32

@@ -228,9 +228,10 @@ def test_every_tile_height_gives_identical_results(tmp_path, prec):
     f64 = prec == fabf.FABF_FP64
     odt = torch.float64 if f64 else torch.float32
     results = []
-    for TH in (8, 16, 24, 32, 40):
-        path = tmp_path / ("tune_%d.txt" % TH)
-        path.write_text("20 5 %d %d 0.0\n" % (prec, TH))
+    for TH, plain in ((8, 0), (16, 0), (24, 0), (32, 0), (40, 0), (8, 1), (40, 1)):
+        # plain = 1: tiles staged with plain cooperative loads instead of TMA
+        path = tmp_path / ("tune_%d_%d.txt" % (TH, plain))
+        path.write_text("20 5 %d %d 0.0 %d\n" % (prec, TH, plain))
         with fabf.Context(device=0, precision=prec, autotune=1, tune_cache_path=str(path)) as c:
             assert fabf.fabf_tile_rows(c, 20, 5, prec) == TH
             outs = [torch.empty(im[1].shape, dtype=odt, device="cuda") for im in d]
