@@ -876,18 +876,6 @@ __device__ __forceinline__ void integrals_c32(float lam, float t0, float s0, flo
     }
 }
 
-// Exact float-free conversion helper: 0 <= |x| < 2^63 to binary32 from three
-// exact 23-bit chunks (two roundings: within one unit in the last place).
-__device__ __forceinline__ float i63_to_float(int64_t x)
-{
-    const uint64_t u = x < 0 ? (uint64_t)0 - (uint64_t)x : (uint64_t)x;
-    const float f0 = u23_to_float((uint32_t)u & 0x7FFFFFu);
-    const float f1 = u23_to_float((uint32_t)(u >> 23) & 0x7FFFFFu);
-    const float f2 = u23_to_float((uint32_t)(u >> 46));
-    const float r = fmaf(f2, 70368744177664.0f, fmaf(f1, 8388608.0f, f0));   // x 2^46, x 2^23
-    return x < 0 ? -r : r;
-}
-
 // Error bound per unit of the sums' scale for the guard of FABF_C32: the
 // binary32 integrals carry up to ~1e-5 of max_k |J_k| in the regimes they are
 // used in, the rest (moments, fit, sums) a few units of 2^-24.
@@ -912,15 +900,17 @@ __device__ __forceinline__ bool c32_integrals_weak(float lam, float t0)
 // error estimate, the binary64 T2 is negative too and the pixel takes the
 // fallback of Eq. (29) (the sigma -> infinity limit): fb_mean, with fallback
 // set.
-template <int N>
+template <int N, typename FbMean>
 __device__ __forceinline__ float fabf_tail_c32(const int64_t (&v)[(N < 1 ? 1 : N) + 1], int alpha, int beta,
-                                               float theta_f, float sigma_f, float fb_mean, int& fallback,
+                                               float theta_f, float sigma_f, FbMean&& fb_mean, int& fallback,
                                                bool& redo)
 {
     constexpr CentredInvTable kA = make_centred_inverse_table();
+    // one correctly rounded conversion each (the conversion pipe is
+    // otherwise idle in this kernel)
     float mu[N + 1];
 #pragma unroll
-    for (int k = 0; k <= N; ++k) mu[k] = i63_to_float(v[k]);
+    for (int k = 0; k <= N; ++k) mu[k] = __ll2float_rn(v[k]);
     // c~ = A~^{-1} mu~: even coefficients from even moments, odd from odd
     float c[N + 1];
 #pragma unroll
@@ -931,10 +921,10 @@ __device__ __forceinline__ float fabf_tail_c32(const int64_t (&v)[(N < 1 ? 1 : N
         c[n] = acc;
     }
     const int d = beta - alpha;
-    const float rd = __frcp_rn((float)d);
+    const float rd = __fdividef(1.0f, (float)d);                 // within 2 ulp
     const float t0 = (theta_f - (float)alpha) * rd;
     const float s0 = (2.0f * theta_f - (float)(alpha + beta)) * rd;
-    const float lam = (float)(d * d) * __frcp_rn(2.0f * sigma_f * sigma_f);
+    const float lam = __fdividef((float)(d * d), 2.0f * sigma_f * sigma_f);
     float J[N + 2];
     integrals_c32<N + 1>(lam, t0, s0, J);
     float T2 = c[0] * J[0], U = c[0] * J[1];
@@ -948,15 +938,17 @@ __device__ __forceinline__ float fabf_tail_c32(const int64_t (&v)[(N < 1 ? 1 : N
     }
     const float R = U / T2;
     const float hd = 0.5f * (float)d;
-    const float est = kGuardUnitC32 * hd * (S1 + fabsf(R) * S2) / fabsf(T2);
     // T2 < 0 beyond its own error bound (kGuardUnitC32 S2, the bound the
     // estimate uses): every precision agrees on the fallback
     if (T2 < -kGuardUnitC32 * S2) {
         fallback = 1;
         redo = c32_integrals_weak(lam, t0);
-        return fb_mean;
+        return fb_mean();
     }
-    redo = !(T2 > kGuardUnitC32 * S2) || !(est <= kFp32GuardGray) || c32_integrals_weak(lam, t0);
+    // error estimate kGuardUnitC32 (d / 2) (S1 + |R| S2) / |T2| <= 0.25 gray,
+    // tested without the division
+    const float est_num = kGuardUnitC32 * hd * (S1 + fabsf(R) * S2);
+    redo = !(T2 > kGuardUnitC32 * S2) || !(est_num <= kFp32GuardGray * T2) || c32_integrals_weak(lam, t0);
     return fmaf(hd, R, 0.5f * (float)(alpha + beta));
 }
 
@@ -1001,7 +993,8 @@ __device__ __forceinline__ float fabf_pixel_c32(int alpha, int beta, int fi, con
         v[k] = (int64_t)((uint64_t)M[k] * (uint64_t)dp);
         dp *= d;
     }
-    return fabf_tail_c32<N>(v, alpha, beta, theta_f, sigma_f, (float)m[1] / (float)m[0], fallback, redo);
+    return fabf_tail_c32<N>(v, alpha, beta, theta_f, sigma_f, [&] { return (float)m[1] / (float)m[0]; }, fallback,
+                            redo);
 }
 
 }  // namespace fabf

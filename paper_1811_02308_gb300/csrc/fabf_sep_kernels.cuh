@@ -239,8 +239,8 @@ __device__ __forceinline__ float sep_pixel_c32(int alpha, int beta, int fi, cons
     for (int k = 0; k <= K; ++k) v[k] = (int64_t)((__int128)sc[k] >> shift);
     // fallback: the weighted window mean m_1 / m_0 (m_0 < 2^32, m_1 < 2^40),
     // as the box path forms it
-    const float fb = (float)(int64_t)m[1] / (float)(int64_t)m[0];
-    return fabf_tail_c32<N>(v, alpha, beta, th, sg, fb, fallback, redo);
+    return fabf_tail_c32<N>(v, alpha, beta, th, sg, [&] { return (float)(int64_t)m[1] / (float)(int64_t)m[0]; },
+                            fallback, redo);
 }
 
 // The compensated form's FP64 redo (fabf_redo_scaled) from the separable
