@@ -849,7 +849,7 @@ __device__ __forceinline__ void integrals_c32(float lam, float t0, float s0, flo
     } else {
         const int bl = min(31, (int)(lam * 4.0f)), bs = min(7, (int)(fabsf(s0) * 2.0f));
         int Kp = c_kp32.v[bl][bs];
-        Kp = (int)__reduce_max_sync(__activemask(), (unsigned)Kp);
+        Kp = (int)__reduce_max_sync(__activemask(), (unsigned)Kp) | 1;   // odd: the step parities are fixed
         const float l1 = lam * (1.0f - t0), l0 = lam * t0;
         float a1 = (float)(Kp + 2) - l1, b1 = (float)(Kp + 2) - l0;
         float a0 = (float)(Kp + 1) - l1, b0 = (float)(Kp + 1) - l0;
@@ -860,9 +860,17 @@ __device__ __forceinline__ void integrals_c32(float lam, float t0, float s0, flo
         const float sg = (Kp & 1) ? 1.0f : -1.0f;   // (-1)^(Kp+1)
         float hi = 0.5f * (__fdividef(E1s, a1) + sg * __fdividef(E0s, b1));   // J_(Kp+1)
         float lo = 0.5f * (__fdividef(E1s, a0) - sg * __fdividef(E0s, b0));   // J_(Kp)
-        // (hi, lo) = (J_(k+1), J_k) -> J_(k-1), for k = Kp .. K + 1
-        for (int k = Kp; k > K; --k) {
-            const float nx = fmaf(lam, fmaf(-s0, lo, hi), (k & 1) ? Ep : Em) * (0.5f * c_recip.f[k]);
+        // (hi, lo) = (J_(k+1), J_k) -> J_(k-1), for k = Kp .. K + 1, two
+        // steps at a time from the odd Kp (odd k adds Ep, even k Em)
+        int k = Kp;
+        for (; k - 1 > K; k -= 2) {
+            const float n1 = fmaf(lam, fmaf(-s0, lo, hi), Ep) * (0.5f * c_recip.f[k]);
+            const float n2 = fmaf(lam, fmaf(-s0, n1, lo), Em) * (0.5f * c_recip.f[k - 1]);
+            hi = n1;
+            lo = n2;
+        }
+        if (k > K) {   // one odd step left (k == K + 1)
+            const float nx = fmaf(lam, fmaf(-s0, lo, hi), Ep) * (0.5f * c_recip.f[k]);
             hi = lo;
             lo = nx;
         }
