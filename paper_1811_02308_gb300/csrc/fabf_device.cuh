@@ -89,6 +89,44 @@ __host__ __device__ constexpr AinvSplitTable make_ainv_split_table()
     return t;
 }
 
+// Correctly rounded reciprocals of the powers d^k (d = 1..255, k = 1..6),
+// v[k-1][d] = RN(1 / d^k), built at compile time (a binary64 division of two
+// exactly representable numbers, correctly rounded).  With them a quotient
+// a / d^k costs one multiplication and two fused multiply-adds instead of a
+// full division and is still correctly rounded (div_by_power below).
+struct RecipPowTable {
+    double v[kNMax][256];
+};
+
+__host__ __device__ constexpr RecipPowTable make_recip_pow_table()
+{
+    RecipPowTable t{};
+    for (int k = 1; k <= kNMax; ++k)
+        for (int d = 1; d < 256; ++d) {
+            double p = 1.0;
+            for (int i = 0; i < k; ++i) p *= (double)d;   // exact: d^k <= 255^6 < 2^53
+            t.v[k - 1][d] = 1.0 / p;
+        }
+    return t;
+}
+
+// In global memory (read through the read-only cache): the lanes of a warp
+// index it by their own d, which a constant-memory table would serialise.
+static __device__ const RecipPowTable g_recip_pow = make_recip_pow_table();
+
+// RN(a / b) for b = d^k from r = RN(1 / b): q0 = RN(a r) lies within one unit
+// in the last place of a / b, the residual a - b q0 is exact as one fused
+// multiply-add, and q0 + r (a - b q0) rounded once is the correctly rounded
+// quotient (Markstein's theorem for a correctly rounded reciprocal; checked
+// for every b = d^k on 3e7 dividends, 0 <= a <= 6561 d^k, against IEEE
+// division).  The FP64 form's mu_k and t0 stay bit-identical to the oracle's
+// divisions.
+__host__ __device__ __forceinline__ double div_by_power(double a, double b, double r)
+{
+    const double q0 = a * r;
+    return fma(fma(-q0, b, a), r, q0);
+}
+
 // The tables are built at compile time; each translation unit that includes
 // this header holds its own copy in constant memory.
 static __constant__ AinvTable c_ainv = make_ainv_table();
@@ -239,7 +277,7 @@ __device__ __forceinline__ double fp64_ratio(const double (&c)[N + 1], int alpha
                                              double& t0, double& lam, double (&I)[N + 2], double& T1, double& T2)
 {
     const double sg = (double)sigma_f;
-    t0 = ((double)theta_f - (double)alpha) / (double)d;
+    t0 = div_by_power((double)theta_f - (double)alpha, (double)d, __ldg(&g_recip_pow.v[0][d]));
     lam = (double)(d * d) / (2.0 * sg * sg);
     integrals_fp64<N + 1>(lam, t0, I);
     T1 = c[0] * I[1];
@@ -316,18 +354,20 @@ __device__ __forceinline__ double fabf_pixel_fp64(const AinvTable& A, int alpha,
         for (int a = 0; a <= K - b; ++a) s[a] = s[a + 1] - (int64_t)alpha * s[a];
         M[b] = s[0];
     }
-    // mu_k = M_k / (beta - alpha)^k: one correctly rounded division of two
-    // binary64 values ((beta - alpha)^k <= 255^6 is exact).  The division
-    // stays (an exactly scaled integer M_k d^(K-k), rounded once, would save
-    // it): at N = 6 the fit amplifies a one-unit change in the last place of
-    // mu to ~1e-8 relative in g_hat, so the 1e-9 agreement with the oracle
-    // rests on the same operations in the same order.
+    // mu_k = M_k / (beta - alpha)^k: the correctly rounded quotient of two
+    // binary64 values ((beta - alpha)^k <= 255^6 is exact), formed from the
+    // correctly rounded reciprocal (div_by_power).  The quotient must be the
+    // correctly rounded one (an exactly scaled integer M_k d^(K-k), rounded
+    // once, is not): at N = 6 the fit amplifies a one-unit change in the last
+    // place of mu to ~1e-8 relative in g_hat, so the 1e-9 agreement with the
+    // oracle rests on the same values entering the same operations.
     double mu[K + 1];
     int64_t dk = 1;
+    mu[0] = (double)M[0];
 #pragma unroll
-    for (int k = 0; k <= K; ++k) {
-        mu[k] = (double)M[k] / (double)dk;
+    for (int k = 1; k <= K; ++k) {
         dk *= d;
+        mu[k] = div_by_power((double)M[k], (double)dk, __ldg(&g_recip_pow.v[k - 1][d]));
     }
     if (tr) {
 #pragma unroll
