@@ -41,15 +41,15 @@ METRIC = "FABF Mpix/s (N=5,w=20) & % of roofline vs plain FP64 form; served p50/
 WORKLOAD = ("1920x1080 uint8 synthetic (200 blobs, 4 step edges, noise 10), box w=20, N=5, "
             "theta=f+zeta (zeta in [-20,20]), sigma in [5,60]")
 # DRAM bytes (read + write) per launch on this workload, from one ncu capture
-# of the launch bench.py times (1920x1080, w = 20, N = 5, the tile height
-# the library picks; profiles/); set to None whenever the kernel changes
-# until it is re-captured.  The float output of a launch stays in the 126 MB
-# L2 when the kernel ends, so the figure is the 9 B/px of compulsory reads.
-NCU_TRAFFIC_BYTES = 18.76e6        # FP64 form kernel (8-row tiles)
-NCU_TRAFFIC_BYTES_FP64FIT = None   # FP64-fit kernel (not captured)
-NCU_TRAFFIC_BYTES_CFP32 = 19.40e6  # compensated FP32 kernel (8-row tiles, 4 CTAs per SM)
-NCU_TRAFFIC_BYTES_C32 = None       # centred binary32 kernel (not captured yet)
-NCU_TRAFFIC_BYTES_SEP = 18.77e6    # separable (Gaussian) kernel, rho = 5, compensated FP32
+# of the launch bench.py times (1920x1080, w = 20, N = 5, the tile height the
+# library picks; profiles/); None for a kernel not captured since it last
+# changed.  The float output of a launch stays in the 126 MB L2 when the
+# kernel ends, so the figure is the 9 B/px of compulsory reads.
+NCU_TRAFFIC_BYTES = 18.77e6        # FP64 form kernel (8-row tiles)
+NCU_TRAFFIC_BYTES_FP64FIT = None   # FP64-fit kernel
+NCU_TRAFFIC_BYTES_CFP32 = None     # compensated binary32 kernel
+NCU_TRAFFIC_BYTES_C32 = 18.78e6    # centred binary32 kernel (16-row tiles, 4 CTAs per SM)
+NCU_TRAFFIC_BYTES_SEP = 18.77e6    # separable (Gaussian) kernel, rho = 5, compensated binary32
 FORM_NAMES = {0: "fp64", 1: "fp64fit_fp32rec", 2: "cfp32", 3: "c32"}
 FORMS = (0, 1, 2, 3)
 DTYPES = {0: "f64", 1: "f64 fit + f32", 2: "f32 (compensated fit)", 3: "f32 (centred fit)"}
@@ -87,11 +87,11 @@ def cfp32_executed_flops_per_pixel(N: int) -> float:
     return 20 * (N + 1) + 14 * (N + 1) ** 2 + 6 + 90 + 4 * N + 8 * (N + 1) + 12
 
 
-# Warp instructions the compensated kernel executes per pixel on this
-# workload (smsp__inst_executed.sum / pixels, one ncu capture of the launch
-# bench.py times; profiles/); None whenever the kernel changes until it is
-# re-captured.
-NCU_INST_PER_PIXEL_CFP32 = None
+# Thread instructions per pixel a binary32 kernel executes on this workload
+# (32 x smsp__inst_executed.sum / pixels, one ncu capture of the launch
+# bench.py times; profiles/); a kernel is left out once it changes until it
+# is captured again.
+NCU_INST_PER_PIXEL = {3: 1245.3}
 
 # This GPU's arithmetic pipe peaks, measured at start-up by fabf_pipe_peaks
 # (CUDA events around FP64 / FP32 FMA, INT32 IMAD and MUFU loops).
@@ -100,7 +100,7 @@ PEAK_SOURCE = ("measured on this GPU in this run (fabf_pipe_peaks: best of 3 eve
                "independent FMA chains per thread, 4 x 256-thread CTAs per SM)")
 
 
-def alu_roofline(prec: int, N: int, npix: int, kern_ms: float, traffic=None) -> dict:
+def alu_roofline(prec: int, N: int, npix: int, kern_ms: float, traffic=None, inst_per_pixel=None) -> dict:
     """Roofline of one launch of the form `prec`: the method's algorithmic
     flops per pixel times the pixels, over the launch's CUDA-event time,
     against the measured peak of the pipe the form runs its arithmetic on
@@ -118,13 +118,14 @@ def alu_roofline(prec: int, N: int, npix: int, kern_ms: float, traffic=None) -> 
         ex = cfp32_executed_flops_per_pixel(N)
         r["executed_flops_per_pixel"] = ex
         r["executed_tflops"] = ex * npix / (kern_ms / 1e3) / 1e12
+    if prec >= 2:
         # instruction issue: one warp instruction per clock per scheduler, the
         # rate the FP32 FMA loop reaches (one FFMA warp instruction per clock)
         issue_peak = PEAKS["fp32_tflops"] / 2.0 / 32.0          # T warp instructions / s
-        r["issue"] = {"peak_t_warp_inst_per_s": issue_peak,
-                      "inst_per_pixel": NCU_INST_PER_PIXEL_CFP32}
-        if NCU_INST_PER_PIXEL_CFP32:
-            ach = NCU_INST_PER_PIXEL_CFP32 * npix / (kern_ms / 1e3) / 1e12
+        ipp = inst_per_pixel
+        r["issue"] = {"peak_t_warp_inst_per_s": issue_peak, "inst_per_pixel": ipp}
+        if ipp:
+            ach = ipp / 32.0 * npix / (kern_ms / 1e3) / 1e12
             r["issue"].update({"achieved_t_warp_inst_per_s": ach, "frac": ach / issue_peak})
     return r
 
@@ -912,7 +913,8 @@ def main():
         row.update(acc[prec])
         row["roofline"] = alu_roofline(prec, NDEG, npix, r["kernel_ms"],
                                        (NCU_TRAFFIC_BYTES, NCU_TRAFFIC_BYTES_FP64FIT, NCU_TRAFFIC_BYTES_CFP32,
-                                        NCU_TRAFFIC_BYTES_C32)[prec])
+                                        NCU_TRAFFIC_BYTES_C32)[prec],
+                                       NCU_INST_PER_PIXEL.get(prec) if (H_, W_) == (1080, 1920) else None)
         form_rows[FORM_NAMES[prec]] = row
     # headline: fastest form as accurate as FP64 (PSNR vs brute force within 0.01 dB)
     best = 0
