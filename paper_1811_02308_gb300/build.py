@@ -18,6 +18,7 @@ SOURCES = [
     "fabf_inst_fp64fit.cu",
     "fabf_inst_cfp32.cu",
     "fabf_inst_c32.cu",
+    "fabf_inst_c32w.cu",
     "fabf_api.cu",
     "fabf_batch_serve.cu",
     "fabf_noalloc.cu",

@@ -213,8 +213,7 @@ int tile_rows_for(fabf_ctx* ctx, int w, int N, int prec, int H, int W)
     int best = kTileCandidates[0];
     for (int TH : kTileCandidates) {
         if (TH > steady) break;
-        const size_t smem = fused_smem_bytes(N, w, Cb, TH) + 1024;      // + the per-CTA reservation
-        const int per_sm = std::max(1, std::min(kCtasPerSm[pc], (int)((size_t)228 * 1024 / smem)));
+        const int per_sm = resident_ctas(pc, N, fused_smem_bytes(N, w, Cb, TH));
         const long long tiles = tiles_x * ((H + TH - 1) / TH);
         if (tiles >= (long long)kMinWaves[pc] * num_sms * per_sm) best = TH;
     }

@@ -132,6 +132,23 @@ constexpr int kMinWaves[kPrecForms] = {1, 1, 6, 3};
 // fabf_kernels.cuh); shared memory may allow fewer.
 constexpr int kCtasPerSm[kPrecForms] = {2, 4, 4, 4};
 inline int prec_index(int prec) { return prec < 0 || prec >= kPrecForms ? 0 : prec; }
+
+// CTAs of a single-image launch resident per SM: the register budget the
+// kernel is compiled for (the centred form at N = 6 runs its 3-CTA build)
+// and the shared memory (dyn_smem plus the 1 KB per-CTA reservation, of
+// 228 KB per SM).
+inline int resident_ctas(int prec, int N, size_t dyn_smem)
+{
+    const int pc = prec_index(prec);
+    int regs = kCtasPerSm[pc];
+    if (pc == 3 && N >= 6) regs = 3;
+    const int by_smem = (int)((size_t)228 * 1024 / (dyn_smem + 1024));
+    return by_smem < 1 ? 1 : (by_smem < regs ? by_smem : regs);
+}
+
+// The centred form's fused kernel compiled for 3 CTAs per SM (fabf_inst_c32w.cu).
+cudaError_t launch_fused_c32_wide(int N, const CUtensorMap& tm, const FusedParams& p, dim3 grid, size_t smem,
+                                  cudaStream_t s);
 constexpr int kDefaultTileRows = 32;               // stage-export runs of the tests
 
 int read_and_clear_status(fabf_ctx* ctx, cudaStream_t s, int* status, uint64_t* nfb, uint64_t* nredo);

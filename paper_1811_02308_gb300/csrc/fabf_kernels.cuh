@@ -749,13 +749,17 @@ __device__ __forceinline__ bool fabf_tile(const CUtensorMap* tmap, const ImageJo
 // bound by the FP64 pipe (two CTAs saturate it); the binary32 forms are
 // bound by instruction issue and latency and gain from a fourth CTA (64
 // registers per thread), measured faster at every image size.
+// The centred form is also compiled for 3 CTAs per SM (up to 85 registers):
+// where shared memory allows only 3 anyway (w >= 32 or so) or at N = 6, whose
+// tail spills at 64 registers, that build is faster (measured 2 % at w = 40,
+// N = 5 and 5 % at w = 20, N = 6; 4 % slower at w <= 20, N = 5).
 template <int PREC>
 struct MinBlocks {
     static constexpr int value = PREC == kPrecFP64 ? 2 : 4;
 };
 
-template <int N, int PREC>
-__global__ void __launch_bounds__(kThreads, MinBlocks<PREC>::value)
+template <int N, int PREC, int MINB = MinBlocks<PREC>::value>
+__global__ void __launch_bounds__(kThreads, MINB)
     fabf_fused_kernel(const __grid_constant__ CUtensorMap tmap, const FusedParams p)
 {
     extern __shared__ __align__(128) uint8_t smem[];

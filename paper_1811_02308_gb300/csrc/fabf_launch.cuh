@@ -1,24 +1,35 @@
 // Kernel launch helpers, instantiated once per precision in
 // fabf_inst_fp64.cu, fabf_inst_fp64fit.cu, fabf_inst_cfp32.cu and
-// fabf_inst_c32.cu (separate translation units so that nvcc compiles them in
-// parallel).
+// fabf_inst_c32.cu, plus the centred form's 3-CTA build in fabf_inst_c32w.cu
+// (separate translation units so that nvcc compiles them in parallel).
 #pragma once
 
 #include <cuda_runtime.h>
 
+#include "fabf_internal.h"
 #include "fabf_kernels.cuh"
 
 namespace fabf {
 
 constexpr int kMaxDynSmem = 110 * 1024;   // >= fused_smem_bytes for every (w <= 40, N <= 6, TH <= 64)
 
+template <int N, int PREC, int MINB>
+cudaError_t launch_fused_build(const CUtensorMap& tm, const FusedParams& p, dim3 grid, size_t smem, cudaStream_t s)
+{
+    const cudaError_t e = set_smem_limit_once<fabf_fused_kernel<N, PREC, MINB>>(kMaxDynSmem);
+    if (e != cudaSuccess) return e;
+    fabf_fused_kernel<N, PREC, MINB><<<grid, kThreads, smem, s>>>(tm, p);
+    return cudaGetLastError();
+}
+
 template <int N, int PREC>
 cudaError_t launch_fused_one(const CUtensorMap& tm, const FusedParams& p, dim3 grid, size_t smem, cudaStream_t s)
 {
-    const cudaError_t e = set_smem_limit_once<fabf_fused_kernel<N, PREC>>(kMaxDynSmem);
-    if (e != cudaSuccess) return e;
-    fabf_fused_kernel<N, PREC><<<grid, kThreads, smem, s>>>(tm, p);
-    return cudaGetLastError();
+    if constexpr (PREC == kPrecC32) {
+        // the 3-CTA build where only 3 CTAs are resident (resident_ctas)
+        if (resident_ctas(PREC, N, smem) <= 3) return launch_fused_c32_wide(N, tm, p, grid, smem, s);
+    }
+    return launch_fused_build<N, PREC, MinBlocks<PREC>::value>(tm, p, grid, smem, s);
 }
 
 template <int PREC>
