@@ -142,6 +142,12 @@ def max_over_ranks(ms: float, device) -> float:
     return float(t.item())
 
 
+def replica_seed(rank: int, i: int) -> int:
+    """Seed of input image i of a rank: every replica filters images of its
+    own (the method needs no exchange between GPUs)."""
+    return 1000 + 17 * rank + i
+
+
 def job_throughput(n_ranks: int, pixels_per_step: int, steps: int, max_ms: float) -> float:
     """Whole-job Mpix/s: the pixels every rank filtered over the max-over-ranks time."""
     return n_ranks * pixels_per_step * steps / (max_ms / 1e3) / 1e6
@@ -831,7 +837,7 @@ def main():
     if args.profile:
         H_, W_ = (int(v) for v in args.profile.lower().split("x"))
         n_distinct, n_slots = 1, 1
-    host = [make_inputs(H_, W_, 1000 + 17 * rank + i, N_BLOBS) for i in range(n_distinct)]
+    host = [make_inputs(H_, W_, replica_seed(rank, i), N_BLOBS) for i in range(n_distinct)]
     slots = {}
     for prec in FORMS:
         odt = torch.float64 if prec == 0 else torch.float32
