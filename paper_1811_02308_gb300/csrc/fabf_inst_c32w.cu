@@ -1,4 +1,4 @@
-// The centred form's fused kernel compiled for 3 CTAs per SM (up to 85
+// The centred form's fused and batch kernels compiled for 3 CTAs per SM (up to 85
 // registers per thread), used where only 3 CTAs are resident anyway (see
 // resident_ctas in fabf_internal.h).
 #include "fabf_internal.h"
@@ -19,6 +19,11 @@ cudaError_t launch_fused_c32_wide(int N, const CUtensorMap& tm, const FusedParam
     case 6: return launch_fused_build<6, kPrecC32, 3>(tm, p, grid, smem, s);
     default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_batch_c32_wide(const BatchParams& p, int grid, size_t smem, cudaStream_t s)
+{
+    return launch_batch_build<kPrecC32, 3>(p, grid, smem, s);
 }
 
 }  // namespace fabf

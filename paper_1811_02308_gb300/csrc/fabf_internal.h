@@ -137,18 +137,26 @@ inline int prec_index(int prec) { return prec < 0 || prec >= kPrecForms ? 0 : pr
 // kernel is compiled for (the centred form at N = 6 runs its 3-CTA build)
 // and the shared memory (dyn_smem plus the 1 KB per-CTA reservation, of
 // 228 KB per SM).
+inline int smem_resident_ctas(size_t dyn_smem)
+{
+    const int n = (int)((size_t)228 * 1024 / (dyn_smem + 1024));
+    return n < 1 ? 1 : n;
+}
+
 inline int resident_ctas(int prec, int N, size_t dyn_smem)
 {
     const int pc = prec_index(prec);
     int regs = kCtasPerSm[pc];
     if (pc == 3 && N >= 6) regs = 3;
-    const int by_smem = (int)((size_t)228 * 1024 / (dyn_smem + 1024));
-    return by_smem < 1 ? 1 : (by_smem < regs ? by_smem : regs);
+    const int by_smem = smem_resident_ctas(dyn_smem);
+    return by_smem < regs ? by_smem : regs;
 }
 
-// The centred form's fused kernel compiled for 3 CTAs per SM (fabf_inst_c32w.cu).
+// The centred form's fused and batch kernels compiled for 3 CTAs per SM
+// (fabf_inst_c32w.cu).
 cudaError_t launch_fused_c32_wide(int N, const CUtensorMap& tm, const FusedParams& p, dim3 grid, size_t smem,
                                   cudaStream_t s);
+cudaError_t launch_batch_c32_wide(const BatchParams& p, int grid, size_t smem, cudaStream_t s);
 constexpr int kDefaultTileRows = 32;               // stage-export runs of the tests
 
 int read_and_clear_status(fabf_ctx* ctx, cudaStream_t s, int* status, uint64_t* nfb, uint64_t* nredo);

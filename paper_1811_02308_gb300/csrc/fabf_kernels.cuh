@@ -791,8 +791,8 @@ __device__ __forceinline__ bool batch_dispatch(const BatchParams& p, const Image
     }
 }
 
-template <int PREC>
-__global__ void __launch_bounds__(kThreads, MinBlocks<PREC>::value) fabf_batch_kernel(const BatchParams p)
+template <int PREC, int MINB = MinBlocks<PREC>::value>
+__global__ void __launch_bounds__(kThreads, MINB) fabf_batch_kernel(const BatchParams p)
 {
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ long long s_tile;

@@ -48,13 +48,24 @@ cudaError_t launch_fused_impl(int N, const CUtensorMap& tm, const FusedParams& p
     }
 }
 
+template <int PREC, int MINB>
+cudaError_t launch_batch_build(const BatchParams& p, int grid, size_t smem, cudaStream_t s)
+{
+    const cudaError_t e = set_smem_limit_once<fabf_batch_kernel<PREC, MINB>>(kMaxDynSmem);
+    if (e != cudaSuccess) return e;
+    fabf_batch_kernel<PREC, MINB><<<grid, kThreads, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
 template <int PREC>
 cudaError_t launch_batch_impl(const BatchParams& p, int grid, size_t smem, cudaStream_t s)
 {
-    const cudaError_t e = set_smem_limit_once<fabf_batch_kernel<PREC>>(kMaxDynSmem);
-    if (e != cudaSuccess) return e;
-    fabf_batch_kernel<PREC><<<grid, kThreads, smem, s>>>(p);
-    return cudaGetLastError();
+    if constexpr (PREC == kPrecC32) {
+        // the largest tile's shared memory sizes the persistent grid; where it
+        // leaves 3 CTAs per SM, the 3-CTA build (more registers, no spills)
+        if (smem_resident_ctas(smem) <= 3) return launch_batch_c32_wide(p, grid, smem, s);
+    }
+    return launch_batch_build<PREC, MinBlocks<PREC>::value>(p, grid, smem, s);
 }
 
 }  // namespace fabf
