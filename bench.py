@@ -771,6 +771,7 @@ def accuracy_vs_oracle(R, slots, n_sample=4000):
     d = [torch.from_numpy(a).to(R.dev) for a in (f, th, s)]
     bf = fabf.fabf_bruteforce(R.ctx, d[0], d[1], d[2], 20, use_f64=True).cpu().numpy()
     ys, xs = rng.integers(0, 4096, n_sample), rng.integers(0, 4096, n_sample)
+    fabf.fabf_get_status_ex(R.ctx)             # clear the counts of the calls above
     for N in (5, 6):
         ref, _ = oracle.fabf_pixels(f, th, s, 20, N, ys, xs)
         row = {}
