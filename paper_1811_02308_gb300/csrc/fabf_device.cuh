@@ -986,9 +986,18 @@ __device__ __forceinline__ float fabf_tail_c32(const int64_t (&v)[(N < 1 ? 1 : N
     }
     const float R = U / T2;
     const float hd = 0.5f * (float)d;
-    // T2 < 0 beyond its own error bound (kGuardUnitC32 S2, the bound the
-    // estimate uses): every precision agrees on the fallback
-    if (T2 < -kGuardUnitC32 * S2) {
+    // Bound on the error of T2: the integrals are within kGuardUnitC32 of
+    // max_k |J_k| each, so |dT2| <= kGuardUnitC32 max|J| sum|c~_k| (the
+    // binary32 fit and sums add a few units of 2^-24 of S2, far less).  T2
+    // below minus that bound is negative in every precision, and the pixel
+    // takes the fallback; within the bound of zero it goes to the FP64 path.
+    float csum = fabsf(c[0]), jmax = fabsf(J[N + 1]);
+#pragma unroll
+    for (int k = 1; k <= N; ++k) csum += fabsf(c[k]);
+#pragma unroll
+    for (int k = 0; k <= N; ++k) jmax = fmaxf(jmax, fabsf(J[k]));
+    const float t2_err = kGuardUnitC32 * csum * jmax;
+    if (T2 < -t2_err) {
         fallback = 1;
         redo = c32_integrals_weak(lam, t0);
         return fb_mean();
@@ -996,7 +1005,7 @@ __device__ __forceinline__ float fabf_tail_c32(const int64_t (&v)[(N < 1 ? 1 : N
     // error estimate kGuardUnitC32 (d / 2) (S1 + |R| S2) / |T2| <= 0.25 gray,
     // tested without the division
     const float est_num = kGuardUnitC32 * hd * (S1 + fabsf(R) * S2);
-    redo = !(T2 > kGuardUnitC32 * S2) || !(est_num <= kFp32GuardGray * T2) || c32_integrals_weak(lam, t0);
+    redo = !(T2 > t2_err) || !(est_num <= kFp32GuardGray * T2) || c32_integrals_weak(lam, t0);
     return fmaf(hd, R, 0.5f * (float)(alpha + beta));
 }
 
