@@ -257,6 +257,38 @@ int fabf_filter_sep(fabf_ctx* ctx, const uint8_t* img, const float* theta, const
  * pointers, capacity < 2r+1), FABF_EUNSUPPORTED (3 rho > 40). */
 int fabf_gaussian_taps(double rho, uint32_t* taps, int capacity, int* r);
 
+/* ---- box-cascade spatial kernel (O(1) in the kernel width) ---------------- */
+
+/* fabf_filter_sep with the taps of fabf_cascade_taps(rb): the cascade of
+ * three boxes of length n = 2 rb + 1, radius r = 3 rb, whose variance along
+ * each axis is rb (rb + 1) -- the combination of box kernels that stands in
+ * for the Gaussian of Eq. (4) at a cost per pixel independent of rb (the
+ * O(1) convolutions of Sec. II-D).  The result is that of fabf_filter_sep on
+ * the same taps, bit for bit (every moment is an exact integer on both
+ * paths); only the cost differs.
+ *   rb         1..13 (r = 3 rb <= 40);
+ *   tile_rows  0: the path's own rule; else the output rows per tile, a
+ *              multiple of 8 from 8 to 64 (the result does not depend on it);
+ *   the other arguments, pointer kinds, synchronisation, precision and
+ *   status reporting are those of fabf_filter_sep.
+ * Errors: FABF_EINVAL (rb < 1, bad tile_rows, as fabf_filter_sep),
+ * FABF_EUNSUPPORTED (rb > 13, N > 6), FABF_ECUDA. */
+int fabf_filter_cascade(fabf_ctx* ctx, const uint8_t* img, const float* theta, const float* sigma,
+                        int H, int W, size_t pitch, int rb, int N, void* out, int out_is_f64,
+                        int tile_rows, void* cuda_stream);
+
+/* Taps of the three-box cascade of radius rb along one axis (host only, no
+ * GPU): the three-fold convolution of 2 rb + 1 ones, 2r + 1 = 6 rb + 1
+ * integers summing to (2 rb + 1)^3 <= 19683; *r = 3 rb.  Errors:
+ * FABF_EINVAL (NULL pointers, rb < 1, capacity < 2r + 1), FABF_EUNSUPPORTED
+ * (rb > 13). */
+int fabf_cascade_taps(int rb, uint32_t* taps, int capacity, int* r);
+
+/* The cascade radius rb (1..13) whose variance rb (rb + 1) is nearest rho^2
+ * (host only).  Errors: FABF_EINVAL (rho <= 0 or not finite, NULL),
+ * FABF_EUNSUPPORTED (rho above the largest cascade, about 13.8). */
+int fabf_cascade_radius(double rho, int* rb);
+
 /* ---- applications (Sec. IV) ---------------------------------------------- */
 
 /* Sharpening and noise removal (Sec. IV-A).  The paper sets theta = f +
@@ -424,6 +456,14 @@ int fabf_debug_stages_sep(fabf_ctx* ctx, const uint8_t* img, const float* theta,
                           int r, int N, uint8_t* alpha, uint8_t* beta, uint64_t* m, uint64_t* M,
                           double* mu, double* c, double* t0lam, double* I, double* T,
                           int32_t* flags, double* out);
+
+/* fabf_debug_stages_sep on the box-cascade path (fabf_filter_cascade's
+ * kernel) with the cascade of radius rb; the same planes and errors. */
+int fabf_debug_stages_cascade(fabf_ctx* ctx, const uint8_t* img, const float* theta,
+                              const float* sigma, int H, int W, size_t pitch, int rb, int N,
+                              uint8_t* alpha, uint8_t* beta, uint64_t* m, uint64_t* M, double* mu,
+                              double* c, double* t0lam, double* I, double* T, int32_t* flags,
+                              double* out);
 
 /* Brute-force filter, Eqs. (1)-(3), with the separable kernel (O(r^2) per
  * pixel); arguments as fabf_bruteforce plus taps and r as fabf_filter_sep. */

@@ -27,10 +27,15 @@ SOURCES = [
     "fabf_sep_p1.cu",
     "fabf_sep_p2.cu",
     "fabf_sep_p3.cu",
+    "fabf_casc_p0.cu",
+    "fabf_casc_p1.cu",
+    "fabf_casc_p2.cu",
+    "fabf_casc_p3.cu",
     "fabf_apps.cu",
     "fabf_peaks.cu",
 ]
-HEADERS = ["fabf_device.cuh", "fabf_kernels.cuh", "fabf_launch.cuh", "fabf_internal.h", "fabf_sep_kernels.cuh"]
+HEADERS = ["fabf_device.cuh", "fabf_kernels.cuh", "fabf_launch.cuh", "fabf_internal.h", "fabf_sep_kernels.cuh",
+           "fabf_casc_kernels.cuh"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

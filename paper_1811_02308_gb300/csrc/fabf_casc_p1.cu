@@ -1,0 +1,11 @@
+// Instantiation of the box-cascade tiles for precision 1 (see fabf_casc_kernels.cuh).
+#include "fabf_casc_kernels.cuh"
+
+namespace fabf {
+
+cudaError_t launch_casc_p1(int N, const CUtensorMap& tm, const SepParams& p, dim3 grid, size_t smem, cudaStream_t s)
+{
+    return launch_casc_impl<1>(N, tm, p, grid, smem, s);
+}
+
+}  // namespace fabf

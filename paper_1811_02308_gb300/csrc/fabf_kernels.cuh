@@ -378,6 +378,93 @@ __device__ __forceinline__ int lane_block_query(const uint8_t* row, const uint8_
     return r;
 }
 
+// Vertical min / max of the kChunk windows [r0 + rr, r0 + rr + 2w] (rows
+// clipped to [rowlo, rowhi]) of every tile column, into the chunk's vmin /
+// vmax rows, four columns per thread: the bytes of tile columns 4g .. 4g+3
+// are one 32-bit word, split into two words of 16-bit lanes (bytes 0, 2 and
+// bytes 1, 3) that the native 16-bit SIMD minimum combines.  Thread Cb + 2g
+// takes the minima of group g and thread Cb + 2g + 1 the maxima, as minima
+// of the complemented bytes (255 - v reverses the order), so the two run the
+// same instructions; these are the threads the running sums of columns
+// 0 .. Cb-1 leave idle (Cb / 2 <= 256 - Cb for Cb <= 160).  Columns outside
+// the image (xs + c outside [0, W)) get 255 / 0.
+__device__ __forceinline__ void vertical_extrema_simd(const uint8_t* tile, uint8_t* vmin, uint8_t* vmax, int Cb,
+                                                      int xs, int W, int r0, int w, int rowlo, int rowhi)
+{
+    const int e = (int)threadIdx.x - Cb;
+    if (e >= 0 && e < (Cb >> 1)) {
+        const int g4 = 4 * (e >> 1);
+        const uint32_t inv = (e & 1) ? 0xFFFFFFFFu : 0u;   // maxima: complemented bytes
+        // bytes of columns outside the image take the identity (the
+        // staged tile holds 0 there)
+        uint32_t outside = 0u;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int Xe = xs + g4 + j;
+            if (Xe < 0 || Xe >= W) outside |= 0xFFu << (8 * j);
+        }
+        const uint32_t* tw = reinterpret_cast<const uint32_t*>(tile) + (g4 >> 2);
+        uint32_t* vw = reinterpret_cast<uint32_t*>((e & 1) ? vmax : vmin) + (g4 >> 2);
+        const int Cw = Cb >> 2;                     // words per tile row
+        // running minima as (even bytes, odd bytes) in 16-bit lanes
+        auto add = [&](uint32_t& m0, uint32_t& m1, int t) {
+            const uint32_t v = tw[t * Cw] ^ inv;
+            m0 = __vminu2(m0, __byte_perm(v, 0u, 0x4240));
+            m1 = __vminu2(m1, __byte_perm(v, 0u, 0x4341));
+        };
+        constexpr uint32_t kId = 0x00FF00FFu;
+        // Window of chunk row rr: tile rows [r0 + rr, r0 + rr + 2w]
+        // = [r0 + rr, r0 + 7] u [r0 + 8, r0 + rr + 2w] (2w + 1 >= 8,
+        // i.e. w >= 4): suffix extrema of the chunk's own rows, then
+        // prefix extrema from r0 + 8 that grow by one row per rr --
+        // 2w + 8 row visits per chunk.  For w < 4 every window is
+        // visited directly (2w + 1 < 8 rows).  The suffix extrema
+        // wait in this thread's own words of the shared rows.
+        const bool split = 2 * w + 1 >= kChunk;
+        uint32_t q0 = kId, q1 = kId;
+        if (split) {
+            uint32_t s0 = kId, s1 = kId;
+#pragma unroll
+            for (int rr = kChunk - 1; rr >= 0; --rr) {
+                const int t = r0 + rr;
+                if (t >= rowlo && t <= rowhi) add(s0, s1, t);
+                vw[rr * Cw] = __byte_perm(s0, s1, 0x6240);
+            }
+            // rows r0 + 8 .. r0 + 2w in two independent chains
+            const int a = max(r0 + kChunk, rowlo), b = min(r0 + 2 * w, rowhi);
+            uint32_t p0 = kId, p1 = kId;
+            int t = a;
+            for (; t + 1 <= b; t += 2) {
+                add(q0, q1, t);
+                add(p0, p1, t + 1);
+            }
+            if (t <= b) add(q0, q1, t);
+            q0 = __vminu2(q0, p0);
+            q1 = __vminu2(q1, p1);
+        }
+#pragma unroll
+        for (int rr = 0; rr < kChunk; ++rr) {
+            const int r = r0 + rr;
+            uint32_t m0, m1;
+            if (split) {
+                const int t = r + 2 * w;            // the row entering the prefix part
+                if (rr > 0 && t >= rowlo && t <= rowhi) add(q0, q1, t);
+                const uint32_t sv = vw[rr * Cw];
+                m0 = __vminu2(q0, __byte_perm(sv, 0u, 0x4240));
+                m1 = __vminu2(q1, __byte_perm(sv, 0u, 0x4341));
+            } else {
+                m0 = kId;
+                m1 = kId;
+                const int a = max(r, rowlo), b = min(r + 2 * w, rowhi);
+                for (int t = a; t <= b; ++t) add(m0, m1, t);
+            }
+            // back from the complement for the maxima; outside
+            // columns get 255 (minima) or 0 (maxima)
+            vw[rr * Cw] = ((__byte_perm(m0, m1, 0x6240) | outside) ^ inv);
+        }
+    }
+}
+
 // Add (Sign = +1) or subtract (Sign = -1) the powers v^1..v^K of one pixel to
 // the running window sums: k = 1, 2 in 32 bits, k >= 3 in 64 bits.  v^2..v^4
 // are exact in 32 bits (255^4 < 2^32), v^5 takes one widening multiply.
@@ -520,88 +607,8 @@ __device__ __forceinline__ bool fabf_tile(const CUtensorMap* tmap, const ImageJo
                 }
             }
         }
-        // 2b. Vertical extrema, four columns per thread: the bytes of tile
-        //     columns 4g .. 4g+3 are one 32-bit word, split into two words
-        //     of 16-bit lanes (bytes 0, 2 and bytes 1, 3) that the native
-        //     16-bit SIMD minimum combines.  Thread Cb + 2g takes the minima
-        //     of group g and thread Cb + 2g + 1 the maxima, as minima of the
-        //     complemented bytes (255 - v reverses the order), so the two run
-        //     the same instructions; these threads are the ones the sums
-        //     leave idle (Cb / 2 <= 256 - Cb for Cb <= 160).
-        {
-            const int e = (int)threadIdx.x - Cb;
-            if (e >= 0 && e < (Cb >> 1)) {
-                const int g4 = 4 * (e >> 1);
-                const uint32_t inv = (e & 1) ? 0xFFFFFFFFu : 0u;   // maxima: complemented bytes
-                // bytes of columns outside the image take the identity (the
-                // staged tile holds 0 there)
-                uint32_t outside = 0u;
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int Xe = xs + g4 + j;
-                    if (Xe < 0 || Xe >= J.W) outside |= 0xFFu << (8 * j);
-                }
-                const uint32_t* tw = reinterpret_cast<const uint32_t*>(tile) + (g4 >> 2);
-                uint32_t* vw = reinterpret_cast<uint32_t*>((e & 1) ? vmax : vmin) + (g4 >> 2);
-                const int Cw = Cb >> 2;                     // words per tile row
-                // running minima as (even bytes, odd bytes) in 16-bit lanes
-                auto add = [&](uint32_t& m0, uint32_t& m1, int t) {
-                    const uint32_t v = tw[t * Cw] ^ inv;
-                    m0 = __vminu2(m0, __byte_perm(v, 0u, 0x4240));
-                    m1 = __vminu2(m1, __byte_perm(v, 0u, 0x4341));
-                };
-                constexpr uint32_t kId = 0x00FF00FFu;
-                // Window of chunk row rr: tile rows [r0 + rr, r0 + rr + 2w]
-                // = [r0 + rr, r0 + 7] u [r0 + 8, r0 + rr + 2w] (2w + 1 >= 8,
-                // i.e. w >= 4): suffix extrema of the chunk's own rows, then
-                // prefix extrema from r0 + 8 that grow by one row per rr --
-                // 2w + 8 row visits per chunk.  For w < 4 every window is
-                // visited directly (2w + 1 < 8 rows).  The suffix extrema
-                // wait in this thread's own words of the shared rows.
-                const bool split = 2 * w + 1 >= kChunk;
-                uint32_t q0 = kId, q1 = kId;
-                if (split) {
-                    uint32_t s0 = kId, s1 = kId;
-#pragma unroll
-                    for (int rr = kChunk - 1; rr >= 0; --rr) {
-                        const int t = r0 + rr;
-                        if (t >= rowlo && t <= rowhi) add(s0, s1, t);
-                        vw[rr * Cw] = __byte_perm(s0, s1, 0x6240);
-                    }
-                    // rows r0 + 8 .. r0 + 2w in two independent chains
-                    const int a = max(r0 + kChunk, rowlo), b = min(r0 + 2 * w, rowhi);
-                    uint32_t p0 = kId, p1 = kId;
-                    int t = a;
-                    for (; t + 1 <= b; t += 2) {
-                        add(q0, q1, t);
-                        add(p0, p1, t + 1);
-                    }
-                    if (t <= b) add(q0, q1, t);
-                    q0 = __vminu2(q0, p0);
-                    q1 = __vminu2(q1, p1);
-                }
-#pragma unroll
-                for (int rr = 0; rr < kChunk; ++rr) {
-                    const int r = r0 + rr;
-                    uint32_t m0, m1;
-                    if (split) {
-                        const int t = r + 2 * w;            // the row entering the prefix part
-                        if (rr > 0 && t >= rowlo && t <= rowhi) add(q0, q1, t);
-                        const uint32_t sv = vw[rr * Cw];
-                        m0 = __vminu2(q0, __byte_perm(sv, 0u, 0x4240));
-                        m1 = __vminu2(q1, __byte_perm(sv, 0u, 0x4341));
-                    } else {
-                        m0 = kId;
-                        m1 = kId;
-                        const int a = max(r, rowlo), b = min(r + 2 * w, rowhi);
-                        for (int t = a; t <= b; ++t) add(m0, m1, t);
-                    }
-                    // back from the complement for the maxima; outside
-                    // columns get 255 (minima) or 0 (maxima)
-                    vw[rr * Cw] = ((__byte_perm(m0, m1, 0x6240) | outside) ^ inv);
-                }
-            }
-        }
+        // 2b. Vertical extrema of the chunk's windows (threads Cb .. Cb + Cb/2 - 1).
+        vertical_extrema_simd(tile, vmin, vmax, Cb, xs, J.W, r0, w, rowlo, rowhi);
         cp_async_wait_all();
         __syncthreads();
 

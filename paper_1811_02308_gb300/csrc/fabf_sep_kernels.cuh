@@ -43,6 +43,7 @@ constexpr uint32_t kTapSumMax = 65535;   // keeps V_k < 2^64 and m_k < 2^81
 
 struct SepTaps {
     int r;
+    int casc_n;                    // 0: direct FIR of g; else the box length n of a 3-box cascade (g its taps)
     uint32_t g[2 * kWMax + 1];
     uint32_t G[2 * kWMax + 2];     // G[t] = g[0] + ... + g[t-1]
 };
@@ -272,6 +273,116 @@ __device__ __forceinline__ double sep_pixel_cfp32_redo(int alpha, int beta, int 
     return fabf_redo_scaled<N>(v, alpha, d, th, sg, fallback);
 }
 
+// Writes one result of a separable-kernel tile to the image's output.
+__device__ __forceinline__ void sep_store(const ImageJob& J, long long pix, double g)
+{
+    if (J.out_f64) static_cast<double*>(J.out)[pix] = g;
+    else static_cast<float*>(J.out)[pix] = (float)g;
+}
+
+// The per-pixel part of Algorithm 1 for chunk row rr (image row Y) of a
+// separable-kernel tile: each lane finishes tile columns lane and lane + 32
+// from the window statistics stats(rr, x, alpha, beta, m, fi) (Eq. (8) and
+// the weighted power sums of Eq. (17)).  The binary32 forms queue the pixels
+// their guard rejects in (redo_n, redo_list) for sep_redo_pass.
+template <int N, int PREC, typename Stats>
+__device__ __forceinline__ void sep_row_pixels(const SepParams& P, Stats& stats, int rr, int Y, int x0,
+                                               const float* s_maps, unsigned* redo_n, uint16_t* redo_list,
+                                               int lane)
+{
+    constexpr int K = N < 1 ? 1 : N;
+    const ImageJob& J = P.job;
+#pragma unroll 1
+    for (int h = 0; h < kTileW / 32; ++h) {
+        const int x = lane + 32 * h;
+        const int Xo = x0 + x;
+        if (Xo >= J.W) continue;
+        int alpha, beta, fi;
+        u128 m[K + 1];
+        stats(rr, x, alpha, beta, m, fi);
+        const long long pix = (long long)Y * J.W + Xo;
+        const float th = s_maps[rr * kTileW + x], sg = s_maps[(kChunk + rr) * kTileW + x];
+        double g;
+        int fb = 0;
+        PixelTrace tr;
+        PixelTrace* trp = (PREC == kPrecFP64 && P.dbg.mu) ? &tr : nullptr;
+        u128 M[K + 1];
+        if (!(sg > 0.0f) || !isfinite(sg) || !isfinite(th)) {
+            g = __longlong_as_double(0x7ff8000000000000LL);
+            if (P.status) atomicOr(P.status, kStatusBadInput);
+            trp = nullptr;
+        } else {
+            if constexpr (PREC == kPrecFP64) {
+                g = sep_pixel_fp64<N>(alpha, beta, fi, m, th, sg, fb, trp, M);
+            } else {
+                bool redo = false;
+                if constexpr (PREC == kPrecC32)
+                    g = (double)sep_pixel_c32<N>(alpha, beta, fi, m, th, sg, fb, redo);
+                else
+                    g = (double)sep_pixel_fp32<N, PREC>(alpha, beta, fi, m, th, sg, fb, redo);
+                if (redo) {   // binary32 not accurate enough here: queue for the FP64 pass
+                    const unsigned slot = atomicAdd(redo_n, 1u);
+                    redo_list[slot] = (uint16_t)((rr << 8) | x);
+                    continue;
+                }
+            }
+            if (fb && P.n_fallback) atomicAdd(P.n_fallback, 1ull);
+        }
+        sep_store(J, pix, g);
+        if (PREC == kPrecFP64 && P.dbg.alpha) {   // the stage planes come from the FP64 form only
+            const SepDebug& D = P.dbg;
+            const long long pl = (long long)J.H * J.W;
+            D.alpha[pix] = (uint8_t)alpha;
+            D.beta[pix] = (uint8_t)beta;
+            for (int k = 0; k <= N; ++k) {
+                D.m[2 * (k * pl + pix)] = (uint64_t)m[k];
+                D.m[2 * (k * pl + pix) + 1] = (uint64_t)(m[k] >> 64);
+            }
+            D.flags[pix] = (alpha == beta ? 1 : 0) | (fb ? 2 : 0);
+            if (trp && alpha != beta) {
+                for (int k = 0; k <= N; ++k) {
+                    D.M[2 * (k * pl + pix)] = (uint64_t)M[k];
+                    D.M[2 * (k * pl + pix) + 1] = (uint64_t)(M[k] >> 64);
+                    D.mu[k * pl + pix] = tr.mu[k];
+                    D.c[k * pl + pix] = tr.c[k];
+                }
+                for (int k = 0; k <= N + 1; ++k) D.I[k * pl + pix] = tr.I[k];
+                D.t0lam[pix] = tr.t0;
+                D.t0lam[pl + pix] = tr.lam;
+                D.T[pix] = tr.T1;
+                D.T[pl + pix] = tr.T2;
+            }
+        }
+    }
+}
+
+// The pixels a binary32 form queued, on the FP64 path (the compensated form's
+// own FP64 redo), packed into full warps; y0r0 is the image row of chunk row 0.
+template <int N, int PREC, typename Stats>
+__device__ __forceinline__ void sep_redo_pass(const SepParams& P, Stats& stats, int y0r0, int x0,
+                                              const float* s_maps, const unsigned* redo_n,
+                                              const uint16_t* redo_list)
+{
+    constexpr int K = N < 1 ? 1 : N;
+    const ImageJob& J = P.job;
+    unsigned long long* redo_count = P.n_fallback ? P.n_fallback + 1 : nullptr;
+    const unsigned nr = *redo_n;
+    for (unsigned i = threadIdx.x; i < nr; i += blockDim.x) {
+        const int e = redo_list[i];
+        const int rr = e >> 8, x = e & 255;
+        int alpha, beta, fi, fb = 0;
+        u128 m[K + 1], M[K + 1];
+        stats(rr, x, alpha, beta, m, fi);
+        const long long pix = (long long)(y0r0 + rr) * J.W + (x0 + x);
+        const float th = s_maps[rr * kTileW + x], sg = s_maps[(kChunk + rr) * kTileW + x];
+        const double g = PREC == kPrecCFP32 ? sep_pixel_cfp32_redo<N>(alpha, beta, fi, m, th, sg, fb)
+                                            : sep_pixel_fp64<N>(alpha, beta, fi, m, th, sg, fb, nullptr, M);
+        sep_store(J, pix, g);
+        if (fb && P.n_fallback) atomicAdd(P.n_fallback, 1ull);
+        if (redo_count) atomicAdd(redo_count, 1ull);
+    }
+}
+
 template <int N, int PREC>
 __device__ __forceinline__ void sep_tile(const CUtensorMap* tmap, const SepParams& P, int tx, int ty,
                                          uint8_t* smem, uint32_t& phase)
@@ -299,7 +410,6 @@ __device__ __forceinline__ void sep_tile(const CUtensorMap* tmap, const SepParam
     uint16_t* redo_list = reinterpret_cast<uint16_t*>(reinterpret_cast<uint8_t*>(redo_n) + 16);
     float* s_maps = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(redo_n) + kRedoBytes);   // [2][kChunk][kTileW]
     const bool maps16 = maps_in_16(J);
-    unsigned long long* redo_count = P.n_fallback ? P.n_fallback + 1 : nullptr;
 
     if (J.use_tma) {
         const bool ok = tma_load_tile(tmap, tile, bar, xs, ys, (uint32_t)(R * Cb), phase);
@@ -479,10 +589,6 @@ __device__ __forceinline__ void sep_tile(const CUtensorMap* tmap, const SepParam
             if constexpr (K >= 5) m[5] = (u128)lo5 + ((u128)hi5 << 32);
             if constexpr (K >= 6) m[6] = (u128)lo6 + ((u128)hi6 << 32);
         };
-        auto store = [&](long long pix, double g) {
-            if (J.out_f64) static_cast<double*>(J.out)[pix] = g;
-            else static_cast<float*>(J.out)[pix] = (float)g;
-        };
 
         // 2. Horizontal pass: warp `warp` owns chunk row `warp`.
         {
@@ -495,89 +601,12 @@ __device__ __forceinline__ void sep_tile(const CUtensorMap* tmap, const SepParam
                 warp_sparse_row<true>(vmin + rr * Cb, Cb, levels, lane);
                 warp_sparse_row<false>(vmax + rr * Cb, Cb, levels, lane);
             }
-            if (Y < J.H) {
-#pragma unroll 1
-                for (int h = 0; h < kTileW / 32; ++h) {
-                    const int x = lane + 32 * h;
-                    const int Xo = x0 + x;
-                    if (Xo >= J.W) continue;
-                    int alpha, beta, fi;
-                    u128 m[K + 1];
-                    stats(rr, x, alpha, beta, m, fi);
-                    const long long pix = (long long)Y * J.W + Xo;
-                    const float th = s_maps[rr * kTileW + x], sg = s_maps[(kChunk + rr) * kTileW + x];
-                    double g;
-                    int fb = 0;
-                    PixelTrace tr;
-                    PixelTrace* trp = (PREC == kPrecFP64 && P.dbg.mu) ? &tr : nullptr;
-                    u128 M[K + 1];
-                    if (!(sg > 0.0f) || !isfinite(sg) || !isfinite(th)) {
-                        g = __longlong_as_double(0x7ff8000000000000LL);
-                        if (P.status) atomicOr(P.status, kStatusBadInput);
-                        trp = nullptr;
-                    } else {
-                        if constexpr (PREC == kPrecFP64) {
-                            g = sep_pixel_fp64<N>(alpha, beta, fi, m, th, sg, fb, trp, M);
-                        } else {
-                            bool redo = false;
-                            if constexpr (PREC == kPrecC32)
-                                g = (double)sep_pixel_c32<N>(alpha, beta, fi, m, th, sg, fb, redo);
-                            else
-                                g = (double)sep_pixel_fp32<N, PREC>(alpha, beta, fi, m, th, sg, fb, redo);
-                            if (redo) {   // binary32 not accurate enough here: queue for the FP64 pass
-                                const unsigned slot = atomicAdd(redo_n, 1u);
-                                redo_list[slot] = (uint16_t)((rr << 8) | x);
-                                continue;
-                            }
-                        }
-                        if (fb && P.n_fallback) atomicAdd(P.n_fallback, 1ull);
-                    }
-                    store(pix, g);
-                    if (PREC == kPrecFP64 && P.dbg.alpha) {   // the stage planes come from the FP64 form only
-                        const SepDebug& D = P.dbg;
-                        const long long pl = (long long)J.H * J.W;
-                        D.alpha[pix] = (uint8_t)alpha;
-                        D.beta[pix] = (uint8_t)beta;
-                        for (int k = 0; k <= N; ++k) {
-                            D.m[2 * (k * pl + pix)] = (uint64_t)m[k];
-                            D.m[2 * (k * pl + pix) + 1] = (uint64_t)(m[k] >> 64);
-                        }
-                        D.flags[pix] = (alpha == beta ? 1 : 0) | (fb ? 2 : 0);
-                        if (trp && alpha != beta) {
-                            for (int k = 0; k <= N; ++k) {
-                                D.M[2 * (k * pl + pix)] = (uint64_t)M[k];
-                                D.M[2 * (k * pl + pix) + 1] = (uint64_t)(M[k] >> 64);
-                                D.mu[k * pl + pix] = tr.mu[k];
-                                D.c[k * pl + pix] = tr.c[k];
-                            }
-                            for (int k = 0; k <= N + 1; ++k) D.I[k * pl + pix] = tr.I[k];
-                            D.t0lam[pix] = tr.t0;
-                            D.t0lam[pl + pix] = tr.lam;
-                            D.T[pix] = tr.T1;
-                            D.T[pl + pix] = tr.T2;
-                        }
-                    }
-                }
-            }
+            if (Y < J.H) sep_row_pixels<N, PREC>(P, stats, rr, Y, x0, s_maps, redo_n, redo_list, lane);
         }
         if constexpr (PREC != kPrecFP64) {
             // 3. The queued pixels on the FP64 path, packed into full warps.
             __syncthreads();
-            const unsigned nr = *redo_n;
-            for (unsigned i = threadIdx.x; i < nr; i += blockDim.x) {
-                const int e = redo_list[i];
-                const int rr = e >> 8, x = e & 255;
-                int alpha, beta, fi, fb = 0;
-                u128 m[K + 1], M[K + 1];
-                stats(rr, x, alpha, beta, m, fi);
-                const long long pix = (long long)(y0 + r0 + rr) * J.W + (x0 + x);
-                const float th = s_maps[rr * kTileW + x], sg = s_maps[(kChunk + rr) * kTileW + x];
-                const double g = PREC == kPrecCFP32 ? sep_pixel_cfp32_redo<N>(alpha, beta, fi, m, th, sg, fb)
-                                                    : sep_pixel_fp64<N>(alpha, beta, fi, m, th, sg, fb, nullptr, M);
-                store(pix, g);
-                if (fb && P.n_fallback) atomicAdd(P.n_fallback, 1ull);
-                if (redo_count) atomicAdd(redo_count, 1ull);
-            }
+            sep_redo_pass<N, PREC>(P, stats, y0 + r0, x0, s_maps, redo_n, redo_list);
         }
         __syncthreads();
     }

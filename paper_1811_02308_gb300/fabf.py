@@ -104,6 +104,10 @@ def load(path: str | None = None):
         "fabf_gaussian_taps": ([C.c_double, vp, i, C.POINTER(i)], i),
         "fabf_debug_stages_sep": ([vp, vp, vp, vp, i, i, sz, vp, i, i] + [vp] * 11, i),
         "fabf_bruteforce_sep": ([vp, vp, vp, vp, i, i, sz, vp, i, vp, i, i, vp], i),
+        "fabf_filter_cascade": ([vp, vp, vp, vp, i, i, sz, i, i, vp, i, i, vp], i),
+        "fabf_cascade_taps": ([i, vp, i, C.POINTER(i)], i),
+        "fabf_cascade_radius": ([C.c_double, C.POINTER(i)], i),
+        "fabf_debug_stages_cascade": ([vp, vp, vp, vp, i, i, sz, i, i] + [vp] * 11, i),
         "fabf_sharpen_maps": ([vp, vp, i, i, sz, C.POINTER(SharpenCfg), vp, vp, vp], i),
         "fabf_texture_sigma": ([vp, vp, i, i, sz, C.POINTER(TextureCfg), vp, vp], i),
         "fabf_sharpen": ([vp, vp, i, i, sz, C.POINTER(SharpenCfg), vp, i, vp], i),
@@ -415,14 +419,11 @@ def fabf_filter_sep(ctx: Context, img, theta, sigma, taps, N: int, out=None, out
     return out, rc
 
 
-def fabf_debug_stages_sep(ctx: Context, img, theta, sigma, taps, N: int):
-    """Every intermediate with the separable kernel; m and M are (N+1, H, W, 2)
-    uint64 word pairs held in int64 tensors (low word first)."""
+def _stage_planes(theta, N: int) -> dict:
     import torch
-    t = _taps(taps)
     H, W = int(theta.shape[0]), int(theta.shape[1])
     dev = theta.device
-    o = dict(
+    return dict(
         alpha=torch.zeros((H, W), dtype=torch.uint8, device=dev),
         beta=torch.zeros((H, W), dtype=torch.uint8, device=dev),
         m=torch.zeros((N + 1, H, W, 2), dtype=torch.int64, device=dev),
@@ -435,11 +436,66 @@ def fabf_debug_stages_sep(ctx: Context, img, theta, sigma, taps, N: int):
         flags=torch.zeros((H, W), dtype=torch.int32, device=dev),
         out=torch.zeros((H, W), dtype=torch.float64, device=dev),
     )
+
+
+_STAGE_KEYS = ("alpha", "beta", "m", "M", "mu", "c", "t0lam", "I", "T", "flags", "out")
+
+
+def fabf_debug_stages_sep(ctx: Context, img, theta, sigma, taps, N: int):
+    """Every intermediate with the separable kernel; m and M are (N+1, H, W, 2)
+    uint64 word pairs held in int64 tensors (low word first)."""
+    t = _taps(taps)
+    H, W = int(theta.shape[0]), int(theta.shape[1])
+    o = _stage_planes(theta, N)
     rc = load().fabf_debug_stages_sep(ctx.handle, _ptr(img), _ptr(theta), _ptr(sigma), H, W,
                                       int(img.shape[1]), t.ctypes.data, len(t) // 2, int(N),
-                                      *[_ptr(o[k]) for k in ("alpha", "beta", "m", "M", "mu", "c",
-                                                             "t0lam", "I", "T", "flags", "out")])
+                                      *[_ptr(o[k]) for k in _STAGE_KEYS])
     _check(rc, "fabf_debug_stages_sep")
+    return o
+
+
+def fabf_cascade_taps(rb: int) -> np.ndarray:
+    """Taps of the three-box cascade of radius rb (``fabf_cascade_taps``)."""
+    buf = np.zeros(2 * 40 + 1, np.uint32)
+    r = C.c_int(0)
+    _check(load().fabf_cascade_taps(int(rb), buf.ctypes.data, len(buf), C.byref(r)), "fabf_cascade_taps")
+    return buf[:2 * r.value + 1].copy()
+
+
+def fabf_cascade_radius(rho: float) -> int:
+    """The cascade radius whose variance rb (rb + 1) is nearest rho^2."""
+    rb = C.c_int(0)
+    _check(load().fabf_cascade_radius(float(rho), C.byref(rb)), "fabf_cascade_radius")
+    return rb.value
+
+
+def fabf_filter_cascade(ctx: Context, img, theta, sigma, rb: int, N: int, out=None, out_is_f64: bool = True,
+                        pitch: int | None = None, stream: int | None = None, tile_rows: int = 0,
+                        check: bool = True):
+    """Algorithm 1 with the three-box cascade of radius rb as spatial kernel,
+    O(1) per pixel in rb (``fabf_filter_cascade``)."""
+    H, W = int(theta.shape[0]), int(theta.shape[1])
+    p = int(pitch) if pitch is not None else int(img.shape[1])
+    if out is None:
+        out = _empty_like_out(theta, H, W, out_is_f64)
+    _check_out(out, H, W, out_is_f64)
+    _check_inputs(img, theta, sigma, H, W, p)
+    s = _stream_of(img, theta, sigma, out) if stream is None else stream
+    rc = load().fabf_filter_cascade(ctx.handle, _ptr(img), _ptr(theta), _ptr(sigma), H, W, p, int(rb), int(N),
+                                    _ptr(out), 1 if out_is_f64 else 0, int(tile_rows), s)
+    if check:
+        _check(rc, "fabf_filter_cascade")
+        return out
+    return out, rc
+
+
+def fabf_debug_stages_cascade(ctx: Context, img, theta, sigma, rb: int, N: int):
+    """fabf_debug_stages_sep's planes from the box-cascade kernel."""
+    H, W = int(theta.shape[0]), int(theta.shape[1])
+    o = _stage_planes(theta, N)
+    rc = load().fabf_debug_stages_cascade(ctx.handle, _ptr(img), _ptr(theta), _ptr(sigma), H, W,
+                                          int(img.shape[1]), int(rb), int(N), *[_ptr(o[k]) for k in _STAGE_KEYS])
+    _check(rc, "fabf_debug_stages_cascade")
     return o
 
 

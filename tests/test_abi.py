@@ -113,6 +113,39 @@ def test_separable_argument_checks_without_gpu(lib):
     assert lib.fabf_filter_sep(null, 0, 0, 0, 4, 4, 4, buf.ctypes.data, 1, 1, 0, 1, 0) == fabf.FABF_EINVAL
 
 
+def test_cascade_taps_are_the_three_fold_box_convolution(lib):
+    for rb in range(1, 14):
+        box = np.ones(2 * rb + 1, np.int64)
+        ref = np.convolve(np.convolve(box, box), box)
+        t = fabf.fabf_cascade_taps(rb)
+        assert len(t) == 6 * rb + 1 and np.array_equal(t.astype(np.int64), ref), rb
+        assert int(t.sum()) == (2 * rb + 1) ** 3
+        # the variance of a sum of three independent uniform variables on
+        # {-rb..rb}: 3 (n^2 - 1) / 12 = rb (rb + 1), exactly
+        d = np.arange(-3 * rb, 3 * rb + 1)
+        assert int((t.astype(np.int64) * d * d).sum()) == rb * (rb + 1) * int(t.sum())
+
+
+def test_cascade_radius_and_argument_checks_without_gpu(lib):
+    for rho in (0.3, 1.0, 1.5, 2.4, 3.0, 5.0, 7.7, 10.0, 13.0, 13.6):
+        rb = fabf.fabf_cascade_radius(rho)
+        best = min(range(1, 14), key=lambda k: abs(k * (k + 1) - rho * rho))
+        assert rb == best, rho
+    buf = np.zeros(81, np.uint32)
+    r = C.c_int(0)
+    rb = C.c_int(0)
+    assert lib.fabf_cascade_radius(0.0, C.byref(rb)) == fabf.FABF_EINVAL
+    assert lib.fabf_cascade_radius(float("inf"), C.byref(rb)) == fabf.FABF_EINVAL
+    assert lib.fabf_cascade_radius(14.5, C.byref(rb)) == fabf.FABF_EUNSUPPORTED
+    assert lib.fabf_cascade_taps(0, buf.ctypes.data, 81, C.byref(r)) == fabf.FABF_EINVAL
+    assert lib.fabf_cascade_taps(14, buf.ctypes.data, 81, C.byref(r)) == fabf.FABF_EUNSUPPORTED
+    assert lib.fabf_cascade_taps(3, buf.ctypes.data, 18, C.byref(r)) == fabf.FABF_EINVAL
+    null = C.c_void_p(0)
+    assert lib.fabf_filter_cascade(null, 0, 0, 0, 4, 4, 4, 1, 1, 0, 1, 0, 0) == fabf.FABF_EINVAL
+    assert lib.fabf_filter_cascade(null, 0, 0, 0, 4, 4, 4, 1, 1, 0, 1, 12, 0) == fabf.FABF_EINVAL
+    assert lib.fabf_filter_cascade(null, 0, 0, 0, 4, 4, 4, 14, 1, 0, 1, 0, 0) == fabf.FABF_EUNSUPPORTED
+
+
 def test_binding_rejects_mismatched_buffers():
     # the binding checks buffer types and sizes before any pointer reaches
     # a kernel (a float32 output passed with out_is_f64 = True would be
