@@ -805,6 +805,8 @@ def main():
     ap.add_argument("--profile-precision", type=int, default=0, choices=[0, 1, 2, 3])
     ap.add_argument("--profile-rho", type=float, default=None,
                     help="with --profile: the separable Gaussian kernel of this rho instead of the box")
+    ap.add_argument("--profile-cascade", type=int, default=None, metavar="RB",
+                    help="with --profile: the three-box cascade of radius RB instead of the box")
     ap.add_argument("--serve-seconds", type=float, default=30.0)
     ap.add_argument("--no-extra", action="store_true", help="skip the batch and serve legs")
     ap.add_argument("--sweep", action="store_true",
@@ -853,7 +855,12 @@ def main():
 
     if args.profile:
         fabf.fabf_set_precision(ctx, args.profile_precision)
-        if args.profile_rho is not None:
+        if args.profile_cascade is not None:
+            f, th, sg, o = slots[0][0]
+            total_ms, _ = R.timed(lambda i: fabf.fabf_filter_cascade(ctx, f, th, sg, args.profile_cascade, NDEG,
+                                                                     out=o, stream=R.sh),
+                                  args.steps, args.warmup)
+        elif args.profile_rho is not None:
             from paper_1811_02308_gb300 import synth
             taps = synth.gaussian_taps(args.profile_rho)
             f, th, sg, o = slots[0][0]
@@ -864,6 +871,7 @@ def main():
                                   args.warmup)
         st, _ = fabf.fabf_get_status(ctx, R.sh)
         print(json.dumps({"profile": args.profile, "precision": args.profile_precision, "rho": args.profile_rho,
+                          "cascade_rb": args.profile_cascade,
                           "ms_per_step": total_ms / args.steps, "status": st}), flush=True)
         ctx.close()
         return 0
