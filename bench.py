@@ -531,6 +531,66 @@ def serve_legs(R, prec, seconds, sweep_rates=(800.0, 2000.0, 4000.0), sweep_seco
     return main
 
 
+def run_cascade(R, slots, steps, rbs=(1, 2, 3, 5, 8, 13), N=NDEG):
+    """The three-box cascade spatial kernel (fabf_filter_cascade, O(1) per
+    pixel in rb) against the direct FIR on the same taps (fabf_filter_sep,
+    O(r)), both on the 1920x1080 inputs in the FP64 and centred binary32
+    forms: Mpix/s per radius, whether the two agree bit for bit, and the
+    PSNR of the cascade's result against the brute-force filter with the
+    Gaussian of the same variance (rho = sqrt(rb (rb + 1))), i.e. how closely
+    the cascade stands in for Eq. (4)."""
+    torch, fabf, ctx = R.torch, R.fabf, R.ctx
+    from paper_1811_02308_gb300 import synth
+    f0, th0, s0, _ = slots[0][0]
+    npix = H_ * W_
+    out = {"workload": "1920x1080 config-1 inputs, N = %d; cascade of three boxes of radius rb (r = 3 rb)" % N}
+    for rb in rbs:
+        taps = np.ascontiguousarray(fabf.fabf_cascade_taps(rb), np.uint32)
+        r = len(taps) // 2
+        rho = float(np.sqrt(rb * (rb + 1)))
+        row = {"rho": rho, "r": r}
+        for prec in (0, 3):
+            fabf.fabf_set_precision(ctx, prec)
+            sl = slots[prec]
+
+            def casc(i, sl=sl, prec=prec):
+                f, th, sg, o = sl[i % len(sl)]
+                rc = R.lib.fabf_filter_cascade(ctx.handle, f.data_ptr(), th.data_ptr(), sg.data_ptr(), H_, W_,
+                                               f.shape[1], rb, N, o.data_ptr(), 1 if prec == 0 else 0, 0, R.sh)
+                if rc != 0:
+                    raise fabf.FabfError(rc, "fabf_filter_cascade")
+
+            def fir(i, sl=sl, prec=prec):
+                f, th, sg, o = sl[i % len(sl)]
+                rc = R.lib.fabf_filter_sep(ctx.handle, f.data_ptr(), th.data_ptr(), sg.data_ptr(), H_, W_,
+                                           f.shape[1], taps.ctypes.data, r, N, o.data_ptr(), 1 if prec == 0 else 0,
+                                           R.sh)
+                if rc != 0:
+                    raise fabf.FabfError(rc, "fabf_filter_sep")
+
+            ms_c, kern_c = R.timed(casc, steps, 3)
+            ms_f, kern_f = R.timed(fir, steps, 3)
+            st, _, _ = fabf.fabf_get_status_ex(ctx, R.sh)
+            casc(0)
+            a = sl[0][3].clone()
+            fir(0)
+            same = bool(torch.equal(a, sl[0][3]))
+            row[FORM_NAMES[prec]] = {"cascade_mpix_per_s": npix * steps / (ms_c / 1e3) / 1e6,
+                                     "fir_mpix_per_s": npix * steps / (ms_f / 1e3) / 1e6,
+                                     "cascade_kernel_ms": kern_c, "fir_kernel_ms": kern_f,
+                                     "equal_to_fir": same, "status": st}
+            if prec == 3 and 3.0 * rho <= 40.0:
+                gt = synth.gaussian_taps(rho)
+                bf = fabf.fabf_bruteforce_sep(ctx, f0, th0, s0, gt, use_f64=False).cpu().numpy()
+                row["psnr_vs_gaussian_bruteforce_db"] = psnr(a.cpu().numpy().astype(np.float64),
+                                                             bf.astype(np.float64))
+        fabf.fabf_set_precision(ctx, 0)
+        out["rb=%d" % rb] = row
+    rates = [out["rb=%d" % rb]["c32"]["cascade_mpix_per_s"] for rb in rbs]
+    out["c32_cascade_min_over_max"] = min(rates) / max(rates)
+    return out
+
+
 def run_gaussian(R, slots, steps, rhos=(3.0, 5.0), N=NDEG):
     """The paper's own spatial kernel (Eq. (4), window [-3 rho, 3 rho]^2) on
     the same 1920x1080 inputs: Mpix/s of the separable FABF kernel in each
@@ -987,6 +1047,7 @@ def main():
                                for k, v in bf_ms.items()}}
     if rank == 0 and not args.no_extra and ws == 1:
         line["gaussian"] = run_gaussian(R, slots, max(10, args.steps // 10))
+        line["cascade"] = run_cascade(R, slots, max(10, args.steps // 2))
         line["applications"] = run_apps(R, slots, max(10, args.steps // 10), forms=(0, best))
         line["batch"] = {FORM_NAMES[p]: run_batch(R, p, max(5, args.steps // 20)) for p in (0, best)}
         line["serve"] = serve_legs(R, best, args.serve_seconds)
