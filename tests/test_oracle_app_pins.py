@@ -149,3 +149,105 @@ def test_texture_smoothing_removes_fine_texture(oracle_mod):
     _, (g1, g2) = oracle_mod.texture_filter(f, 3, 5, 2, 1.0, 8.0, 5.0, 60.0, taps, lq_for(taps, 10.0), 10.0, 40.0)
     inner = (slice(4, 20), slice(4, 20))
     assert g2[inner].std() < 0.3 * f[inner].std()
+
+
+# ---- properties the maps' definitions fix, independent of evaluation order
+
+def test_log_of_planes_and_parabolas_in_the_interior(oracle_mod):
+    # the Gaussian smoothing keeps an affine image affine (its taps are
+    # symmetric) and the 5-point Laplacian of an affine function is 0; of x^2
+    # it is 2 S^2 after smoothing with taps summing to S (second difference of
+    # x^2 is 2, the tap sums multiply), away from the clamped borders
+    taps = synth.gaussian_taps(1.0)
+    r = len(taps) // 2
+    S = int(taps.sum())
+    x = np.arange(16)
+    plane = np.clip(np.add.outer(3 * np.arange(12), 7 * x), 0, 255).astype(np.uint8)
+    para = np.tile((x * x).astype(np.uint8), (12, 1))
+    inner = (slice(r + 1, 12 - r - 1), slice(r + 1, 16 - r - 1))
+    Lp = oracle_mod.sharpen_log(plane, taps)
+    Lq = oracle_mod.sharpen_log(para, taps)
+    assert np.all(Lp[inner] == 0)
+    assert np.all(Lq[inner] == 2 * S * S)
+    # a zero Laplacian gives the widest kernel, a saturated one the narrowest
+    sg = oracle_mod.sharpen_sigma(plane, taps, lq_for(taps, 10.0), 10.0, 40.0)
+    assert np.all(sg[inner] == np.float32(40.0))
+    sq = oracle_mod.sharpen_sigma(para, taps, 2 * S * S, 10.0, 40.0)
+    assert np.all(sq[inner] == np.float32(10.0))
+
+
+def test_sharpen_theta_keeps_affine_images_in_the_interior(oracle_mod):
+    # the window mean of an affine image over a symmetric window is its
+    # centre value, so theta = 2 f - mean = f wherever the window is inside
+    w = 2
+    f = np.add.outer(5 * np.arange(10), 9 * np.arange(14)).astype(np.uint8)
+    th = oracle_mod.sharpen_theta(f, w)
+    inner = (slice(w, 10 - w), slice(w, 14 - w))
+    assert np.array_equal(th[inner], f[inner].astype(np.float32))
+
+
+def test_width_maps_are_monotone_and_bounded(oracle_mod):
+    f = image(40, 50, 21, n_blobs=8)
+    taps = synth.gaussian_taps(1.0)
+    Lq = lq_for(taps, 4.0)
+    L = np.abs(oracle_mod.sharpen_log(f, taps)).ravel()
+    sg = oracle_mod.sharpen_sigma(f, taps, Lq, 10.0, 40.0).ravel()
+    order = np.argsort(np.minimum(L, Lq), kind="stable")
+    assert np.all(np.diff(sg[order].astype(np.float64)) <= 0)          # non-increasing in |LoG|
+    assert sg.min() >= 10.0 and sg.max() <= 40.0
+    ts = oracle_mod.texture_sigma(f, 2, 1.0, 8.0, 5.0, 60.0)
+    assert ts.min() >= 5.0 and ts.max() <= 60.0
+
+
+def test_maps_commute_with_transposition_and_offsets(oracle_mod):
+    f = image(23, 31, 22, n_blobs=6)
+    taps = synth.gaussian_taps(1.5)
+    Lq = lq_for(taps, 6.0)
+    assert np.array_equal(oracle_mod.sharpen_theta(f.T.copy(), 3), oracle_mod.sharpen_theta(f, 3).T)
+    assert np.array_equal(oracle_mod.sharpen_log(f.T.copy(), taps), oracle_mod.sharpen_log(f, taps).T)
+    assert np.array_equal(oracle_mod.texture_sigma(f.T.copy(), 2, 1.0, 8.0, 5.0, 60.0),
+                          oracle_mod.texture_sigma(f, 2, 1.0, 8.0, 5.0, 60.0).T)
+    # mirror images: the Laplacian of the symmetric smoothing is mirrored
+    assert np.array_equal(oracle_mod.sharpen_log(f[:, ::-1].copy(), taps), oracle_mod.sharpen_log(f, taps)[:, ::-1])
+    # an offset of the intensities moves theta by the offset and leaves the
+    # widths unchanged (both depend on differences only)
+    g = (f.astype(np.int64) // 2 + 20).astype(np.uint8)
+    h = (g.astype(np.int64) + 37).astype(np.uint8)
+    assert np.array_equal(oracle_mod.sharpen_sigma(h, taps, Lq, 10.0, 40.0),
+                          oracle_mod.sharpen_sigma(g, taps, Lq, 10.0, 40.0))
+    assert np.array_equal(oracle_mod.texture_sigma(h, 2, 1.0, 8.0, 5.0, 60.0),
+                          oracle_mod.texture_sigma(g, 2, 1.0, 8.0, 5.0, 60.0))
+    # (theta is one rounding of an exact quotient: the offset moves it within
+    # two binary32 units of the values' binade)
+    d = oracle_mod.sharpen_theta(h, 3).astype(np.float64) - oracle_mod.sharpen_theta(g, 3).astype(np.float64)
+    assert np.all(np.abs(d - 37.0) <= 2 * float(np.spacing(np.float32(256))))
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_mrtv_of_a_ramp_a_step_and_a_stripe_texture(oracle_mod, k):
+    # closed forms of mRTV = delta * max|grad| / (sum|grad| + eps) over a
+    # (2k+1)^2 window inside the image (forward differences):
+    #   ramp f = b x:           delta = 2k b, max = b, sum = (2k+1)^2 b
+    #   step of height h:       delta = h,    max = h, sum = (2k+1) h
+    #   stripes 0, h, 0, h...:  delta = h,    max = h, sum = (2k+1)^2 h
+    # and sigma = hi - (hi - lo) min(mRTV / msat, 1)
+    n = 2 * k + 1
+    eps, msat, lo, hi = 1.0, 64.0, 5.0, 60.0
+    H, W = 4 * k + 5, 6 * k + 12
+    b, h = 3, 90
+    ramp = np.tile((b * np.arange(W)).astype(np.uint8), (H, 1))
+    step = np.zeros((H, W), np.uint8)
+    step[:, W // 2:] = h
+    stripes = np.tile(((np.arange(W) % 2) * h).astype(np.uint8), (H, 1))
+    y, xc = H // 2, W // 2
+    cases = [(ramp, xc, 2 * k * b * b / (n * n * b + eps)),
+             (step, xc, h * h / (n * h + eps)),
+             (stripes, xc, h * h / (n * n * h + eps))]
+    for img, x, mrtv in cases:
+        sg = oracle_mod.texture_sigma(img, k, eps, msat, lo, hi)
+        ref = hi - (hi - lo) * min(mrtv / msat, 1.0)
+        assert abs(float(sg[y, x]) - ref) <= 1e-5 * hi, (k, mrtv, sg[y, x], ref)
+    # an edge is far more structure than a fine texture of the same contrast
+    s_step = oracle_mod.texture_sigma(step, k, eps, msat, lo, hi)[y, xc]
+    s_tex = oracle_mod.texture_sigma(stripes, k, eps, msat, lo, hi)[y, xc]
+    assert s_step < s_tex
