@@ -49,7 +49,6 @@ NCU_TRAFFIC_BYTES = 18.77e6        # FP64 form kernel (8-row tiles)
 NCU_TRAFFIC_BYTES_FP64FIT = None   # FP64-fit kernel
 NCU_TRAFFIC_BYTES_CFP32 = None     # compensated binary32 kernel
 NCU_TRAFFIC_BYTES_C32 = 18.78e6    # centred binary32 kernel (16-row tiles, 4 CTAs per SM)
-NCU_TRAFFIC_BYTES_SEP = 18.77e6    # separable (Gaussian) kernel, rho = 5, compensated binary32
 FORM_NAMES = {0: "fp64", 1: "fp64fit_fp32rec", 2: "cfp32", 3: "c32"}
 FORMS = (0, 1, 2, 3)
 DTYPES = {0: "f64", 1: "f64 fit + f32", 2: "f32 (compensated fit)", 3: "f32 (centred fit)"}

@@ -35,7 +35,7 @@ SOURCES = [
     "fabf_peaks.cu",
 ]
 HEADERS = ["fabf_device.cuh", "fabf_kernels.cuh", "fabf_launch.cuh", "fabf_internal.h", "fabf_sep_kernels.cuh",
-           "fabf_casc_kernels.cuh"]
+           "fabf_casc_kernels.cuh", "fabf_fp64_tables.h"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

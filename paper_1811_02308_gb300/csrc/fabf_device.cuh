@@ -10,7 +10,10 @@
 #pragma once
 
 #include <cstdint>
+#include <cstring>
 #include <cuda_runtime.h>
+
+#include "fabf_fp64_tables.h"
 
 namespace fabf {
 
@@ -134,6 +137,124 @@ static __constant__ AinvSplitTable c_ainv_split = make_ainv_split_table();
 static __constant__ RecipTable c_recip = make_recip_table();
 
 // ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// The binary64 erfcx and exp of the FP64 integrals, written for this path
+// (their tables are made by gen_fp64_tables.py with mpmath): cheaper on the
+// FP64 pipe than the general library functions, which the FP64 form is
+// bound by, and as accurate (within 2 units in the last place; checked on
+// the host against mpmath, tests/test_fp64_functions.py).
+// ---------------------------------------------------------------------------
+static __device__ const double g_erfcx_tab[(FABF_ERFCX_DEG + 2) * (FABF_ERFCX_NSEG + 1)] = {FABF_ERFCX_TABLE,
+                                                                                            FABF_ERFCX_P0_LO};
+static __device__ const double g_exp2_64[64] = {FABF_EXP2_64_TABLE};
+
+#ifdef __CUDA_ARCH__
+#define FABF_TABLE_LOAD(p) __ldg(p)
+#else
+#define FABF_TABLE_LOAD(p) (*(p))
+#endif
+
+__host__ __device__ __forceinline__ int low_word(double v)
+{
+#ifdef __CUDA_ARCH__
+    return __double2loint(v);
+#else
+    uint64_t b;
+    std::memcpy(&b, &v, 8);
+    return (int)(uint32_t)b;
+#endif
+}
+
+// 2^m for -1022 <= m <= 1023, exactly.
+__host__ __device__ __forceinline__ double pow2i(int m)
+{
+#ifdef __CUDA_ARCH__
+    return __hiloint2double((m + 1023) << 20, 0);
+#else
+    const uint64_t b = (uint64_t)(m + 1023) << 52;
+    double v;
+    std::memcpy(&v, &b, 8);
+    return v;
+#endif
+}
+
+// erfcx(x) = exp(x^2) erfc(x) for x >= 0.  On [0, 8): 32 pieces of width
+// 1/4, each a degree-11 polynomial in t = 8x - 2i - 1 (Chebyshev
+// interpolants, truncation below 2e-17 relative); x >= 8: erfcx(x) =
+// g(1/x^2) / x with g a degree-11 polynomial in t = 128/x^2 - 1.
+// The coefficient k of piece i is tab[k (NSEG + 1) + i]; row DEG + 1 holds
+// the low parts of the constant coefficients, added before the final
+// rounding (p = p0 + lo + t q(t)).
+__host__ __device__ __forceinline__ double erfcx_fp64_with(double x, const double* tab)
+{
+    constexpr int S = FABF_ERFCX_NSEG + 1;
+    double t;
+    int i;
+    const bool large = !(x < 8.0);
+    if (!large) {
+        const double q = 4.0 * x;            // exact
+        const double fq = floor(q);
+        i = (int)fq;
+        i = i < 0 ? 0 : i;                    // (x >= 0 by contract; keeps the index in the table)
+        t = fma(2.0, q - fq, -1.0);           // 8x - 2i - 1, exact
+    } else {
+        const double r = 1.0 / x;
+        t = fma(128.0, r * r, -1.0);
+        i = FABF_ERFCX_NSEG;
+    }
+    const double* c = tab + i;
+    double q = FABF_TABLE_LOAD(c + FABF_ERFCX_DEG * S);
+#pragma unroll
+    for (int k = FABF_ERFCX_DEG - 1; k >= 1; --k) q = fma(q, t, FABF_TABLE_LOAD(c + k * S));
+    double p = FABF_TABLE_LOAD(c) + fma(q, t, FABF_TABLE_LOAD(c + (FABF_ERFCX_DEG + 1) * S));
+    if (large) p /= x;                             // 0 at x = inf
+    return p;
+}
+
+// exp(x) for x <= 709 by Tang's table-driven method (ACM TOMS 15(2), 1989):
+// N = rint(64 x / ln 2) = 64 m + j, r = x - N ln2/64 (two-part constant),
+// exp(x) = 2^m 2^(j/64) (1 + p(r)) with p the Taylor polynomial of degree 6
+// (|r| <= ln2/128: truncation below 3e-20).  Results below the normal range
+// are scaled in two steps (one rounding into the subnormals); x below
+// -745.2 gives 0.
+__host__ __device__ __forceinline__ double exp_fp64_with(double x, const double* T)
+{
+    if (!(x > -745.2)) return x != x ? x : 0.0;
+    constexpr double kShift = 0x1.8p52;
+    const double y = fma(x, FABF_EXP_INV_L, kShift);
+    const double Nd = y - kShift;             // rint(64 x / ln 2), exact
+    const int N = low_word(y);
+    double r = fma(-Nd, FABF_EXP_L1, x);
+    r = fma(-Nd, FABF_EXP_L2, r);
+    const int j = N & 63, m = N >> 6;
+    const double q = fma(fma(fma(fma(r, 1.0 / 720.0, 1.0 / 120.0), r, 1.0 / 24.0), r, 1.0 / 6.0), r, 0.5);
+    const double p = fma(r * r, q, r);        // exp(r) - 1
+    const double Tj = FABF_TABLE_LOAD(T + j);
+    const double e = fma(Tj, p, Tj);
+    if (m >= -1022) return e * pow2i(m);
+    return (e * pow2i(m + 54)) * 0x1p-54;
+}
+
+__device__ __forceinline__ double erfcx_fp64(double x) { return erfcx_fp64_with(x, g_erfcx_tab); }
+__device__ __forceinline__ double exp_fp64(double x) { return exp_fp64_with(x, g_exp2_64); }
+
+// The FP64 form's integrals take these (Own = true); the binary32 forms' FP64
+// recompute of the few pixels their guard rejects takes the library's
+// functions (Own = false), whose code keeps the registers of their hot loop
+// free (the table-driven versions made it spill at 64 registers).
+template <bool Own>
+__device__ __forceinline__ double erfcx_sel(double x)
+{
+    if constexpr (Own) return erfcx_fp64(x);
+    else return erfcx(x);
+}
+template <bool Own>
+__device__ __forceinline__ double exp_sel(double x)
+{
+    if constexpr (Own) return exp_fp64(x);
+    else return exp(x);
+}
+
 // Integrals I_k = int_0^1 t^k exp(-lambda (t - t0)^2) dt, Eq. (28), k = 0..K,
 // each multiplied by exp(lambda d^2) with d the distance from t0 to [0, 1].
 // That factor is common to numerator and denominator of Eq. (29) and keeps
@@ -196,7 +317,7 @@ __device__ __forceinline__ int backward_start_index(double lam, double t0)
     return c_kp64.v[min(31, (int)(lf * 32.0f))][min(7, (int)(af * 2.0f))];
 }
 
-template <int K>
+template <int K, bool Own = true>
 __device__ __forceinline__ void integrals_fp64(double lam, double t0, double (&I)[K + 1])
 {
     static_assert(K >= 1 && K <= 7, "K out of range");
@@ -212,15 +333,15 @@ __device__ __forceinline__ void integrals_fp64(double lam, double t0, double (&I
         //   outside [0, 1]: erfcx(sqrt(lambda) d) - E erfcx(sqrt(lambda)(1 + d)),
         // a = sqrt(lambda)(1 - t0), b = sqrt(lambda) t0, E = E1 (t0 < 0) or E0.
         const double d = t0 < 0.0 ? -t0 : (t0 > 1.0 ? t0 - 1.0 : 0.0);
-        const double E0s = exp(-lam * ((t0 - d) * (t0 + d)));
-        const double E1s = exp(-lam * ((1.0 - t0 - d) * (1.0 - t0 + d)));
+        const double E0s = exp_sel<Own>(-lam * ((t0 - d) * (t0 + d)));
+        const double E1s = exp_sel<Own>(-lam * ((1.0 - t0 - d) * (1.0 - t0 + d)));
         const bool inside = d == 0.0;
         const double S = inside ? 2.0 : 0.0;
         const double ca = inside ? E1s : -1.0;
         const double xa = inside ? sl * (1.0 - t0) : sl * d;
         const double cb = inside ? E0s : (t0 < 0.0 ? E1s : E0s);
         const double xb = inside ? sl * t0 : sl * (1.0 + d);
-        const double I0 = h * (S - ca * erfcx(xa) - cb * erfcx(xb));
+        const double I0 = h * (S - ca * erfcx_sel<Own>(xa) - cb * erfcx_sel<Own>(xb));
         const double e1 = E1s * inv2l;
         I[0] = I0;
         I[1] = fma(t0, I0, (E0s - E1s) * inv2l);
@@ -228,7 +349,7 @@ __device__ __forceinline__ void integrals_fp64(double lam, double t0, double (&I
         for (int k = 2; k <= K; ++k) I[k] = fma(t0, I[k - 1], fma((double)(k - 1) * inv2l, I[k - 2], -e1));
     } else {
         const double d = t0 < 0.0 ? -t0 : (t0 > 1.0 ? t0 - 1.0 : 0.0);
-        const double E1s = exp(-lam * ((1.0 - t0 - d) * (1.0 - t0 + d)));   // exp(-lam (1-t0)^2 + lam d^2)
+        const double E1s = exp_sel<Own>(-lam * ((1.0 - t0 - d) * (1.0 - t0 + d)));   // exp(-lam (1-t0)^2 + lam d^2)
         int Kp = backward_start_index(lam, t0);
         Kp = __reduce_max_sync(__activemask(), (unsigned)Kp);
         const double l2 = 2.0 * lam;
@@ -272,14 +393,14 @@ struct PixelTrace {       // optional per-pixel export of every stage
 // Eqs. (25), (28)-(29) from the fitted coefficients c (any common scale:
 // it cancels in F): t0, lambda, the integrals and the two sums, in the order
 // of Algorithm 1; returns F = T1 / T2.
-template <int N>
+template <int N, bool Own = true>
 __device__ __forceinline__ double fp64_ratio(const double (&c)[N + 1], int alpha, int d, float theta_f, float sigma_f,
                                              double& t0, double& lam, double (&I)[N + 2], double& T1, double& T2)
 {
     const double sg = (double)sigma_f;
     t0 = div_by_power((double)theta_f - (double)alpha, (double)d, __ldg(&g_recip_pow.v[0][d]));
     lam = (double)(d * d) / (2.0 * sg * sg);
-    integrals_fp64<N + 1>(lam, t0, I);
+    integrals_fp64<N + 1, Own>(lam, t0, I);
     T1 = c[0] * I[1];
     T2 = c[0] * I[0];
 #pragma unroll
@@ -290,7 +411,7 @@ __device__ __forceinline__ double fp64_ratio(const double (&c)[N + 1], int alpha
     return T1 / T2;
 }
 
-template <int N>
+template <int N, bool Own = true>
 __device__ __forceinline__ double fabf_tail_fp64(const AinvTable& A, int alpha, int d,
                                                  const double (&mu)[(N < 1 ? 1 : N) + 1], float theta_f,
                                                  float sigma_f, int& fallback, PixelTrace* tr)
@@ -306,7 +427,7 @@ __device__ __forceinline__ double fabf_tail_fp64(const AinvTable& A, int alpha, 
         c[n] = acc;
     }
     double t0, lam, I[N + 2], T1, T2;
-    double F = fp64_ratio<N>(c, alpha, d, theta_f, sigma_f, t0, lam, I, T1, T2);
+    double F = fp64_ratio<N, Own>(c, alpha, d, theta_f, sigma_f, t0, lam, I, T1, T2);
     fallback = 0;
     if (!(T2 > 0.0) || !isfinite(F)) {   // fitted polynomial not positive enough
         F = mu[1] / mu[0];                // sigma -> infinity limit (spatial-kernel mean)
@@ -329,7 +450,7 @@ __device__ __forceinline__ double fabf_tail_fp64(const AinvTable& A, int alpha, 
     return (double)alpha + (double)d * F;
 }
 
-template <int N>
+template <int N, bool Own = true>
 __device__ __forceinline__ double fabf_pixel_fp64(const AinvTable& A, int alpha, int beta, int fi,
                                                   const int64_t (&m)[(N < 1 ? 1 : N) + 1],
                                                   float theta_f, float sigma_f, int& fallback,
@@ -373,7 +494,7 @@ __device__ __forceinline__ double fabf_pixel_fp64(const AinvTable& A, int alpha,
 #pragma unroll
         for (int k = 0; k <= N; ++k) tr->M[k] = M[k];
     }
-    return fabf_tail_fp64<N>(A, alpha, d, mu, theta_f, sigma_f, fallback, tr);
+    return fabf_tail_fp64<N, Own>(A, alpha, d, mu, theta_f, sigma_f, fallback, tr);
 }
 
 
@@ -693,7 +814,7 @@ __device__ __forceinline__ double fabf_redo_scaled(const uint64_t (&v)[(N < 1 ? 
         c[n] = (double)sh + (double)sc;
     }
     double t0, lam, I[N + 2], T1, T2;
-    double F = fp64_ratio<N>(c, alpha, d, theta_f, sigma_f, t0, lam, I, T1, T2);
+    double F = fp64_ratio<N, false>(c, alpha, d, theta_f, sigma_f, t0, lam, I, T1, T2);
     fallback = 0;
     if (!(T2 > 0.0) || !isfinite(F)) {   // the sigma -> infinity limit, as fabf_tail_fp64
         F = ((double)muh[1] + (double)mul[1]) / ((double)muh[0] + (double)mul[0]);

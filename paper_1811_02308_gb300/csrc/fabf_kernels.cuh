@@ -737,7 +737,7 @@ __device__ __forceinline__ bool fabf_tile(const CUtensorMap* tmap, const ImageJo
                 const long long pix = (long long)(y0 + r0 + rr) * J.W + (x0 + x);
                 const float th = s_maps[rr * kTileW + x], sg = s_maps[(kChunk + rr) * kTileW + x];
                 const double g = PREC == kPrecCFP32 ? fabf_pixel_cfp32_redo<N>(alpha, beta, fi, m, th, sg, fb)
-                                                    : fabf_pixel_fp64<N>(c_ainv, alpha, beta, fi, m, th, sg, fb,
+                                                    : fabf_pixel_fp64<N, false>(c_ainv, alpha, beta, fi, m, th, sg, fb,
                                                                          nullptr);
                 store(pix, g);
                 if (fb && n_fallback) atomicAdd(n_fallback, 1ull);

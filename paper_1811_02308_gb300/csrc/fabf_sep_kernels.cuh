@@ -138,7 +138,7 @@ __device__ __forceinline__ void sep_shifted_moments(int alpha, const u128 (&m)[K
 }
 
 // Algorithm 1 at one pixel in binary64 from the weighted power sums m_k.
-template <int N>
+template <int N, bool Own = true>
 __device__ __forceinline__ double sep_pixel_fp64(int alpha, int beta, int fi, const u128 (&m)[(N < 1 ? 1 : N) + 1],
                                                  float th, float sg, int& fallback, PixelTrace* tr,
                                                  u128 (&M)[(N < 1 ? 1 : N) + 1])
@@ -155,7 +155,7 @@ __device__ __forceinline__ double sep_pixel_fp64(int alpha, int beta, int fi, co
         mu[k] = u128_to_double_rn(M[k]) / (double)dk;
         dk *= d;
     }
-    return fabf_tail_fp64<N>(c_ainv, alpha, d, mu, th, sg, fallback, tr);
+    return fabf_tail_fp64<N, Own>(c_ainv, alpha, d, mu, th, sg, fallback, tr);
 }
 
 // The binary32 forms at one pixel: exactly scaled moments mu'_k = M_k
@@ -376,7 +376,7 @@ __device__ __forceinline__ void sep_redo_pass(const SepParams& P, Stats& stats, 
         const long long pix = (long long)(y0r0 + rr) * J.W + (x0 + x);
         const float th = s_maps[rr * kTileW + x], sg = s_maps[(kChunk + rr) * kTileW + x];
         const double g = PREC == kPrecCFP32 ? sep_pixel_cfp32_redo<N>(alpha, beta, fi, m, th, sg, fb)
-                                            : sep_pixel_fp64<N>(alpha, beta, fi, m, th, sg, fb, nullptr, M);
+                                            : sep_pixel_fp64<N, false>(alpha, beta, fi, m, th, sg, fb, nullptr, M);
         sep_store(J, pix, g);
         if (fb && P.n_fallback) atomicAdd(P.n_fallback, 1ull);
         if (redo_count) atomicAdd(redo_count, 1ull);
