@@ -190,3 +190,48 @@ def test_cascade_host_buffers_unaligned_pitch_and_status(ctx, oracle_mod):
     s2[3, 4] = 0.0
     _, rc = fabf.fabf_filter_cascade(ctx, f, th, s2, rb, 5, check=False)
     assert rc == fabf.FABF_EINVAL
+
+
+@pytest.mark.parametrize("H,W,rb,N", [(65535, 9, 13, 6), (5, 65535, 13, 5), (65535, 3, 1, 3)])
+def test_cascade_maximum_dimensions(ctx, oracle_mod, H, W, rb, N):
+    # the largest height / width the ABI accepts, every pixel computed in the
+    # FP64 and centred forms, sampled pixels (and the corners) by the oracle
+    f, th, s = inputs(H, W, 950 + W, n_blobs=10)
+    taps = cascade_taps(rb)
+    d = [dev(a) for a in (f, th, s)]
+    g64 = fabf.fabf_filter_cascade(ctx, *d, rb, N).cpu().numpy()
+    st, _ = fabf.fabf_get_status(ctx)
+    assert st == fabf.FABF_OK
+    fabf.fabf_set_precision(ctx, fabf.FABF_C32)
+    try:
+        g32 = fabf.fabf_filter_cascade(ctx, *d, rb, N, out_is_f64=False).cpu().numpy()
+        st, _ = fabf.fabf_get_status(ctx)
+    finally:
+        fabf.fabf_set_precision(ctx, fabf.FABF_FP64)
+    assert st == fabf.FABF_OK
+    rng = np.random.default_rng(H + W + rb)
+    ys = np.concatenate([rng.integers(0, H, 1200), [0, 0, H - 1, H - 1]])
+    xs = np.concatenate([rng.integers(0, W, 1200), [0, W - 1, 0, W - 1]])
+    ref, _ = oracle_mod.fabf_sep_pixels(f, th, s, taps, N, ys, xs)
+    assert g_err(g64[ys, xs], ref) <= RTOL_G
+    assert float(np.max(np.abs(g32[ys, xs].astype(np.float64) - ref))) <= 0.3
+    assert np.isfinite(g64).all() and np.isfinite(g32).all()
+
+
+@pytest.mark.parametrize("prec", FORMS)
+def test_cascade_pinned_host_buffers_equal_device_path(ctx, prec):
+    # pinned theta, sigma and out are read and written in place by the kernel
+    # (only the image is copied): the result equals the device-pointer call
+    f, th, s = inputs(130, 210, 61)
+    fabf.fabf_set_precision(ctx, prec)
+    try:
+        for f64 in (True, False):
+            dref = fabf.fabf_filter_cascade(ctx, dev(f), dev(th), dev(s), 4, 5, out_is_f64=f64).cpu().numpy()
+            img = torch.from_numpy(f).pin_memory()
+            pth = torch.from_numpy(th).pin_memory()
+            psg = torch.from_numpy(s).pin_memory()
+            pout = torch.empty((130, 210), dtype=torch.float64 if f64 else torch.float32).pin_memory()
+            fabf.fabf_filter_cascade(ctx, img, pth, psg, 4, 5, out=pout, out_is_f64=f64)
+            assert np.array_equal(pout.numpy(), dref), (prec, f64)
+    finally:
+        fabf.fabf_set_precision(ctx, fabf.FABF_FP64)
