@@ -200,6 +200,25 @@ int read_and_clear_status(fabf_ctx* ctx, cudaStream_t s, int* status, uint64_t* 
     return FABF_OK;
 }
 
+unsigned* pinned_call_status(fabf_ctx* ctx) { return ctx->m_status ? ctx->m_status : ctx->d_status; }
+
+unsigned long long* pinned_call_nfb(fabf_ctx* ctx) { return ctx->m_status ? ctx->m_nfb : ctx->d_nfb; }
+
+int finish_pinned_call(fabf_ctx* ctx, cudaStream_t s)
+{
+    int st = FABF_OK;
+    if (!ctx->m_status) {
+        const int rc = read_and_clear_status(ctx, s, &st, nullptr, nullptr);
+        return rc ? rc : st;
+    }
+    const cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_status(e);
+    volatile unsigned* w = static_cast<volatile unsigned*>(ctx->h_mwords);
+    const unsigned bits = w[0];
+    for (size_t i = 0; i < fabf_ctx::kWordBytes / sizeof(unsigned); ++i) w[i] = 0u;
+    return (bits & kStatusTimeout) ? FABF_ETIMEOUT : (bits & kStatusBadInput) ? FABF_EINVAL : FABF_OK;
+}
+
 int run_fused_prec(fabf_ctx* ctx, int prec, const uint8_t* img, size_t pitch, const float* theta,
                    const float* sigma, int H, int W, int w, int N, void* out, int out_f64, int TH,
                    const DebugPlanes* dbg, unsigned* status, unsigned long long* nfb, cudaStream_t s,
@@ -392,16 +411,14 @@ static int filter_mapped(fabf_ctx* ctx, const uint8_t* img, bool img_dev, const 
     const size_t smem = make_job(&p.job, &tm, d_img, d_pitch, k_th, k_sg, H, W, w, N, k_out, out_f64,
                                  tile_rows_for(ctx, w, N, prec, H, W));
     p.job.maps_host = 1;
-    p.status = ctx->d_status;
-    p.n_fallback = ctx->d_nfb;
+    p.status = pinned_call_status(ctx);
+    p.n_fallback = pinned_call_nfb(ctx);
     const cudaError_t e = launch_fused(prec, N, tm, p, dim3(p.job.tiles_x, p.job.tiles_y), smem, s);
     if (e != cudaSuccess) {
         cudaStreamSynchronize(s);
         return cuda_status(e);
     }
-    int st = FABF_OK;
-    const int rc = read_and_clear_status(ctx, s, &st, nullptr, nullptr);
-    return rc ? rc : st;
+    return finish_pinned_call(ctx, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -438,6 +455,23 @@ int fabf_create(const fabf_config* cfg, fabf_ctx** out)
     }
     ctx->d_status = static_cast<unsigned*>(words);
     ctx->d_nfb = reinterpret_cast<unsigned long long*>(static_cast<uint8_t*>(words) + fabf_ctx::kNfbOffset);
+    int native_atomics = 0;
+    if (cudaDeviceGetAttribute(&native_atomics, cudaDevAttrHostNativeAtomicSupported, c.device) == cudaSuccess &&
+        native_atomics) {
+        void* hm = nullptr;
+        void* dm = nullptr;
+        if (cudaHostAlloc(&hm, fabf_ctx::kWordBytes, cudaHostAllocMapped) == cudaSuccess) {
+            std::memset(hm, 0, fabf_ctx::kWordBytes);
+            if (cudaHostGetDevicePointer(&dm, hm, 0) == cudaSuccess) {
+                ctx->h_mwords = hm;
+                ctx->m_status = static_cast<unsigned*>(dm);
+                ctx->m_nfb = reinterpret_cast<unsigned long long*>(static_cast<uint8_t*>(dm) + fabf_ctx::kNfbOffset);
+            } else {
+                cudaFreeHost(hm);
+            }
+        }
+        (void)cudaGetLastError();
+    }
     *out = ctx;
     return FABF_OK;
 }
@@ -453,6 +487,7 @@ int fabf_destroy(fabf_ctx* ctx)
     if (ctx->stage) cudaFree(ctx->stage);
     cudaFree(ctx->d_status);                 // the block holding d_nfb too
     cudaFreeHost(ctx->h_words);
+    if (ctx->h_mwords) cudaFreeHost(ctx->h_mwords);
     delete ctx;
     return FABF_OK;
 }

@@ -42,6 +42,14 @@ struct fabf_ctx {
     unsigned long long* d_nfb = nullptr;
     void* h_words = nullptr;
     std::mutex status_lock;
+    // a second status block in mapped pinned host memory, for the calls on
+    // pinned host buffers (one at a time, under stage_lock): the kernel's
+    // atomics land in host memory and the host reads them after the stream
+    // wait, with no copy or clear on the stream.  Only where the GPU's
+    // atomics on host memory are native (nullptr otherwise).
+    void* h_mwords = nullptr;                // host view
+    unsigned* m_status = nullptr;            // device view of the same block
+    unsigned long long* m_nfb = nullptr;
     void* stage = nullptr;                   // grow-only staging buffer for host pointers
     size_t stage_bytes = 0;
     std::mutex stage_lock;                   // one host-pointer call at a time uses the staging buffer
@@ -160,6 +168,14 @@ cudaError_t launch_batch_c32_wide(const BatchParams& p, int grid, size_t smem, c
 constexpr int kDefaultTileRows = 32;               // stage-export runs of the tests
 
 int read_and_clear_status(fabf_ctx* ctx, cudaStream_t s, int* status, uint64_t* nfb, uint64_t* nredo);
+
+// Status words for a call on pinned host buffers (the caller holds
+// stage_lock): the mapped block where the context has one, else the device
+// block; finish_pinned_call waits for the stream and returns the kernels'
+// status, clearing the words.
+unsigned* pinned_call_status(fabf_ctx* ctx);
+unsigned long long* pinned_call_nfb(fabf_ctx* ctx);
+int finish_pinned_call(fabf_ctx* ctx, cudaStream_t s);
 
 // Grow the context's staging buffer to at least `bytes`.
 int ensure_stage(fabf_ctx* ctx, size_t bytes);

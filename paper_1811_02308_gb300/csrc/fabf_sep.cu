@@ -192,14 +192,13 @@ static int filter_sep_impl(fabf_ctx* ctx, const uint8_t* img, const float* theta
         rc = stage_image(ctx, img, pi.device, H, W, pitch, s, &d_img, &d_pitch);
         if (rc) return rc;
         rc = run_sep(prec, T, d_img, d_pitch, static_cast<const float*>(pt.kptr), static_cast<const float*>(ps.kptr),
-                     H, W, N, const_cast<void*>(po.kptr), out_is_f64, TH, nullptr, ctx->d_status, ctx->d_nfb, s, 1);
+                     H, W, N, const_cast<void*>(po.kptr), out_is_f64, TH, nullptr, pinned_call_status(ctx),
+                     pinned_call_nfb(ctx), s, 1);
         if (rc) {
             cudaStreamSynchronize(s);
             return rc;
         }
-        int st = FABF_OK;
-        rc = read_and_clear_status(ctx, s, &st, nullptr, nullptr);
-        return rc ? rc : st;
+        return finish_pinned_call(ctx, s);
     }
     return with_device_buffers(
         ctx, img, theta, sigma, H, W, pitch, out, out_is_f64, s,

@@ -358,3 +358,29 @@ def test_pipelined_host_path_equals_device_path(ctx, H, W, w, N, f64, pitch_extr
         finally:
             fabf.fabf_set_precision(ctx, fabf.FABF_FP64)
         assert np.array_equal(host_out, d), (prec, np.abs(host_out - d).max())
+
+
+def test_pinned_host_buffers_report_status_and_clear_it(ctx):
+    # the pinned-buffer path reads the kernels' status words from mapped host
+    # memory: a non-positive sigma gives FABF_EINVAL (and NaN at that pixel),
+    # and the next call starts from clear words
+    f, th, s = inputs(70, 90, 5)
+    pth = torch.from_numpy(th).pin_memory()
+    bad = s.copy()
+    bad[10, 11] = 0.0
+    psg_bad = torch.from_numpy(bad).pin_memory()
+    psg = torch.from_numpy(s).pin_memory()
+    pout = torch.zeros((70, 90), dtype=torch.float64).pin_memory()
+    img = torch.from_numpy(f).pin_memory()
+    for prec in (fabf.FABF_FP64, fabf.FABF_C32):
+        fabf.fabf_set_precision(ctx, prec)
+        try:
+            _, rc = fabf.fabf_filter(ctx, img, pth, psg_bad, 3, 5, out=pout, check=False)
+            assert rc == fabf.FABF_EINVAL
+            assert np.isnan(pout.numpy()[10, 11]) and np.isfinite(np.delete(pout.numpy().ravel(), 10 * 90 + 11)).all()
+            _, rc = fabf.fabf_filter(ctx, img, pth, psg, 3, 5, out=pout, check=False)
+            assert rc == fabf.FABF_OK
+            st, _ = fabf.fabf_get_status(ctx)
+            assert st == fabf.FABF_OK
+        finally:
+            fabf.fabf_set_precision(ctx, fabf.FABF_FP64)
