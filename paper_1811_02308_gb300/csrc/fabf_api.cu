@@ -378,15 +378,45 @@ static int filter_host_pipelined(fabf_ctx* ctx, const uint8_t* img, const float*
 // device memory).  Synchronous: returns the kernels' status.  (Copying the
 // image in bands that start their tiles early measured no faster.)
 // ---------------------------------------------------------------------------
-int fabf::stage_image(fabf_ctx* ctx, const uint8_t* img, bool img_dev, int H, int W, size_t pitch, cudaStream_t s,
-                      const uint8_t** d_img, size_t* d_pitch)
+// Rows of 16-byte words of a pinned host image into the staging buffer.
+__global__ void __launch_bounds__(256) stage_rows_kernel(const uint4* __restrict__ src, long long src_pitch16,
+                                                         uint4* __restrict__ dst, long long dst_pitch16, int H,
+                                                         int row16)
+{
+    const long long total = (long long)H * row16;
+    for (long long i = (long long)blockIdx.x * 256 + threadIdx.x; i < total; i += (long long)gridDim.x * 256) {
+        const long long y = i / row16, x = i - y * row16;
+        dst[y * dst_pitch16 + x] = src[y * src_pitch16 + x];
+    }
+}
+
+int fabf::stage_image(fabf_ctx* ctx, const uint8_t* img, const PtrInfo& pi, int H, int W, size_t pitch,
+                      cudaStream_t s, const uint8_t** d_img, size_t* d_pitch)
 {
     *d_img = img;
     *d_pitch = pitch;
-    if (img_dev) return FABF_OK;
+    if (pi.device) return FABF_OK;
     const size_t ipitch = ((size_t)W + 15) & ~(size_t)15;
     const int rc = ensure_stage(ctx, ipitch * H);
     if (rc) return rc;
+    // the kernel reads exactly W bytes of every row: W a multiple of 16 (no
+    // read past the caller's last row), 16-byte aligned rows
+    if (pi.kptr && W % 16 == 0 && pitch % 16 == 0 && (reinterpret_cast<uintptr_t>(pi.kptr) & 15) == 0) {
+        // one 16-byte word per thread where the image allows (every load in
+        // flight at once: the link's latency, not its bandwidth, bounds a
+        // copy of this size)
+        const long long words = (long long)H * (W / 16);
+        const long long cap = 16LL * (ctx->num_sms > 0 ? ctx->num_sms : 1);
+        const int blocks = (int)std::min<long long>(cap, (words + 255) / 256);
+        stage_rows_kernel<<<blocks, 256, 0, s>>>(static_cast<const uint4*>(pi.kptr), (long long)(pitch / 16),
+                                                 static_cast<uint4*>(ctx->stage), (long long)(ipitch / 16), H,
+                                                 W / 16);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_status(e);
+        *d_img = static_cast<const uint8_t*>(ctx->stage);
+        *d_pitch = ipitch;
+        return FABF_OK;
+    }
     const cudaError_t e = ipitch == pitch
                               ? cudaMemcpyAsync(ctx->stage, img, pitch * H, cudaMemcpyHostToDevice, s)
                               : cudaMemcpy2DAsync(ctx->stage, ipitch, img, pitch, W, H, cudaMemcpyHostToDevice, s);
@@ -396,13 +426,13 @@ int fabf::stage_image(fabf_ctx* ctx, const uint8_t* img, bool img_dev, int H, in
     return FABF_OK;
 }
 
-static int filter_mapped(fabf_ctx* ctx, const uint8_t* img, bool img_dev, const float* k_th, const float* k_sg,
+static int filter_mapped(fabf_ctx* ctx, const uint8_t* img, const PtrInfo& pi, const float* k_th, const float* k_sg,
                          int H, int W, size_t pitch, int w, int N, void* k_out, int out_f64, cudaStream_t s)
 {
     std::lock_guard<std::mutex> staged(ctx->stage_lock);
     const uint8_t* d_img = nullptr;
     size_t d_pitch = 0;
-    const int src = stage_image(ctx, img, img_dev, H, W, pitch, s, &d_img, &d_pitch);
+    const int src = stage_image(ctx, img, pi, H, W, pitch, s, &d_img, &d_pitch);
     if (src) return src;
     const int prec = ctx->precision;
     FusedParams p;
@@ -513,7 +543,7 @@ int fabf_filter(fabf_ctx* ctx, const uint8_t* img, const float* theta, const flo
     const bool di = pi.device, dt = pt.device, ds = ps.device, dout = po.device;
     if (!(dt && ds && dout) && pt.kptr && ps.kptr && po.kptr)
         // pinned host maps and output: read and written in place by the kernel
-        return filter_mapped(ctx, img, di, static_cast<const float*>(pt.kptr), static_cast<const float*>(ps.kptr),
+        return filter_mapped(ctx, img, pi, static_cast<const float*>(pt.kptr), static_cast<const float*>(ps.kptr),
                              H, W, pitch, w, N, const_cast<void*>(po.kptr), out_is_f64, s);
     if (!di && !dt && !ds && !dout)
         return filter_host_pipelined(ctx, img, theta, sigma, H, W, pitch, w, N, out, out_is_f64, s);

@@ -181,8 +181,11 @@ int finish_pinned_call(fabf_ctx* ctx, cudaStream_t s);
 int ensure_stage(fabf_ctx* ctx, size_t bytes);
 
 // A host image copied into the staging buffer (16-byte rows for TMA) on s,
-// a device image passed through; the caller holds stage_lock.
-int stage_image(fabf_ctx* ctx, const uint8_t* img, bool img_dev, int H, int W, size_t pitch, cudaStream_t s,
+// a device image passed through; the caller holds stage_lock.  A pinned
+// image whose rows are whole 16-byte words is copied by a kernel that reads
+// it over the chip-to-chip link from every SM (faster than one copy-engine
+// transfer at these sizes); other host images by cudaMemcpy(2D)Async.
+int stage_image(fabf_ctx* ctx, const uint8_t* img, const PtrInfo& pi, int H, int W, size_t pitch, cudaStream_t s,
                 const uint8_t** d_img, size_t* d_pitch);
 
 // Run `launch(d_img, d_pitch, d_theta, d_sigma, d_out)` on device buffers.

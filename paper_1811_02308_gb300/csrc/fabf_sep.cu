@@ -189,7 +189,7 @@ static int filter_sep_impl(fabf_ctx* ctx, const uint8_t* img, const float* theta
         std::lock_guard<std::mutex> staged(ctx->stage_lock);
         const uint8_t* d_img = nullptr;
         size_t d_pitch = 0;
-        rc = stage_image(ctx, img, pi.device, H, W, pitch, s, &d_img, &d_pitch);
+        rc = stage_image(ctx, img, pi, H, W, pitch, s, &d_img, &d_pitch);
         if (rc) return rc;
         rc = run_sep(prec, T, d_img, d_pitch, static_cast<const float*>(pt.kptr), static_cast<const float*>(ps.kptr),
                      H, W, N, const_cast<void*>(po.kptr), out_is_f64, TH, nullptr, pinned_call_status(ctx),
