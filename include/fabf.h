@@ -465,6 +465,13 @@ int fabf_debug_stages_cascade(fabf_ctx* ctx, const uint8_t* img, const float* th
                               double* c, double* t0lam, double* I, double* T, int32_t* flags,
                               double* out);
 
+/* The FP64 form's own binary64 erfcx and exp (the functions of its
+ * integrals, Eq. (31)) on n device arguments: erfcx_out[j] = erfcx(|x[j]|),
+ * exp_out[j] = exp(-|x[j]|), all device pointers; synchronous.  Test entry
+ * point.  Errors: FABF_EINVAL (NULL or host pointers, n < 0), FABF_ECUDA. */
+int fabf_debug_fp64_functions(fabf_ctx* ctx, const double* x, int64_t n, double* erfcx_out,
+                              double* exp_out);
+
 /* Brute-force filter, Eqs. (1)-(3), with the separable kernel (O(r^2) per
  * pixel); arguments as fabf_bruteforce plus taps and r as fabf_filter_sep. */
 int fabf_bruteforce_sep(fabf_ctx* ctx, const uint8_t* img, const float* theta,

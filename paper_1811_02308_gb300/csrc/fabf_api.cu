@@ -451,6 +451,22 @@ static int filter_mapped(fabf_ctx* ctx, const uint8_t* img, const PtrInfo& pi, c
     return finish_pinned_call(ctx, s);
 }
 
+namespace fabf {
+
+// The FP64 form's erfcx and exp on n arguments (test entry point): erfcx at
+// |x|, exp at -|x|, the domains the integrals use.
+static __global__ void __launch_bounds__(256) fp64_functions_kernel(const double* x, long long n, double* erfcx_out,
+                                                             double* exp_out)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double a = fabs(x[i]);
+    erfcx_out[i] = erfcx_fp64(a);
+    exp_out[i] = exp_fp64(-a);
+}
+
+}  // namespace fabf
+
 // ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
@@ -652,6 +668,20 @@ int fabf_debug_integrals(fabf_ctx* ctx, const double* lambda, const double* t0, 
     case 6: integrals_kernel<6><<<blocks, threads>>>(lambda, t0, n, fp32, out); break;
     default: integrals_kernel<7><<<blocks, threads>>>(lambda, t0, n, fp32, out); break;
     }
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    return cuda_status(e);
+}
+
+int fabf_debug_fp64_functions(fabf_ctx* ctx, const double* x, int64_t n, double* erfcx_out, double* exp_out)
+{
+    if (!ctx || !x || !erfcx_out || !exp_out || n < 0) return FABF_EINVAL;
+    if (n == 0) return FABF_OK;
+    if (!is_device_ptr(x) || !is_device_ptr(erfcx_out) || !is_device_ptr(exp_out)) return FABF_EINVAL;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return FABF_ECUDA;
+    const int threads = 256;
+    const unsigned blocks = (unsigned)((n + threads - 1) / threads);
+    fp64_functions_kernel<<<blocks, threads>>>(x, n, erfcx_out, exp_out);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     return cuda_status(e);

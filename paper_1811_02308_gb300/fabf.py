@@ -105,6 +105,7 @@ def load(path: str | None = None):
         "fabf_debug_stages_sep": ([vp, vp, vp, vp, i, i, sz, vp, i, i] + [vp] * 11, i),
         "fabf_bruteforce_sep": ([vp, vp, vp, vp, i, i, sz, vp, i, vp, i, i, vp], i),
         "fabf_filter_cascade": ([vp, vp, vp, vp, i, i, sz, i, i, vp, i, i, vp], i),
+        "fabf_debug_fp64_functions": ([vp, vp, C.c_int64, vp, vp], i),
         "fabf_cascade_taps": ([i, vp, i, C.POINTER(i)], i),
         "fabf_cascade_radius": ([C.c_double, C.POINTER(i)], i),
         "fabf_debug_stages_cascade": ([vp, vp, vp, vp, i, i, sz, i, i] + [vp] * 11, i),
@@ -497,6 +498,17 @@ def fabf_debug_stages_cascade(ctx: Context, img, theta, sigma, rb: int, N: int):
                                           int(img.shape[1]), int(rb), int(N), *[_ptr(o[k]) for k in _STAGE_KEYS])
     _check(rc, "fabf_debug_stages_cascade")
     return o
+
+
+def fabf_debug_fp64_functions(ctx: Context, x):
+    """(erfcx(|x|), exp(-|x|)) from the FP64 form's own functions, on device
+    float64 tensors."""
+    import torch
+    e1 = torch.empty_like(x)
+    e2 = torch.empty_like(x)
+    _check(load().fabf_debug_fp64_functions(ctx.handle, _ptr(x), int(x.numel()), _ptr(e1), _ptr(e2)),
+           "fabf_debug_fp64_functions")
+    return e1, e2
 
 
 def fabf_bruteforce_sep(ctx: Context, img, theta, sigma, taps, out=None, out_is_f64: bool = True,
