@@ -146,7 +146,7 @@ static __constant__ RecipTable c_recip = make_recip_table();
 // ---------------------------------------------------------------------------
 static __device__ const double g_erfcx_tab[(FABF_ERFCX_DEG + 2) * (FABF_ERFCX_NSEG + 1)] = {FABF_ERFCX_TABLE,
                                                                                             FABF_ERFCX_P0_LO};
-static __device__ const double g_exp2_64[64] = {FABF_EXP2_64_TABLE};
+static __device__ const double g_exp2_tab[1 << FABF_EXP_TABLE_BITS] = {FABF_EXP2_TABLE};
 
 #ifdef __CUDA_ARCH__
 #define FABF_TABLE_LOAD(p) __ldg(p)
@@ -178,10 +178,10 @@ __host__ __device__ __forceinline__ double pow2i(int m)
 #endif
 }
 
-// erfcx(x) = exp(x^2) erfc(x) for x >= 0.  On [0, 8): 32 pieces of width
-// 1/4, each a degree-11 polynomial in t = 8x - 2i - 1 (Chebyshev
+// erfcx(x) = exp(x^2) erfc(x) for x >= 0.  On [0, 8): 64 pieces of width
+// 1/8, each a degree-9 polynomial in t = 16x - 2i - 1 (Chebyshev
 // interpolants, truncation below 2e-17 relative); x >= 8: erfcx(x) =
-// g(1/x^2) / x with g a degree-11 polynomial in t = 128/x^2 - 1.
+// g(1/x^2) / x with g a degree-9 polynomial in t = 128/x^2 - 1.
 // The coefficient k of piece i is tab[k (NSEG + 1) + i]; row DEG + 1 holds
 // the low parts of the constant coefficients, added before the final
 // rounding (p = p0 + lo + t q(t)).
@@ -192,11 +192,11 @@ __host__ __device__ __forceinline__ double erfcx_fp64_with(double x, const doubl
     int i;
     const bool large = !(x < 8.0);
     if (!large) {
-        const double q = 4.0 * x;            // exact
+        const double q = 8.0 * x;            // exact
         const double fq = floor(q);
         i = (int)fq;
         i = i < 0 ? 0 : i;                    // (x >= 0 by contract; keeps the index in the table)
-        t = fma(2.0, q - fq, -1.0);           // 8x - 2i - 1, exact
+        t = fma(2.0, q - fq, -1.0);           // 16x - 2i - 1, exact
     } else {
         const double r = 1.0 / x;
         t = fma(128.0, r * r, -1.0);
@@ -212,9 +212,9 @@ __host__ __device__ __forceinline__ double erfcx_fp64_with(double x, const doubl
 }
 
 // exp(x) for x <= 709 by Tang's table-driven method (ACM TOMS 15(2), 1989):
-// N = rint(64 x / ln 2) = 64 m + j, r = x - N ln2/64 (two-part constant),
-// exp(x) = 2^m 2^(j/64) (1 + p(r)) with p the Taylor polynomial of degree 6
-// (|r| <= ln2/128: truncation below 3e-20).  Results below the normal range
+// N = rint(256 x / ln 2) = 256 m + j, r = x - N ln2/256 (two-part
+// constant), exp(x) = 2^m 2^(j/256) (1 + p(r)) with p the Taylor polynomial
+// of degree 5 (|r| <= ln2/512: truncation below 1e-20).  Results below the normal range
 // are scaled in two steps (one rounding into the subnormals); x below
 // -745.2 gives 0.
 __host__ __device__ __forceinline__ double exp_fp64_with(double x, const double* T)
@@ -222,12 +222,12 @@ __host__ __device__ __forceinline__ double exp_fp64_with(double x, const double*
     if (!(x > -745.2)) return x != x ? x : 0.0;
     constexpr double kShift = 0x1.8p52;
     const double y = fma(x, FABF_EXP_INV_L, kShift);
-    const double Nd = y - kShift;             // rint(64 x / ln 2), exact
+    const double Nd = y - kShift;             // rint(256 x / ln 2), exact
     const int N = low_word(y);
     double r = fma(-Nd, FABF_EXP_L1, x);
     r = fma(-Nd, FABF_EXP_L2, r);
-    const int j = N & 63, m = N >> 6;
-    const double q = fma(fma(fma(fma(r, 1.0 / 720.0, 1.0 / 120.0), r, 1.0 / 24.0), r, 1.0 / 6.0), r, 0.5);
+    const int j = N & ((1 << FABF_EXP_TABLE_BITS) - 1), m = N >> FABF_EXP_TABLE_BITS;
+    const double q = fma(fma(fma(r, 1.0 / 120.0, 1.0 / 24.0), r, 1.0 / 6.0), r, 0.5);
     const double p = fma(r * r, q, r);        // exp(r) - 1
     const double Tj = FABF_TABLE_LOAD(T + j);
     const double e = fma(Tj, p, Tj);
@@ -236,7 +236,7 @@ __host__ __device__ __forceinline__ double exp_fp64_with(double x, const double*
 }
 
 __device__ __forceinline__ double erfcx_fp64(double x) { return erfcx_fp64_with(x, g_erfcx_tab); }
-__device__ __forceinline__ double exp_fp64(double x) { return exp_fp64_with(x, g_exp2_64); }
+__device__ __forceinline__ double exp_fp64(double x) { return exp_fp64_with(x, g_exp2_tab); }
 
 // The FP64 form's integrals take these (Own = true); the binary32 forms' FP64
 // recompute of the few pixels their guard rejects takes the library's

@@ -2,17 +2,17 @@
 binary64 erfcx and exp (fabf_device.cuh, `erfcx_fp64`, `exp_fp64`).
 
 erfcx(x) = exp(x^2) erfc(x), x >= 0:
-  * x < 8: 32 intervals [i/4, (i+1)/4); on each, the Chebyshev interpolant of
-    degree 11 at the Chebyshev points (computed with mpmath at 50 digits),
-    rewritten as a polynomial in t = 8x - 2i - 1 in [-1, 1) and rounded to
+  * x < 8: 64 intervals [i/8, (i+1)/8); on each, the Chebyshev interpolant of
+    degree 9 at the Chebyshev points (computed with mpmath at 50 digits),
+    rewritten as a polynomial in t = 16x - 2i - 1 in [-1, 1) and rounded to
     binary64.  Its truncation error is below 2e-17 relative (the Chebyshev
-    coefficients beyond degree 11 sum to less than that on every interval).
+    coefficients beyond degree 9 sum to less than that on every interval).
   * x >= 8: erfcx(x) = g(u) / x with u = 1/x^2 in (0, 1/64] and
     g(u) = x erfcx(x) (g(0) = 1/sqrt(pi), the asymptotic expansion's limit),
-    the Chebyshev interpolant of g of degree 11 on [0, 1/64] in t = 128u - 1.
+    the Chebyshev interpolant of g of degree 9 on [0, 1/64] in t = 128u - 1.
   The constant coefficient of each piece is also written as hi + lo.
-exp: Tang's table-driven method (ACM TOMS 15(2), 1989): 2^(j/64), j = 0..63,
-  correctly rounded, and the reduction constant ln2/64 split in two parts.
+exp: Tang's table-driven method (ACM TOMS 15(2), 1989): 2^(j/256), j = 0..255,
+  correctly rounded, and the reduction constant ln2/256 split in two parts.
 
 Run with: python gen_fp64_tables.py > fabf_fp64_tables.h  (mpmath needed; the
 header is committed, so building the library does not run this script)."""
@@ -24,8 +24,9 @@ import mpmath as mp
 
 mp.mp.dps = 50
 
-DEG = 11                 # polynomial degree of every erfcx piece
-NSEG = 32                # pieces of width 1/4 on [0, 8)
+DEG = 9                  # polynomial degree of every erfcx piece
+NSEG = 64                # pieces of width 1/8 on [0, 8)
+EXP_J = 256              # table entries of exp
 NCOEF = DEG + 1
 
 
@@ -72,13 +73,13 @@ def hexd(v) -> str:
 
 
 def main(out=sys.stdout):
-    pieces = [cheb_interp_power(erfcx, mp.mpf(i) / 4, mp.mpf(i + 1) / 4, DEG) for i in range(NSEG)]
+    pieces = [cheb_interp_power(erfcx, mp.mpf(i) / 8, mp.mpf(i + 1) / 8, DEG) for i in range(NSEG)]
     pieces.append(cheb_interp_power(g_large, 0, mp.mpf(1) / 64, DEG))
     nrow = NSEG + 1
     w = out.write
     w("// Generated by gen_fp64_tables.py (mpmath, 50 digits); do not edit.\n")
     w("// erfcx pieces: coefficient k of piece i at [k * %d + i]; pieces 0..%d are\n" % (nrow, NSEG - 1))
-    w("// polynomials in t = 8x - 2i - 1 on [i/4, (i+1)/4), piece %d the large-x\n" % NSEG)
+    w("// polynomials in t = 16x - 2i - 1 on [i/8, (i+1)/8), piece %d the large-x\n" % NSEG)
     w("// polynomial in t = 128/x^2 - 1 of x erfcx(x).\n")
     w("#pragma once\n\n")
     w("#define FABF_ERFCX_DEG %d\n" % DEG)
@@ -94,16 +95,17 @@ def main(out=sys.stdout):
     w("#define FABF_ERFCX_P0_LO \\\n")
     lo = [hexd(pieces[i][0] - mp.mpf(float(pieces[i][0]))) for i in range(nrow)]
     w(", \\\n".join("    " + ", ".join(lo[r:r + 4]) for r in range(0, nrow, 4)) + "\n\n")
-    # exp: 2^(j/64) correctly rounded, and ln2/64 = L1 + L2
-    w("#define FABF_EXP2_64_TABLE \\\n")
-    vals = [hexd(mp.mpf(2) ** (mp.mpf(j) / 64)) for j in range(64)]
-    w(", \\\n".join("    " + ", ".join(vals[r:r + 4]) for r in range(0, 64, 4)) + "\n\n")
-    ln2_64 = mp.log(2) / 64
-    L1 = mp.mpf(float(ln2_64))
-    L2 = mp.mpf(float(ln2_64 - L1))
-    w("#define FABF_EXP_INV_L %s   // 64 / ln 2\n" % hexd(64 / mp.log(2)))
-    w("#define FABF_EXP_L1 %s      // ln 2 / 64, leading part\n" % hexd(L1))
-    w("#define FABF_EXP_L2 %s      // ln 2 / 64 - L1\n" % hexd(L2))
+    # exp: 2^(j/256) correctly rounded, and ln2/256 = L1 + L2
+    w("#define FABF_EXP_TABLE_BITS 8\n")
+    w("#define FABF_EXP2_TABLE \\\n")
+    vals = [hexd(mp.mpf(2) ** (mp.mpf(j) / EXP_J)) for j in range(EXP_J)]
+    w(", \\\n".join("    " + ", ".join(vals[r:r + 4]) for r in range(0, EXP_J, 4)) + "\n\n")
+    ln2_j = mp.log(2) / EXP_J
+    L1 = mp.mpf(float(ln2_j))
+    L2 = mp.mpf(float(ln2_j - L1))
+    w("#define FABF_EXP_INV_L %s   // 256 / ln 2\n" % hexd(EXP_J / mp.log(2)))
+    w("#define FABF_EXP_L1 %s      // ln 2 / 256, leading part\n" % hexd(L1))
+    w("#define FABF_EXP_L2 %s      // ln 2 / 256 - L1\n" % hexd(L2))
 
 
 if __name__ == "__main__":

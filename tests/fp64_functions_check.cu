@@ -7,7 +7,7 @@
 #include "../paper_1811_02308_gb300/csrc/fabf_device.cuh"
 
 static const double h_erfcx[] = {FABF_ERFCX_TABLE, FABF_ERFCX_P0_LO};
-static const double h_exp[] = {FABF_EXP2_64_TABLE};
+static const double h_exp[] = {FABF_EXP2_TABLE};
 
 int main()
 {
