@@ -22,7 +22,8 @@
 //     shared memory between chunks; each output row costs one step on four
 //     bytes of the staged tile.  A tile starts 2r steps above its first
 //     output row with zero sums (the rows above the staged tile count as 0,
-//     which changes no window of an output row).  The vertical window
+//     which changes no window of an output row); those 2r steps are taken
+//     as one weighted sum per row (weights made on the host).  The vertical window
 //     extrema are the box kernel's (16-bit SIMD, threads Cb .. Cb + Cb/2).
 //  2. Horizontal phase, warp rr on chunk row rr: e of each V_k row, three
 //     warp prefix sums in registers, and m_k = the third prefix sum at the
@@ -106,6 +107,36 @@ __device__ __forceinline__ void casc_vertical_step(uint32_t (&u32)[3][2], uint64
             u64[0][k] += e64[k];
             u64[1][k] += u64[0][k];
             u64[2][k] += u64[1][k];
+        }
+    }
+}
+
+// The start sums of column c as one weighted sum per tile row: the powers
+// of byte b enter U1, U2 and V with the row's weights (w1, w2, w3) (the sums
+// after the 2r start-up steps from zero, unrolled; exact in the same
+// wrapping arithmetic).
+template <int K>
+__device__ __forceinline__ void casc_weighted_add(uint32_t (&u32)[3][2], uint64_t (&u64)[3][4], uint32_t b, int w1,
+                                                  int w2, int w3)
+{
+    const int w[3] = {w1, w2, w3};
+    const uint32_t q = b * b;
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+        u32[s][0] += (uint32_t)w[s] * b;
+        if constexpr (K >= 2) u32[s][1] += (uint32_t)w[s] * q;
+    }
+    if constexpr (K >= 3) {
+        const uint32_t p3 = q * b;
+        const uint32_t p4 = p3 * b;
+        const uint64_t p5 = (uint64_t)p4 * b;
+#pragma unroll
+        for (int s = 0; s < 3; ++s) {
+            const uint64_t ws = (uint64_t)(int64_t)w[s];
+            u64[s][0] += ws * p3;
+            if constexpr (K >= 4) u64[s][1] += ws * p4;
+            if constexpr (K >= 5) u64[s][2] += ws * p5;
+            if constexpr (K >= 6) u64[s][3] += ws * (p5 * b);
         }
     }
 }
@@ -243,12 +274,14 @@ __device__ __forceinline__ void casc_tile(const CUtensorMap* tmap, const SepPara
         }
     };
 
-    // Zero sums 2r steps above output row 0 (tile rows 0 .. 2r - 1 enter).
+    // The sums 2r steps after zero sums above output row 0 (tile rows 0 ..
+    // 2r - 1 entered), as one weighted sum per row.
     if (col_in) {
         uint32_t u32[3][2] = {};
         uint64_t u64[3][4] = {};
-#pragma unroll 1
-        for (int a = 0; a < 2 * r; ++a) step(u32, u64, a);
+#pragma unroll 2
+        for (int a = 0; a < 2 * r; ++a)
+            casc_weighted_add<K>(u32, u64, tile[a * Cb + c], T.pre_w[0][a], T.pre_w[1][a], T.pre_w[2][a]);
         save(u32, u64);
     }
 

@@ -146,7 +146,26 @@ static int make_cascade(int rb, SepTaps* T)
     if (rc) return rc;
     rc = make_taps(taps, r, T);
     if (rc) return rc;
-    T->casc_n = 2 * rb + 1;
+    // Weights of tile row t (0 <= t < A = 2r) in the running sums after A
+    // steps from zero, U1 = sum_a e(a), U2 = sum_a (A - a) e(a), V = sum_a
+    // (A - a)(A - a + 1)/2 e(a), with e(a) = sum_j c_j p(a - jn), c = (1, -3,
+    // 3, -1): the start sums of a tile as one weighted sum per row.
+    const int n = 2 * rb + 1, A = 2 * r;
+    const int c[4] = {1, -3, 3, -1};
+    for (int t = 0; t < A; ++t) {
+        int w1 = 0, w2 = 0, w3 = 0;
+        for (int j = 0; j < 4; ++j) {
+            const int L = A - t - j * n;   // steps left after row t enters as a = t + jn
+            if (L <= 0) continue;
+            w1 += c[j];
+            w2 += c[j] * L;
+            w3 += c[j] * L * (L + 1) / 2;
+        }
+        T->pre_w[0][t] = (int16_t)w1;
+        T->pre_w[1][t] = (int16_t)w2;
+        T->pre_w[2][t] = (int16_t)w3;
+    }
+    T->casc_n = n;
     return FABF_OK;
 }
 

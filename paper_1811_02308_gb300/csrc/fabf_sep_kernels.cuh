@@ -44,6 +44,7 @@ constexpr uint32_t kTapSumMax = 65535;   // keeps V_k < 2^64 and m_k < 2^81
 struct SepTaps {
     int r;
     int casc_n;                    // 0: direct FIR of g; else the box length n of a 3-box cascade (g its taps)
+    int16_t pre_w[3][2 * kWMax];   // cascade: weights of tile row t in the start sums U1, U2, V (2r rows)
     uint32_t g[2 * kWMax + 1];
     uint32_t G[2 * kWMax + 2];     // G[t] = g[0] + ... + g[t-1]
 };
