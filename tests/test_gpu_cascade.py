@@ -107,7 +107,7 @@ def test_cascade_stages_match_oracle(ctx, oracle_mod, H, W, rb, N, seed):
 
 
 @pytest.mark.parametrize("prec", FORMS)
-@pytest.mark.parametrize("rb,N", [(1, 5), (3, 6), (6, 4), (13, 5)])
+@pytest.mark.parametrize("rb,N", [(1, 5), (3, 6), (6, 4), (13, 5), (2, 0), (1, 2), (9, 3)])
 def test_cascade_equals_fir_bit_for_bit(ctx, prec, rb, N):
     # both paths sum exact integer moments, so the results agree in every bit
     f, th, s = inputs(150, 233, 100 + rb)
