@@ -90,7 +90,7 @@ def cfp32_executed_flops_per_pixel(N: int) -> float:
 # (32 x smsp__inst_executed.sum / pixels, one ncu capture of the launch
 # bench.py times; profiles/); a kernel is left out once it changes until it
 # is captured again.
-NCU_INST_PER_PIXEL = {3: 1253.5}
+NCU_INST_PER_PIXEL = {3: 1222.2}
 
 # This GPU's arithmetic pipe peaks, measured at start-up by fabf_pipe_peaks
 # (CUDA events around FP64 / FP32 FMA, INT32 IMAD and MUFU loops).
