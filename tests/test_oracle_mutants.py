@@ -69,6 +69,17 @@ MUTANTS = {
     "sharpening centre sign": ("* m[0] - m[1];", "* m[0] + m[1];"),
     "LoG centre weight": ("S[1] + S[2] + S[3] + S[4] - 4 * S[0]", "S[1] + S[2] + S[3] + S[4] - 5 * S[0]"),
     "texture gradient direction": ("clampi(xx + 1, 0, W - 1)", "clampi(xx - 1, 0, W - 1)"),
+    "LoG neighbour offset": ("const int dy[5] = {0, -1, 1, 0, 0}, dx[5] = {0, 0, 0, -1, 1};",
+                             "const int dy[5] = {0, -1, 2, 0, 0}, dx[5] = {0, 0, 0, -1, 1};"),
+    "sharpening saturation inverted": ("const int64_t q = L < Lq ? L : Lq;", "const int64_t q = L < Lq ? Lq : L;"),
+    "sharpening centre factor": ("const int64_t num = 2 * (int64_t)f", "const int64_t num = 3 * (int64_t)f"),
+    "mRTV with the gradient sum for its maximum": (
+        "const float mrtv = (float)((int64_t)(fmax - fmin) * gmax)",
+        "const float mrtv = (float)((int64_t)(fmax - fmin) * gsum)"),
+    "mRTV epsilon dropped": ("((float)gsum + (float)eps);", "((float)gsum);"),
+    "texture vertical gradient dropped": (
+        "const int64_t g = (vx > v ? vx - v : v - vx) + (vy > v ? vy - v : v - vy);",
+        "const int64_t g = (vx > v ? vx - v : v - vx);"),
     "texture width map reversed": ("u = 1.0f;\n            const float hi = (float)s_hi, lo = (float)s_lo;\n"
                                    "            sigma[(long)y * W + x] = hi - (hi - lo) * u;",
                                    "u = 1.0f;\n            const float hi = (float)s_hi, lo = (float)s_lo;\n"
@@ -100,6 +111,48 @@ def _refs():
 
 def _window(f, y, x, w):
     return f[max(0, y - w):y + w + 1, max(0, x - w):x + w + 1].astype(np.int64).ravel()
+
+
+def map_properties():
+    """Properties the Sec. IV maps' definitions fix whatever the evaluation
+    order (the closed forms of tests/test_oracle_app_pins.py): the LoG of an
+    affine image is 0 and of x^2 is 2 S^2 in the interior, theta = f on an
+    affine image, sigma at its bounds for a zero and a saturated LoG, mRTV's
+    closed forms on a ramp, a step and a stripe texture, and both width maps
+    commute with transposition."""
+    taps = synth.gaussian_taps(1.0)
+    r = len(taps) // 2
+    S = int(taps.sum())
+    x = np.arange(16)
+    plane = np.clip(np.add.outer(3 * np.arange(12), 7 * x), 0, 255).astype(np.uint8)
+    para = np.tile((x * x).astype(np.uint8), (12, 1))
+    inner = (slice(r + 1, 12 - r - 1), slice(r + 1, 16 - r - 1))
+    assert np.all(oracle.sharpen_log(plane, taps)[inner] == 0)
+    assert np.all(oracle.sharpen_log(para, taps)[inner] == 2 * S * S)
+    assert np.all(oracle.sharpen_sigma(plane, taps, 1000, 10.0, 40.0)[inner] == np.float32(40.0))
+    assert np.all(oracle.sharpen_sigma(para, taps, 2 * S * S, 10.0, 40.0)[inner] == np.float32(10.0))
+    aff = np.add.outer(5 * np.arange(10), 9 * np.arange(14)).astype(np.uint8)
+    assert np.array_equal(oracle.sharpen_theta(aff, 2)[2:8, 2:12], aff[2:8, 2:12].astype(np.float32))
+    k, n, eps, msat, lo, hi = 1, 3, 1.0, 64.0, 5.0, 60.0
+    Hh, Ww, b, h = 9, 18, 3, 90
+    ramp = np.tile((b * np.arange(Ww)).astype(np.uint8), (Hh, 1))
+    step = np.zeros((Hh, Ww), np.uint8)
+    step[:, Ww // 2:] = h
+    stripes = np.tile(((np.arange(Ww) % 2) * h).astype(np.uint8), (Hh, 1))
+    for img, mr in ((ramp, 2 * k * b * b / (n * n * b + eps)), (step, h * h / (n * h + eps)),
+                    (stripes, h * h / (n * n * h + eps))):
+        sg = oracle.texture_sigma(img, k, eps, msat, lo, hi)[Hh // 2, Ww // 2]
+        assert abs(float(sg) - (hi - (hi - lo) * min(mr / msat, 1.0))) <= 1e-5 * hi
+    f = synth.make_inputs(15, 19, 8, n_blobs=4)[0]
+    assert np.array_equal(oracle.texture_sigma(f.T.copy(), 2, 1.0, 8.0, 5.0, 60.0),
+                          oracle.texture_sigma(f, 2, 1.0, 8.0, 5.0, 60.0).T)
+    assert np.array_equal(oracle.sharpen_log(f.T.copy(), taps), oracle.sharpen_log(f, taps).T)
+
+
+APPLICATION_MUTANTS = ["sharpening centre sign", "LoG centre weight", "texture gradient direction",
+                       "texture width map reversed", "LoG neighbour offset", "sharpening saturation inverted",
+                       "sharpening centre factor", "mRTV with the gradient sum for its maximum",
+                       "mRTV epsilon dropped", "texture vertical gradient dropped"]
 
 
 def battery():
@@ -275,7 +328,8 @@ def battery():
             mr = f32(int(fi[sl].max() - fi[sl].min()) * int(g[sl].max())) / (f32(int(g[sl].sum())) + f32(1.0))
             assert ts[y, x] == f32(60.0) - (f32(60.0) - f32(5.0)) * min(mr / f32(8.0), f32(1.0))
 
-    for name, fn in [("hilbert", hilbert), ("window", window_stats), ("integrals", integrals),
+    for name, fn in [("map properties", map_properties),
+                     ("hilbert", hilbert), ("window", window_stats), ("integrals", integrals),
                      ("fit", fit_moments), ("constant", constant_image), ("box mean", box_mean_limit),
                      ("truncated normal", truncated_normal), ("bruteforce", bruteforce),
                      ("fallback", fallback_rule), ("separable", separable), ("applications", applications)]:
@@ -315,3 +369,23 @@ def test_mutant_is_caught(source, name):
         with oracle.use_library(lib):
             fails = battery()
     assert fails, "planted mistake '%s' was not caught by any pin" % name
+
+
+def test_unmodified_oracle_has_the_map_properties(source):
+    with tempfile.TemporaryDirectory() as d:
+        lib = _build(source, d, "orig_maps")
+        with oracle.use_library(lib):
+            map_properties()
+
+
+@pytest.mark.parametrize("name", APPLICATION_MUTANTS)
+def test_application_mutant_breaks_a_map_property(source, name):
+    # the properties alone (no restatement of the maps' evaluation order)
+    # catch each planted mistake in the Sec. IV maps
+    old, new = MUTANTS[name]
+    assert source.count(old) == 1, "mutation site no longer unique: %r" % old
+    with tempfile.TemporaryDirectory() as d:
+        lib = _build(source.replace(old, new), d, "mut_maps")
+        with oracle.use_library(lib):
+            with pytest.raises(Exception):
+                map_properties()
