@@ -286,7 +286,7 @@ int fabf_cascade_taps(int rb, uint32_t* taps, int capacity, int* r);
 
 /* The cascade radius rb (1..13) whose variance rb (rb + 1) is nearest rho^2
  * (host only).  Errors: FABF_EINVAL (rho <= 0 or not finite, NULL),
- * FABF_EUNSUPPORTED (rho above the largest cascade, about 13.8). */
+ * FABF_EUNSUPPORTED (rho above 14, where rb = 14 would be nearest). */
 int fabf_cascade_radius(double rho, int* rb);
 
 /* ---- applications (Sec. IV) ---------------------------------------------- */
