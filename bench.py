@@ -530,6 +530,64 @@ def serve_legs(R, prec, seconds, sweep_rates=(800.0, 2000.0, 4000.0), sweep_seco
     return main
 
 
+def run_paper_tables(R, steps=5):
+    """The shapes of the paper's Tables I and II (Sec. III) on a synthetic
+    512x512 stand-in for its test image (classical bilateral filter: theta =
+    f, sigma = 40; Gaussian spatial kernel of Eq. (4)).  Table I: PSNR of
+    Algorithm 1 (FP64 form) against the GPU FP64 brute force for N = 0..6 at
+    rho = 3, 5, 10.  Table II: ms per image for N = 1, 3, 5 at rho = 3, 5, 7,
+    9, 11 -- FABF in the FP64 form (direct FIR, the paper's precision and
+    convolution), the centred binary32 form with the three-box cascade of the
+    same variance, and the brute force (FP64 and binary32)."""
+    torch, fabf, ctx = R.torch, R.fabf, R.ctx
+    from paper_1811_02308_gb300 import synth
+    H = W = 512
+    f, _, _ = synth.make_inputs(H, W, 4242, n_blobs=40)
+    th = f.astype(np.float32)
+    sg = np.full((H, W), 40.0, np.float32)
+    d = [torch.from_numpy(a).to(R.dev) for a in (f, th, sg)]
+    out = torch.empty((H, W), dtype=torch.float64, device=R.dev)
+    out32 = torch.empty((H, W), dtype=torch.float32, device=R.dev)
+
+    def ms_of(fn):
+        total, _ = R.timed(lambda i: fn(), steps, 2)
+        return total / steps
+
+    table1 = {"N": list(range(7))}
+    fabf.fabf_set_precision(ctx, 0)
+    for rho in (3, 5, 10):
+        taps = synth.gaussian_taps(rho)
+        bf = fabf.fabf_bruteforce_sep(ctx, *d, taps, use_f64=True).cpu().numpy()
+        row = []
+        for N in range(7):
+            g = fabf.fabf_filter_sep(ctx, *d, taps, N, out=out).cpu().numpy()
+            row.append(round(psnr(g, bf), 2))
+        table1["rho=%d" % rho] = row
+    table2 = {}
+    for rho in (3, 5, 7, 9, 11):
+        taps = synth.gaussian_taps(rho)
+        rb = fabf.fabf_cascade_radius(rho)
+        row = {}
+        for N in (1, 3, 5):
+            fabf.fabf_set_precision(ctx, 0)
+            row["fp64 N=%d" % N] = round(ms_of(lambda: fabf.fabf_filter_sep(ctx, *d, taps, N, out=out,
+                                                                              stream=R.sh)), 3)
+            fabf.fabf_set_precision(ctx, 3)
+            row["centred cascade N=%d" % N] = round(ms_of(lambda: fabf.fabf_filter_cascade(
+                ctx, *d, rb, N, out=out32, out_is_f64=False, stream=R.sh)), 3)
+        fabf.fabf_set_precision(ctx, 0)
+        row["brute force fp64"] = round(ms_of(lambda: fabf.fabf_bruteforce_sep(ctx, *d, taps, out=out, use_f64=True,
+                                                                              stream=R.sh)), 3)
+        row["brute force fp32"] = round(ms_of(lambda: fabf.fabf_bruteforce_sep(ctx, *d, taps, out=out32,
+                                                                              out_is_f64=False, use_f64=False,
+                                                                              stream=R.sh)), 3)
+        row["cascade rb"] = rb
+        table2["rho=%d" % rho] = row
+    st, _ = fabf.fabf_get_status(ctx, R.sh)
+    return {"workload": "512x512 synthetic (40 blobs), theta = f, sigma = 40, Gaussian taps of Eq. (4)",
+            "table1_psnr_db": table1, "table2_ms": table2, "status": st}
+
+
 def run_cascade(R, slots, steps, rbs=(1, 2, 3, 5, 8, 13), N=NDEG):
     """The three-box cascade spatial kernel (fabf_filter_cascade, O(1) per
     pixel in rb) against the direct FIR on the same taps (fabf_filter_sep,
@@ -1047,6 +1105,7 @@ def main():
     if rank == 0 and not args.no_extra and ws == 1:
         line["gaussian"] = run_gaussian(R, slots, max(10, args.steps // 10))
         line["cascade"] = run_cascade(R, slots, max(10, args.steps // 2))
+        line["paper_tables"] = run_paper_tables(R)
         line["applications"] = run_apps(R, slots, max(10, args.steps // 10), forms=(0, best))
         line["batch"] = {FORM_NAMES[p]: run_batch(R, p, max(5, args.steps // 20)) for p in (0, best)}
         line["serve"] = serve_legs(R, best, args.serve_seconds)
