@@ -87,3 +87,27 @@ def test_binary32_forms_against_oracle_on_timed_workload(ctx, oracle_mod, worklo
         err = np.abs(g[ys, xs].astype(np.float64) - ref)
         mx, rms = float(err.max()), float(np.sqrt(np.mean(err * err)))
         assert mx <= MAX_GRAY and rms <= RMS_GRAY[N], (prec, N, mx, rms, n_redo)
+
+
+@pytest.mark.parametrize("N", [5, 6])
+def test_binary32_forms_against_oracle_at_4096(ctx, oracle_mod, N):
+    # config 3: 4096x4096, 2000 blobs, w = 20, sigma in [5, 60] (theta = f),
+    # every binary32 form against the oracle on 1200 sampled pixels
+    Hc = Wc = 4096
+    f, th, s = synth.make_inputs(Hc, Wc, synth.config_seed(3, 0), n_blobs=2000, zeta_range=None,
+                                 sigma_range=(5, 60))
+    rng = np.random.default_rng(40 + N)
+    ys = np.concatenate([rng.integers(0, Hc, 1200), [0, 0, Hc - 1, Hc - 1]])
+    xs = np.concatenate([rng.integers(0, Wc, 1200), [0, Wc - 1, 0, Wc - 1]])
+    ref, _ = oracle_mod.fabf_pixels(f, th, s, WR, N, ys, xs)
+    d = [torch.from_numpy(a).cuda() for a in (f, th, s)]
+    for prec in (fabf.FABF_FP64FIT_FP32REC, fabf.FABF_CFP32, fabf.FABF_C32):
+        fabf.fabf_set_precision(ctx, prec)
+        try:
+            g = fabf.fabf_filter(ctx, *d, WR, N, out_is_f64=False)[ys, xs].cpu().numpy()
+            st, _, _ = fabf.fabf_get_status_ex(ctx)
+        finally:
+            fabf.fabf_set_precision(ctx, fabf.FABF_FP64)
+        assert st == fabf.FABF_OK
+        err = np.abs(g.astype(np.float64) - ref)
+        assert float(err.max()) <= MAX_GRAY and float(np.sqrt(np.mean(err * err))) <= RMS_GRAY[N], (prec, N)
