@@ -96,9 +96,13 @@ __host__ __device__ constexpr AinvSplitTable make_ainv_split_table()
 // v[k-1][d] = RN(1 / d^k), built at compile time (a binary64 division of two
 // exactly representable numbers, correctly rounded).  With them a quotient
 // a / d^k costs one multiplication and two fused multiply-adds instead of a
-// full division and is still correctly rounded (div_by_power below).
+// full division and is still correctly rounded (div_by_power below).  The
+// powers themselves, p[k-1][d] = d^k (exact), are loaded with them rather
+// than converted from integers (the conversion issues on the FP64 pipe,
+// which bounds the FP64 form).
 struct RecipPowTable {
     double v[kNMax][256];
+    double p[kNMax][256];
 };
 
 __host__ __device__ constexpr RecipPowTable make_recip_pow_table()
@@ -109,6 +113,7 @@ __host__ __device__ constexpr RecipPowTable make_recip_pow_table()
             double p = 1.0;
             for (int i = 0; i < k; ++i) p *= (double)d;   // exact: d^k <= 255^6 < 2^53
             t.v[k - 1][d] = 1.0 / p;
+            t.p[k - 1][d] = p;
         }
     return t;
 }
@@ -116,6 +121,14 @@ __host__ __device__ constexpr RecipPowTable make_recip_pow_table()
 // In global memory (read through the read-only cache): the lanes of a warp
 // index it by their own d, which a constant-memory table would serialise.
 static __device__ const RecipPowTable g_recip_pow = make_recip_pow_table();
+
+// 0 <= v < 2^52 as a binary64 value, exactly: the bit pattern of 2^52 + v
+// (v fills the mantissa), less 2^52.  One addition on the FP64 pipe in place
+// of a 64-bit integer conversion.
+__device__ __forceinline__ double small_to_double(int64_t v)
+{
+    return __hiloint2double(0x43300000 | (int)((uint64_t)v >> 32), (int)(uint32_t)v) - 0x1p52;
+}
 
 // RN(a / b) for b = d^k from r = RN(1 / b): q0 = RN(a r) lies within one unit
 // in the last place of a / b, the residual a - b q0 is exact as one fused
@@ -311,17 +324,28 @@ __host__ __device__ constexpr KpTableF64 make_kp_table_f64()
 
 static __constant__ KpTableF64 c_kp64 = make_kp_table_f64();
 
+// An approximation of 1 / x (x normal, positive): the hardware's approximate
+// binary64 reciprocal (PTX rcp.approx.ftz.f64), far closer than the few
+// percent the recursion's start values need.
+__device__ __forceinline__ double rcp_approx_f64(double x)
+{
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+    return r;
+}
+
 __device__ __forceinline__ int backward_start_index(double lam, double t0)
 {
     const float lf = (float)lam, af = fabsf((float)t0);
     return c_kp64.v[min(31, (int)(lf * 32.0f))][min(7, (int)(af * 2.0f))];
 }
 
+// inv2l is 1 / (2 lambda) to within a unit or two in the last place (the
+// forward recursion's coefficient; the callers form it without a division).
 template <int K, bool Own = true>
-__device__ __forceinline__ void integrals_fp64(double lam, double t0, double (&I)[K + 1])
+__device__ __forceinline__ void integrals_fp64(double lam, double inv2l, double t0, double (&I)[K + 1])
 {
     static_assert(K >= 1 && K <= 7, "K out of range");
-    const double inv2l = 0.5 / lam;
     if (lam >= kLambdaForward) {
         const double rl = rsqrt(lam);
         const double sl = lam * rl;                               // sqrt(lambda)
@@ -355,8 +379,10 @@ __device__ __forceinline__ void integrals_fp64(double lam, double t0, double (&I
         const double l2 = 2.0 * lam;
         const double q = l2 * (t0 - 1.0);
         double r1 = (double)(Kp + 2) + q, r0 = (double)(Kp + 1) + q;
-        double hi = E1s / (r1 > 1.0 ? r1 : (double)(Kp + 2));    // I_{Kp+1}
-        double lo = E1s / (r0 > 1.0 ? r0 : (double)(Kp + 1));    // I_{Kp}
+        // start values: a few percent is enough (the recursion damps their
+        // error below 1e-13 by index K), so approximate reciprocals
+        double hi = E1s * rcp_approx_f64(r1 > 1.0 ? r1 : (double)(Kp + 2));   // I_{Kp+1}
+        double lo = E1s * rcp_approx_f64(r0 > 1.0 ? r0 : (double)(Kp + 1));   // I_{Kp}
         // (hi, lo) = (I_k, I_{k-1}); produce I_{k-2} for k = Kp+1 .. K+2.
         for (int k = Kp + 1; k >= K + 2; --k) {
             const double nx = fma(l2, fma(-t0, lo, hi), E1s) * c_recip.v[k - 1];
@@ -398,9 +424,13 @@ __device__ __forceinline__ double fp64_ratio(const double (&c)[N + 1], int alpha
                                              double& t0, double& lam, double (&I)[N + 2], double& T1, double& T2)
 {
     const double sg = (double)sigma_f;
-    t0 = div_by_power((double)theta_f - (double)alpha, (double)d, __ldg(&g_recip_pow.v[0][d]));
-    lam = (double)(d * d) / (2.0 * sg * sg);
-    integrals_fp64<N + 1, Own>(lam, t0, I);
+    const double sg2 = sg * sg;                                   // exact (24-bit mantissas)
+    t0 = div_by_power((double)theta_f - small_to_double(alpha), __ldg(&g_recip_pow.p[0][d]),
+                      __ldg(&g_recip_pow.v[0][d]));
+    lam = __ldg(&g_recip_pow.p[1][d]) / (2.0 * sg2);
+    // 1 / (2 lambda) = sigma^2 / d^2: one rounding of sg2 RN(1 / d^2)
+    const double inv2l = sg2 * __ldg(&g_recip_pow.v[1][d]);
+    integrals_fp64<N + 1, Own>(lam, inv2l, t0, I);
     T1 = c[0] * I[1];
     T2 = c[0] * I[0];
 #pragma unroll
@@ -447,7 +477,7 @@ __device__ __forceinline__ double fabf_tail_fp64(const AinvTable& A, int alpha, 
         tr->T2 = T2;
         tr->fallback = fallback;
     }
-    return (double)alpha + (double)d * F;
+    return small_to_double(alpha) + small_to_double(d) * F;
 }
 
 template <int N, bool Own = true>
@@ -482,13 +512,14 @@ __device__ __forceinline__ double fabf_pixel_fp64(const AinvTable& A, int alpha,
     // once, is not): at N = 6 the fit amplifies a one-unit change in the last
     // place of mu to ~1e-8 relative in g_hat, so the 1e-9 agreement with the
     // oracle rests on the same values entering the same operations.
+    // 0 <= M_k <= m_0 d^k <= 6561 255^4 < 2^45 for k <= 4: exact without
+    // the conversion instruction
     double mu[K + 1];
-    int64_t dk = 1;
-    mu[0] = (double)M[0];
+    mu[0] = small_to_double(M[0]);
 #pragma unroll
     for (int k = 1; k <= K; ++k) {
-        dk *= d;
-        mu[k] = div_by_power((double)M[k], (double)dk, __ldg(&g_recip_pow.v[k - 1][d]));
+        const double a = k <= 4 ? small_to_double(M[k]) : (double)M[k];
+        mu[k] = div_by_power(a, __ldg(&g_recip_pow.p[k - 1][d]), __ldg(&g_recip_pow.v[k - 1][d]));
     }
     if (tr) {
 #pragma unroll

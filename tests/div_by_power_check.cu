@@ -22,6 +22,7 @@ int main()
             const double b = (double)bk;
             volatile double one = 1.0;
             if (t.v[k - 1][d] != one / b) ++bad_table;
+            if (t.p[k - 1][d] != b) ++bad_table;
             const double r = t.v[k - 1][d];
             const uint64_t mmax = 6561ull * bk;
             for (int i = 0; i < 2000; ++i) {
