@@ -178,6 +178,31 @@ __host__ __device__ __forceinline__ int low_word(double v)
 #endif
 }
 
+// The high 32 bits of a binary64 value, and the value whose high bits are hi
+// and low bits zero.
+__host__ __device__ __forceinline__ int high_word(double v)
+{
+#ifdef __CUDA_ARCH__
+    return __double2hiint(v);
+#else
+    uint64_t b;
+    std::memcpy(&b, &v, 8);
+    return (int)(uint32_t)(b >> 32);
+#endif
+}
+
+__host__ __device__ __forceinline__ double from_high_word(int hi)
+{
+#ifdef __CUDA_ARCH__
+    return __hiloint2double(hi, 0);
+#else
+    const uint64_t b = (uint64_t)(uint32_t)hi << 32;
+    double v;
+    std::memcpy(&v, &b, 8);
+    return v;
+#endif
+}
+
 // 2^m for -1022 <= m <= 1023, exactly.
 __host__ __device__ __forceinline__ double pow2i(int m)
 {
@@ -205,10 +230,17 @@ __host__ __device__ __forceinline__ double erfcx_fp64_with(double x, const doubl
     int i;
     const bool large = !(x < 8.0);
     if (!large) {
-        const double q = 8.0 * x;            // exact
-        const double fq = floor(q);
-        i = (int)fq;
-        i = i < 0 ? 0 : i;                    // (x >= 0 by contract; keeps the index in the table)
+        const double q = 8.0 * x;            // exact, in [0, 64)
+        // i = floor(q) and its binary64 value from q's bits (integer
+        // operations: the FP64 pipe, which bounds the FP64 form, stays
+        // free).  q < 64 has at most 5 integer bits, all in the high word:
+        // with e the unbiased exponent, i is the top e + 1 bits of the
+        // significand and floor(q) is q with the bits below them cleared.
+        const int hi = high_word(q);
+        const int e = (hi >> 20) - 1023;      // < 0 for q < 1 (and for +0)
+        const int sh = 20 - (e < 0 ? 0 : e);
+        i = e < 0 ? 0 : ((hi & 0xFFFFF) | 0x100000) >> sh;
+        const double fq = e < 0 ? 0.0 : from_high_word(hi & ~((1 << sh) - 1));
         t = fma(2.0, q - fq, -1.0);           // 16x - 2i - 1, exact
     } else {
         const double r = 1.0 / x;
@@ -322,7 +354,22 @@ __host__ __device__ constexpr KpTableF64 make_kp_table_f64()
     return t;
 }
 
-static __constant__ KpTableF64 c_kp64 = make_kp_table_f64();
+// In global memory (read-only cache): the lanes index it by their own bin,
+// which a constant-memory table would serialise.
+static __device__ const KpTableF64 g_kp64 = make_kp_table_f64();
+
+// min(cap, floor(|v| 2^s)) from the bits of v (integer operations only):
+// with e the unbiased exponent of |v| plus s, the value is the top e + 1
+// bits of the significand (0 for e < 0; cap once e reaches 20, which covers
+// infinities and NaN).  Requires cap < 2^20.
+__device__ __forceinline__ int floor_scaled_abs(double v, int s, int cap)
+{
+    const int hi = high_word(v) & 0x7FFFFFFF;
+    const int e = (hi >> 20) - 1023 + s;
+    if (e < 0) return 0;
+    if (e >= 20) return cap;
+    return min(cap, ((hi & 0xFFFFF) | 0x100000) >> (20 - e));
+}
 
 // An approximation of 1 / x (x normal, positive): the hardware's approximate
 // binary64 reciprocal (PTX rcp.approx.ftz.f64), far closer than the few
@@ -336,8 +383,7 @@ __device__ __forceinline__ double rcp_approx_f64(double x)
 
 __device__ __forceinline__ int backward_start_index(double lam, double t0)
 {
-    const float lf = (float)lam, af = fabsf((float)t0);
-    return c_kp64.v[min(31, (int)(lf * 32.0f))][min(7, (int)(af * 2.0f))];
+    return __ldg(&g_kp64.v[floor_scaled_abs(lam, 5, 31)][floor_scaled_abs(t0, 1, 7)]);
 }
 
 // inv2l is 1 / (2 lambda) to within a unit or two in the last place (the
@@ -378,11 +424,12 @@ __device__ __forceinline__ void integrals_fp64(double lam, double inv2l, double 
         Kp = __reduce_max_sync(__activemask(), (unsigned)Kp);
         const double l2 = 2.0 * lam;
         const double q = l2 * (t0 - 1.0);
-        double r1 = (double)(Kp + 2) + q, r0 = (double)(Kp + 1) + q;
+        const double kp2 = small_to_double(Kp + 2), kp1 = small_to_double(Kp + 1);
+        const double r1 = kp2 + q, r0 = kp1 + q;
         // start values: a few percent is enough (the recursion damps their
         // error below 1e-13 by index K), so approximate reciprocals
-        double hi = E1s * rcp_approx_f64(r1 > 1.0 ? r1 : (double)(Kp + 2));   // I_{Kp+1}
-        double lo = E1s * rcp_approx_f64(r0 > 1.0 ? r0 : (double)(Kp + 1));   // I_{Kp}
+        double hi = E1s * rcp_approx_f64(r1 > 1.0 ? r1 : kp2);   // I_{Kp+1}
+        double lo = E1s * rcp_approx_f64(r0 > 1.0 ? r0 : kp1);   // I_{Kp}
         // (hi, lo) = (I_k, I_{k-1}); produce I_{k-2} for k = Kp+1 .. K+2.
         for (int k = Kp + 1; k >= K + 2; --k) {
             const double nx = fma(l2, fma(-t0, lo, hi), E1s) * c_recip.v[k - 1];
@@ -999,7 +1046,7 @@ __host__ __device__ constexpr KpTableC32 make_kp_table_c32()
     return t;
 }
 
-static __constant__ KpTableC32 c_kp32 = make_kp_table_c32();
+static __device__ const KpTableC32 g_kp32 = make_kp_table_c32();   // global: lanes index it by their own bin
 
 // lambda at and above which integrals_c32 recurses forward.
 constexpr float kLambdaForwardC32 = 8.0f;
@@ -1014,7 +1061,7 @@ constexpr float kLambdaForwardC32 = 8.0f;
 //  lambda >= 8: forward, as written;
 //  lambda <  8: downward (the recursion solved for J_(k-1)), which damps
 //               errors once k exceeds about lambda (1 + |s0|) / 2, from a
-//               start index Kp taken from c_kp32 and made warp-uniform, with the
+//               start index Kp taken from g_kp32 and made warp-uniform, with the
 //               start values J_k ~ (E1 / (k + 1 - lambda (1 - t0))
 //               + (-1)^k E0 / (k + 1 - lambda t0)) / 2 (the mass of s^k near
 //               s = +-1); no erf is needed.
@@ -1044,7 +1091,7 @@ __device__ __forceinline__ void integrals_c32(float lam, float t0, float s0, flo
             J[k + 1] = fmaf(s0, J[k], fmaf((float)(2 * k) * il, J[k - 1], -((k & 1) ? Ep : Em) * il));
     } else {
         const int bl = min(31, (int)(lam * 4.0f)), bs = min(7, (int)(fabsf(s0) * 2.0f));
-        int Kp = c_kp32.v[bl][bs];
+        int Kp = __ldg(&g_kp32.v[bl][bs]);
         Kp = (int)__reduce_max_sync(__activemask(), (unsigned)Kp) | 1;   // odd: the step parities are fixed
         const float l1 = lam * (1.0f - t0), l0 = lam * t0;
         float a1 = (float)(Kp + 2) - l1, b1 = (float)(Kp + 2) - l0;
