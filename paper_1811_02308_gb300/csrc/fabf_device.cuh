@@ -130,6 +130,19 @@ __device__ __forceinline__ double small_to_double(int64_t v)
     return __hiloint2double(0x43300000 | (int)((uint64_t)v >> 32), (int)(uint32_t)v) - 0x1p52;
 }
 
+// A finite binary32 value as binary64, exactly, from its bits (integer
+// operations in place of the conversion instruction, which issues on the FP64
+// pipe): the exponent rebiased by 1023 - 127, the significand moved up 29
+// bits.  Zero, subnormals, infinities and NaN take the conversion.
+__device__ __forceinline__ double float_to_double(float x)
+{
+    const unsigned u = __float_as_uint(x);
+    const unsigned ef = (u >> 23) & 0xFFu;
+    if (ef == 0u || ef == 0xFFu) return (double)x;
+    const unsigned hi = (u & 0x80000000u) | ((ef + 896u) << 20) | ((u >> 3) & 0xFFFFFu);
+    return __hiloint2double((int)hi, (int)(u << 29));
+}
+
 // RN(a / b) for b = d^k from r = RN(1 / b): q0 = RN(a r) lies within one unit
 // in the last place of a / b, the residual a - b q0 is exact as one fused
 // multiply-add, and q0 + r (a - b q0) rounded once is the correctly rounded
@@ -228,7 +241,7 @@ __host__ __device__ __forceinline__ double erfcx_fp64_with(double x, const doubl
     constexpr int S = FABF_ERFCX_NSEG + 1;
     double t;
     int i;
-    const bool large = !(x < 8.0);
+    const bool large = high_word(x) >= 0x40200000;   // x >= 8 (or NaN) for x >= 0
     if (!large) {
         const double q = 8.0 * x;            // exact, in [0, 64)
         // i = floor(q) and its binary64 value from q's bits (integer
@@ -260,11 +273,14 @@ __host__ __device__ __forceinline__ double erfcx_fp64_with(double x, const doubl
 // N = rint(256 x / ln 2) = 256 m + j, r = x - N ln2/256 (two-part
 // constant), exp(x) = 2^m 2^(j/256) (1 + p(r)) with p the Taylor polynomial
 // of degree 5 (|r| <= ln2/512: truncation below 1e-20).  Results below the normal range
-// are scaled in two steps (one rounding into the subnormals); x below
-// -745.2 gives 0.
+// are scaled in two steps (one rounding into the subnormals); x at or below
+// -745.25 gives 0.
 __host__ __device__ __forceinline__ double exp_fp64_with(double x, const double* T)
 {
-    if (!(x > -745.2)) return x != x ? x : 0.0;
+    // x <= -745.25 (high word compared as an integer; the FP64 pipe stays
+    // free): below half the smallest subnormal, the result is 0
+    const int hx = high_word(x);
+    if (hx < 0 && (hx & 0x7FFFFFFF) >= 0x40874A00) return x != x ? x : 0.0;
     constexpr double kShift = 0x1.8p52;
     const double y = fma(x, FABF_EXP_INV_L, kShift);
     const double Nd = y - kShift;             // rint(256 x / ln 2), exact
@@ -386,14 +402,26 @@ __device__ __forceinline__ int backward_start_index(double lam, double t0)
     return __ldg(&g_kp64.v[floor_scaled_abs(lam, 5, 31)][floor_scaled_abs(t0, 1, 7)]);
 }
 
-// inv2l is 1 / (2 lambda) to within a unit or two in the last place (the
-// forward recursion's coefficient; the callers form it without a division).
+// The distance d from t0 to [0, 1] and whether t0 lies below 0, with the
+// comparisons made on t0's bits as 64-bit integers (ordered as the values
+// for t0 >= 0; the sign bit makes negative ones negative): the FP64 pipe
+// stays free.  t0 = -0 gives d = +0, as t0 = +0 does.
+__device__ __forceinline__ double dist_to_unit(double t0, bool& below)
+{
+    const long long b = __double_as_longlong(t0);
+    below = b < 0;
+    return below ? -t0 : (b > 0x3FF0000000000000LL ? t0 - 1.0 : 0.0);
+}
+
+// inv2l = 1 / (2 lambda) and rl = 1 / sqrt(lambda), each to within a unit or
+// two in the last place (the callers form them without a division or a
+// square root: 1 / (2 lambda) = sigma^2 / d^2, 1 / sqrt(lambda) =
+// sqrt(2) sigma / d).
 template <int K, bool Own = true>
-__device__ __forceinline__ void integrals_fp64(double lam, double inv2l, double t0, double (&I)[K + 1])
+__device__ __forceinline__ void integrals_fp64(double lam, double inv2l, double rl, double t0, double (&I)[K + 1])
 {
     static_assert(K >= 1 && K <= 7, "K out of range");
     if (lam >= kLambdaForward) {
-        const double rl = rsqrt(lam);
         const double sl = lam * rl;                               // sqrt(lambda)
         const double h = 0.88622692545275801364908374167057 * rl; // 1/2 sqrt(pi/lambda)
         // One path for the three positions of t0 (no divergence): with d the
@@ -402,14 +430,15 @@ __device__ __forceinline__ void integrals_fp64(double lam, double inv2l, double 
         //   inside  [0, 1]: erf(a) + erf(b) = 2 - E1 erfcx(a) - E0 erfcx(b),
         //   outside [0, 1]: erfcx(sqrt(lambda) d) - E erfcx(sqrt(lambda)(1 + d)),
         // a = sqrt(lambda)(1 - t0), b = sqrt(lambda) t0, E = E1 (t0 < 0) or E0.
-        const double d = t0 < 0.0 ? -t0 : (t0 > 1.0 ? t0 - 1.0 : 0.0);
+        bool below;
+        const double d = dist_to_unit(t0, below);
         const double E0s = exp_sel<Own>(-lam * ((t0 - d) * (t0 + d)));
         const double E1s = exp_sel<Own>(-lam * ((1.0 - t0 - d) * (1.0 - t0 + d)));
-        const bool inside = d == 0.0;
+        const bool inside = __double_as_longlong(d) == 0;          // d == +0
         const double S = inside ? 2.0 : 0.0;
         const double ca = inside ? E1s : -1.0;
         const double xa = inside ? sl * (1.0 - t0) : sl * d;
-        const double cb = inside ? E0s : (t0 < 0.0 ? E1s : E0s);
+        const double cb = inside ? E0s : (below ? E1s : E0s);
         const double xb = inside ? sl * t0 : sl * (1.0 + d);
         const double I0 = h * (S - ca * erfcx_sel<Own>(xa) - cb * erfcx_sel<Own>(xb));
         const double e1 = E1s * inv2l;
@@ -418,7 +447,8 @@ __device__ __forceinline__ void integrals_fp64(double lam, double inv2l, double 
 #pragma unroll
         for (int k = 2; k <= K; ++k) I[k] = fma(t0, I[k - 1], fma((double)(k - 1) * inv2l, I[k - 2], -e1));
     } else {
-        const double d = t0 < 0.0 ? -t0 : (t0 > 1.0 ? t0 - 1.0 : 0.0);
+        bool below;
+        const double d = dist_to_unit(t0, below);
         const double E1s = exp_sel<Own>(-lam * ((1.0 - t0 - d) * (1.0 - t0 + d)));   // exp(-lam (1-t0)^2 + lam d^2)
         int Kp = backward_start_index(lam, t0);
         Kp = __reduce_max_sync(__activemask(), (unsigned)Kp);
@@ -470,14 +500,15 @@ template <int N, bool Own = true>
 __device__ __forceinline__ double fp64_ratio(const double (&c)[N + 1], int alpha, int d, float theta_f, float sigma_f,
                                              double& t0, double& lam, double (&I)[N + 2], double& T1, double& T2)
 {
-    const double sg = (double)sigma_f;
+    const double sg = float_to_double(sigma_f);
     const double sg2 = sg * sg;                                   // exact (24-bit mantissas)
-    t0 = div_by_power((double)theta_f - small_to_double(alpha), __ldg(&g_recip_pow.p[0][d]),
-                      __ldg(&g_recip_pow.v[0][d]));
+    const double rd = __ldg(&g_recip_pow.v[0][d]);                // RN(1 / d)
+    t0 = div_by_power(float_to_double(theta_f) - small_to_double(alpha), __ldg(&g_recip_pow.p[0][d]), rd);
     lam = __ldg(&g_recip_pow.p[1][d]) / (2.0 * sg2);
-    // 1 / (2 lambda) = sigma^2 / d^2: one rounding of sg2 RN(1 / d^2)
+    // 1 / (2 lambda) = sigma^2 / d^2 and 1 / sqrt(lambda) = sqrt(2) sigma / d
     const double inv2l = sg2 * __ldg(&g_recip_pow.v[1][d]);
-    integrals_fp64<N + 1, Own>(lam, inv2l, t0, I);
+    const double rl = (sg * 1.4142135623730951) * rd;
+    integrals_fp64<N + 1, Own>(lam, inv2l, rl, t0, I);
     T1 = c[0] * I[1];
     T2 = c[0] * I[0];
 #pragma unroll

@@ -857,7 +857,7 @@ __global__ void integrals_kernel(const double* lam, const double* t0, long long 
         for (int k = 0; k <= K; ++k) out[i * (K + 1) + k] = (double)I[k];
     } else {
         double I[K + 1];
-        integrals_fp64<K>(lam[i], 0.5 / lam[i], t0[i], I);
+        integrals_fp64<K>(lam[i], 0.5 / lam[i], rsqrt(lam[i]), t0[i], I);
 #pragma unroll
         for (int k = 0; k <= K; ++k) out[i * (K + 1) + k] = I[k];
     }
