@@ -229,10 +229,10 @@ __host__ __device__ __forceinline__ double pow2i(int m)
 #endif
 }
 
-// erfcx(x) = exp(x^2) erfc(x) for x >= 0.  On [0, 8): 64 pieces of width
-// 1/8, each a degree-9 polynomial in t = 16x - 2i - 1 (Chebyshev
-// interpolants, truncation below 2e-17 relative); x >= 8: erfcx(x) =
-// g(1/x^2) / x with g a degree-9 polynomial in t = 128/x^2 - 1.
+// erfcx(x) = exp(x^2) erfc(x) for x >= 0.  On [0, 12): 384 pieces of width
+// 1/32, each a degree-7 polynomial in t = 64x - 2i - 1 (Chebyshev
+// interpolants, truncation below 2e-18 relative); x >= 12: erfcx(x) =
+// g(1/x^2) / x with g a degree-7 polynomial in t = 288/x^2 - 1.
 // The coefficient k of piece i is tab[k (NSEG + 1) + i]; row DEG + 1 holds
 // the low parts of the constant coefficients, added before the final
 // rounding (p = p0 + lo + t q(t)).
@@ -241,12 +241,12 @@ __host__ __device__ __forceinline__ double erfcx_fp64_with(double x, const doubl
     constexpr int S = FABF_ERFCX_NSEG + 1;
     double t;
     int i;
-    const bool large = high_word(x) >= 0x40200000;   // x >= 8 (or NaN) for x >= 0
+    const bool large = high_word(x) >= FABF_ERFCX_XL_HIGH_WORD;   // x >= 12 (or NaN) for x >= 0
     if (!large) {
-        const double q = 8.0 * x;            // exact, in [0, 64)
+        const double q = FABF_ERFCX_PER_UNIT * x;   // exact, in [0, 384)
         // i = floor(q) and its binary64 value from q's bits (integer
         // operations: the FP64 pipe, which bounds the FP64 form, stays
-        // free).  q < 64 has at most 5 integer bits, all in the high word:
+        // free).  q < 384 has at most 9 integer bits, all in the high word:
         // with e the unbiased exponent, i is the top e + 1 bits of the
         // significand and floor(q) is q with the bits below them cleared.
         const int hi = high_word(q);
@@ -254,10 +254,10 @@ __host__ __device__ __forceinline__ double erfcx_fp64_with(double x, const doubl
         const int sh = 20 - (e < 0 ? 0 : e);
         i = e < 0 ? 0 : ((hi & 0xFFFFF) | 0x100000) >> sh;
         const double fq = e < 0 ? 0.0 : from_high_word(hi & ~((1 << sh) - 1));
-        t = fma(2.0, q - fq, -1.0);           // 16x - 2i - 1, exact
+        t = fma(2.0, q - fq, -1.0);           // 64x - 2i - 1, exact
     } else {
         const double r = 1.0 / x;
-        t = fma(128.0, r * r, -1.0);
+        t = fma(FABF_ERFCX_LARGE_T, r * r, -1.0);
         i = FABF_ERFCX_NSEG;
     }
     const double* c = tab + i;
@@ -270,9 +270,9 @@ __host__ __device__ __forceinline__ double erfcx_fp64_with(double x, const doubl
 }
 
 // exp(x) for x <= 709 by Tang's table-driven method (ACM TOMS 15(2), 1989):
-// N = rint(256 x / ln 2) = 256 m + j, r = x - N ln2/256 (two-part
-// constant), exp(x) = 2^m 2^(j/256) (1 + p(r)) with p the Taylor polynomial
-// of degree 5 (|r| <= ln2/512: truncation below 1e-20).  Results below the normal range
+// N = rint(1024 x / ln 2) = 1024 m + j, r = x - N ln2/1024 (two-part
+// constant), exp(x) = 2^m 2^(j/1024) (1 + p(r)) with p the Taylor polynomial
+// of degree 4 (|r| <= ln2/2048: truncation below 4e-20).  Results below the normal range
 // are scaled in two steps (one rounding into the subnormals); x at or below
 // -745.25 gives 0.
 __host__ __device__ __forceinline__ double exp_fp64_with(double x, const double* T)
@@ -283,12 +283,12 @@ __host__ __device__ __forceinline__ double exp_fp64_with(double x, const double*
     if (hx < 0 && (hx & 0x7FFFFFFF) >= 0x40874A00) return x != x ? x : 0.0;
     constexpr double kShift = 0x1.8p52;
     const double y = fma(x, FABF_EXP_INV_L, kShift);
-    const double Nd = y - kShift;             // rint(256 x / ln 2), exact
+    const double Nd = y - kShift;             // rint(1024 x / ln 2), exact
     const int N = low_word(y);
     double r = fma(-Nd, FABF_EXP_L1, x);
     r = fma(-Nd, FABF_EXP_L2, r);
     const int j = N & ((1 << FABF_EXP_TABLE_BITS) - 1), m = N >> FABF_EXP_TABLE_BITS;
-    const double q = fma(fma(fma(r, 1.0 / 120.0, 1.0 / 24.0), r, 1.0 / 6.0), r, 0.5);
+    const double q = fma(fma(r, 1.0 / 24.0, 1.0 / 6.0), r, 0.5);
     const double p = fma(r * r, q, r);        // exp(r) - 1
     const double Tj = FABF_TABLE_LOAD(T + j);
     const double e = fma(Tj, p, Tj);
