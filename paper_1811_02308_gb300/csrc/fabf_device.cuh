@@ -413,6 +413,14 @@ __device__ __forceinline__ double dist_to_unit(double t0, bool& below)
     return below ? -t0 : (b > 0x3FF0000000000000LL ? t0 - 1.0 : 0.0);
 }
 
+// T2 > 0 and F finite, tested on the bits (integer operations; the FP64
+// pipe stays free).  A positive T2 is a positive 64-bit pattern; a NaN T2
+// makes F NaN, which the exponent test catches.
+__device__ __forceinline__ bool ratio_usable(double T2, double F)
+{
+    return __double_as_longlong(T2) > 0 && (high_word(F) & 0x7FF00000) != 0x7FF00000;
+}
+
 // inv2l = 1 / (2 lambda) and rl = 1 / sqrt(lambda), each to within a unit or
 // two in the last place (the callers form them without a division or a
 // square root: 1 / (2 lambda) = sigma^2 / d^2, 1 / sqrt(lambda) =
@@ -437,9 +445,9 @@ __device__ __forceinline__ void integrals_fp64(double lam, double inv2l, double 
         const bool inside = __double_as_longlong(d) == 0;          // d == +0
         const double S = inside ? 2.0 : 0.0;
         const double ca = inside ? E1s : -1.0;
-        const double xa = inside ? sl * (1.0 - t0) : sl * d;
+        const double xa = sl * (inside ? 1.0 - t0 : d);
         const double cb = inside ? E0s : (below ? E1s : E0s);
-        const double xb = inside ? sl * t0 : sl * (1.0 + d);
+        const double xb = sl * (inside ? t0 : 1.0 + d);
         const double I0 = h * (S - ca * erfcx_sel<Own>(xa) - cb * erfcx_sel<Own>(xb));
         const double e1 = E1s * inv2l;
         I[0] = I0;
@@ -516,7 +524,15 @@ __device__ __forceinline__ double fp64_ratio(const double (&c)[N + 1], int alpha
         T1 = fma(c[k - 1], I[k], T1);
         T2 = fma(c[k - 1], I[k - 1], T2);
     }
-    return T1 / T2;
+    // F = T1 / T2 to within about one unit in the last place, without the
+    // division's special-case handling: the approximate reciprocal, one
+    // Newton step, and one correction of the quotient from its exact
+    // residual.  T2 <= 0, zero or not finite gives a non-finite or unused
+    // F: the callers take the fallback then.
+    const double r0 = rcp_approx_f64(T2);
+    const double r1 = fma(r0, fma(-T2, r0, 1.0), r0);
+    const double F0 = T1 * r1;
+    return fma(fma(-T2, F0, T1), r1, F0);
 }
 
 template <int N, bool Own = true>
@@ -537,7 +553,7 @@ __device__ __forceinline__ double fabf_tail_fp64(const AinvTable& A, int alpha, 
     double t0, lam, I[N + 2], T1, T2;
     double F = fp64_ratio<N, Own>(c, alpha, d, theta_f, sigma_f, t0, lam, I, T1, T2);
     fallback = 0;
-    if (!(T2 > 0.0) || !isfinite(F)) {   // fitted polynomial not positive enough
+    if (!ratio_usable(T2, F)) {       // fitted polynomial not positive enough
         F = mu[1] / mu[0];                // sigma -> infinity limit (spatial-kernel mean)
         fallback = 1;
     }
@@ -925,7 +941,7 @@ __device__ __forceinline__ double fabf_redo_scaled(const uint64_t (&v)[(N < 1 ? 
     double t0, lam, I[N + 2], T1, T2;
     double F = fp64_ratio<N, false>(c, alpha, d, theta_f, sigma_f, t0, lam, I, T1, T2);
     fallback = 0;
-    if (!(T2 > 0.0) || !isfinite(F)) {   // the sigma -> infinity limit, as fabf_tail_fp64
+    if (!ratio_usable(T2, F)) {       // the sigma -> infinity limit, as fabf_tail_fp64
         F = ((double)muh[1] + (double)mul[1]) / ((double)muh[0] + (double)mul[0]);
         fallback = 1;
     }
