@@ -60,6 +60,32 @@ STAGE_CASES = [
 ]
 
 
+def test_t0_and_lambda_are_the_correctly_rounded_quotients(ctx):
+    """t0 = (theta - alpha) / d and lambda = d^2 / (2 sigma^2) (Eq. 25) in the
+    FP64 form equal the IEEE binary64 quotients bit for bit, on 147k windows
+    of a noise image with sigma spread over nine decades and theta over
+    [-50, 300] (the kernel forms both quotients without the division
+    instruction)."""
+    H = W = 384
+    rng = np.random.default_rng(77)
+    f = rng.integers(0, 256, (H, W), dtype=np.uint8)
+    th = rng.uniform(-50, 300, (H, W)).astype(np.float32)
+    s = (10.0 ** rng.uniform(-3, 6, (H, W))).astype(np.float32)
+    s[0, :8] = [np.float32(v) for v in (1e-3, 0.1, 1.0, 5.0, 60.0, 255.0, 1e5, 1e6)]
+    o = fabf.fabf_debug_stages(ctx, dev(f), dev(th), dev(s), 2, 2)
+    a = o["alpha"].cpu().numpy().astype(np.float64)
+    b = o["beta"].cpu().numpy().astype(np.float64)
+    t0lam = o["t0lam"].cpu().numpy()
+    live = b > a
+    assert live.sum() > 140000
+    d = (b - a)[live]
+    s64 = s.astype(np.float64)[live]
+    lam_ref = (d * d) / (2.0 * s64 * s64)
+    t0_ref = (th.astype(np.float64)[live] - a[live]) / d
+    assert np.array_equal(t0lam[1][live].view(np.uint64), lam_ref.view(np.uint64))
+    assert np.array_equal(t0lam[0][live].view(np.uint64), t0_ref.view(np.uint64))
+
+
 @pytest.mark.parametrize("H,W,w,N,seed", STAGE_CASES)
 def test_stages_match_oracle(ctx, oracle_mod, H, W, w, N, seed):
     f, th, s = inputs(H, W, seed)
