@@ -440,12 +440,17 @@ __device__ __forceinline__ void integrals_fp64(double lam, double inv2l, double 
         // a = sqrt(lambda)(1 - t0), b = sqrt(lambda) t0, E = E1 (t0 < 0) or E0.
         bool below;
         const double d = dist_to_unit(t0, below);
-        const double E0s = exp_sel<Own>(-lam * ((t0 - d) * (t0 + d)));
-        const double E1s = exp_sel<Own>(-lam * ((1.0 - t0 - d) * (1.0 - t0 + d)));
         const bool inside = __double_as_longlong(d) == 0;          // d == +0
+        // t0^2 - d^2 and (1 - t0)^2 - d^2 in each position of t0: inside,
+        // t0^2 and (1 - t0)^2; below 0, 0 and 1 - 2 t0; above 1, 2 t0 - 1 and 0
+        const double u = 1.0 - t0, v = fma(2.0, t0, -1.0);
+        const double g0 = inside ? t0 * t0 : (below ? 0.0 : v);
+        const double g1 = inside ? u * u : (below ? -v : 0.0);
+        const double E0s = exp_sel<Own>(-lam * g0);
+        const double E1s = exp_sel<Own>(-lam * g1);
         const double S = inside ? 2.0 : 0.0;
         const double ca = inside ? E1s : -1.0;
-        const double xa = sl * (inside ? 1.0 - t0 : d);
+        const double xa = sl * (inside ? u : d);
         const double cb = inside ? E0s : (below ? E1s : E0s);
         const double xb = sl * (inside ? t0 : 1.0 + d);
         const double I0 = h * (S - ca * erfcx_sel<Own>(xa) - cb * erfcx_sel<Own>(xb));
@@ -457,17 +462,24 @@ __device__ __forceinline__ void integrals_fp64(double lam, double inv2l, double 
     } else {
         bool below;
         const double d = dist_to_unit(t0, below);
-        const double E1s = exp_sel<Own>(-lam * ((1.0 - t0 - d) * (1.0 - t0 + d)));   // exp(-lam (1-t0)^2 + lam d^2)
+        const bool inside = __double_as_longlong(d) == 0;
+        const double u = 1.0 - t0;
+        // (1 - t0)^2 - d^2: (1 - t0)^2 inside, 1 - 2 t0 below 0, 0 above 1
+        const double g1 = inside ? u * u : (below ? fma(-2.0, t0, 1.0) : 0.0);
+        const double E1s = exp_sel<Own>(-lam * g1);   // exp(-lam (1-t0)^2 + lam d^2)
         int Kp = backward_start_index(lam, t0);
         Kp = __reduce_max_sync(__activemask(), (unsigned)Kp);
         const double l2 = 2.0 * lam;
-        const double q = l2 * (t0 - 1.0);
+        const double q = -l2 * u;                      // 2 lambda (t0 - 1)
         const double kp2 = small_to_double(Kp + 2), kp1 = small_to_double(Kp + 1);
         const double r1 = kp2 + q, r0 = kp1 + q;
         // start values: a few percent is enough (the recursion damps their
         // error below 1e-13 by index K), so approximate reciprocals
-        double hi = E1s * rcp_approx_f64(r1 > 1.0 ? r1 : kp2);   // I_{Kp+1}
-        double lo = E1s * rcp_approx_f64(r0 > 1.0 ? r0 : kp1);   // I_{Kp}
+        // (r > 1 tested on the bits: ordered as the values, negative ones
+        // negative)
+        constexpr long long kOneBits = 0x3FF0000000000000LL;
+        double hi = E1s * rcp_approx_f64(__double_as_longlong(r1) > kOneBits ? r1 : kp2);   // I_{Kp+1}
+        double lo = E1s * rcp_approx_f64(__double_as_longlong(r0) > kOneBits ? r0 : kp1);   // I_{Kp}
         // (hi, lo) = (I_k, I_{k-1}); produce I_{k-2} for k = Kp+1 .. K+2.
         for (int k = Kp + 1; k >= K + 2; --k) {
             const double nx = fma(l2, fma(-t0, lo, hi), E1s) * c_recip.v[k - 1];
