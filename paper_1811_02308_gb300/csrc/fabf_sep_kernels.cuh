@@ -95,7 +95,7 @@ __device__ __forceinline__ double u128_to_double_rn(u128 v)
         top = (hi << (64 - s)) | (lo >> s);
         sticky = (lo << (64 - s)) != 0;
     }
-    return ldexp(__ull2double_rn(top | sticky), s);
+    return __ull2double_rn(top | sticky) * pow2i(s);   // exact scaling by 2^s
 }
 
 // acc += g * v for a 64-bit v and a 16-bit g whose product fits in 64 bits.
@@ -149,13 +149,13 @@ __device__ __forceinline__ double sep_pixel_fp64(int alpha, int beta, int fi, co
     if (alpha == beta) return (double)fi;                // flat window, Sec. II-A
     const int d = beta - alpha;
     sep_shifted_moments<K>(alpha, m, M);
+    // mu_k = RN(M_k / d^k): the correctly rounded quotient from the
+    // correctly rounded reciprocal of d^k (div_by_power), as in the box path
     double mu[K + 1];
-    int64_t dk = 1;
+    mu[0] = u128_to_double_rn(M[0]);
 #pragma unroll
-    for (int k = 0; k <= K; ++k) {
-        mu[k] = u128_to_double_rn(M[k]) / (double)dk;
-        dk *= d;
-    }
+    for (int k = 1; k <= K; ++k)
+        mu[k] = div_by_power(u128_to_double_rn(M[k]), __ldg(&g_recip_pow.p[k - 1][d]), __ldg(&g_recip_pow.v[k - 1][d]));
     return fabf_tail_fp64<N, Own>(c_ainv, alpha, d, mu, th, sg, fallback, tr);
 }
 
