@@ -64,8 +64,9 @@ def test_t0_and_lambda_are_the_correctly_rounded_quotients(ctx):
     """t0 = (theta - alpha) / d and lambda = d^2 / (2 sigma^2) (Eq. 25) in the
     FP64 form equal the IEEE binary64 quotients bit for bit, on 147k windows
     of a noise image with sigma spread over nine decades and theta over
-    [-50, 300] (the kernel forms both quotients without the division
-    instruction)."""
+    [-50, 300] (the kernel forms t0 from a table of correctly rounded
+    reciprocals, and lambda's operands from a table of powers of d and from
+    the bits of sigma)."""
     H = W = 384
     rng = np.random.default_rng(77)
     f = rng.integers(0, 256, (H, W), dtype=np.uint8)
