@@ -45,7 +45,7 @@ WORKLOAD = ("1920x1080 uint8 synthetic (200 blobs, 4 step edges, noise 10), box 
 # library picks; profiles/); None for a kernel not captured since it last
 # changed.  The float output of a launch stays in the 126 MB L2 when the
 # kernel ends, so the figure is the 9 B/px of compulsory reads.
-NCU_TRAFFIC_BYTES = 18.77e6        # FP64 form kernel (8-row tiles)
+NCU_TRAFFIC_BYTES = 18.81e6        # FP64 form kernel (8-row tiles)
 NCU_TRAFFIC_BYTES_FP64FIT = None   # FP64-fit kernel
 NCU_TRAFFIC_BYTES_CFP32 = None     # compensated binary32 kernel
 NCU_TRAFFIC_BYTES_C32 = 18.78e6    # centred binary32 kernel (16-row tiles, 4 CTAs per SM)
@@ -90,7 +90,7 @@ def cfp32_executed_flops_per_pixel(N: int) -> float:
 # (32 x smsp__inst_executed.sum / pixels, one ncu capture of the launch
 # bench.py times; profiles/); a kernel is left out once it changes until it
 # is captured again.
-NCU_INST_PER_PIXEL = {3: 1222.2}
+NCU_INST_PER_PIXEL = {3: 1225.4}
 
 # This GPU's arithmetic pipe peaks, measured at start-up by fabf_pipe_peaks
 # (CUDA events around FP64 / FP32 FMA, INT32 IMAD and MUFU loops).
