@@ -216,6 +216,31 @@ __host__ __device__ __forceinline__ double from_high_word(int hi)
 #endif
 }
 
+// RN(x) in binary32 from x's bits (integer operations; the conversion
+// instruction issues on the FP64 pipe, which bounds the forms with a binary64
+// fit): the top 23 fraction bits, rounded to nearest even on the 29 below
+// them (a carry into the exponent is the correct result, up to infinity).
+// Results outside the normal binary32 range, zero, infinities and NaN take
+// the conversion instruction.
+__host__ __device__ __forceinline__ float double_to_float_rn(double x)
+{
+    const int hi = high_word(x);
+    const unsigned lo = (unsigned)low_word(x);
+    const int e = ((hi >> 20) & 0x7FF) - 1023 + 127;              // binary32 biased exponent
+    if (e < 1 || e > 254) return (float)x;
+    const unsigned m = ((unsigned)(hi & 0xFFFFF) << 3) | (lo >> 29);
+    const unsigned rem = lo & 0x1FFFFFFFu;
+    unsigned b = ((unsigned)hi & 0x80000000u) | ((unsigned)e << 23) | m;
+    b += (rem > 0x10000000u || (rem == 0x10000000u && (m & 1u))) ? 1u : 0u;
+#ifdef __CUDA_ARCH__
+    return __uint_as_float(b);
+#else
+    float f;
+    std::memcpy(&f, &b, 4);
+    return f;
+#endif
+}
+
 // 2^m for -1022 <= m <= 1023, exactly.
 __host__ __device__ __forceinline__ double pow2i(int m)
 {
@@ -778,7 +803,7 @@ __device__ __forceinline__ float fabf_fit_tail_fp64fit(const AinvTable& A, const
         double acc = 0.0;
 #pragma unroll
         for (int k = 0; k <= N; ++k) acc = fma(A.v[N][n][k], mu[k], acc);
-        c[n] = (float)acc;
+        c[n] = double_to_float_rn(acc);
     }
     return fabf_tail_fp32<N>(c, [&] { return (float)(mu[1] / mu[0]); }, alpha, d, theta_f, sigma_f, fallback, redo);
 }

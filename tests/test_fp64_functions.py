@@ -86,3 +86,27 @@ def test_table_header_is_the_generators_output():
                          check=True)
     with open(os.path.join(CSRC, "fabf_fp64_tables.h")) as fh:
         assert fh.read() == res.stdout
+
+
+def test_double_to_float_rounding_is_ieee(checker):
+    """The FP64-fit form rounds its binary64 coefficients to binary32 from the
+    bits (double_to_float_rn); the result equals IEEE round-to-nearest-even
+    (numpy's cast) on random values over the whole binary32 range, on exact
+    ties of both parities, at the range edges and past them."""
+    rng = np.random.default_rng(9)
+    mant = rng.integers(0, 1 << 52, 4000, dtype=np.uint64)
+    expo = rng.integers(1023 - 160, 1023 + 140, 4000, dtype=np.uint64)
+    sign = rng.integers(0, 2, 4000, dtype=np.uint64) << np.uint64(63)
+    xs = list((sign | (expo << np.uint64(52)) | mant).view(np.float64))
+    # ties: the 29 discarded bits exactly one half, with even and odd kept bits
+    for k in range(200):
+        kept = int(rng.integers(0, 1 << 23))
+        e = int(rng.integers(1023 - 126, 1023 + 128))
+        xs.append(np.uint64((e << 52) | (kept << 29) | (1 << 28)).view(np.float64).item())
+    big = float(np.finfo(np.float32).max)
+    xs += [0.0, -0.0, 1.0, -1.0, big, np.nextafter(big, np.inf), big * (1 + 2.0 ** -25), big * (1 + 2.0 ** -24),
+           float(np.finfo(np.float32).tiny), 1e-39, -1e-45, 1e-50, 1e300, -1e300, float("inf"), 3.4028235677973366e38]
+    got = np.array(checker("d2f", xs))
+    with np.errstate(over="ignore"):
+        ref = np.array(xs, dtype=np.float64).astype(np.float32).astype(np.float64)
+    assert np.array_equal(got.view(np.uint64), ref.view(np.uint64))
